@@ -1,0 +1,212 @@
+/*
+ * bfvm.h -- C ABI of the GB300 substrate transport step.
+ *
+ * The library advances the hybrid transport PDE of Eq. (1)
+ *
+ *     d rho/dt = D lap(rho) - lambda rho
+ *                + sum_i delta(x - x_i) V_i (S_i (rho*_i - rho) - U_i rho)
+ *
+ * (element-wise over substrates) with the locally-one-dimensional (LOD)
+ * implicit finite-volume scheme that the paper ports to the GPU
+ * ("Using OpenACC programming model for PhysiCell", "Elements of
+ * Parallelism": x-, y- and z-diffusion sweeps, Dirichlet conditions applied
+ * on the device, AXPY-style line updates).  One step is
+ *
+ *   1. Dirichlet prologue: the outer voxel shell of every Dirichlet
+ *      substrate is set to its value;
+ *   2. x-solve: for every line along x, rho <- A_x^{-1} rho, where the line
+ *      matrix has diagonal 1 + lambda dt/3 + c (ends) or 1 + lambda dt/3 + 2c
+ *      (inside), off-diagonals -c, c = D dt / dx^2 (zero-flux faces); then
+ *      the Dirichlet shell again;
+ *   3. the same along y, then along z;
+ *   4. cell sources: for each cell i in ascending index order, in its voxel v,
+ *      rho_v <- (rho_v + dt (V_i/V_vox) S_i rho*_i) / (1 + dt (V_i/V_vox)(S_i+U_i)),
+ *      V_vox = dx^3 (the delta term of Eq. 1, implicit in time).
+ *
+ * A cell at position p (micrometres, domain origin at 0) belongs to voxel
+ * v_a = min(floor(p_a / dx), n_a - 1) on each axis a.
+ *
+ * Conventions shared by every call:
+ *  - Field layout seen by callers: rho[s][z][y][x], x fastest, contiguous,
+ *    n_sub * nz * ny * nx elements, element type double for precision 64 and
+ *    float for precision 32.
+ *  - Ownership: the context owns all of its device state (field,
+ *    coefficient tables, binned cell data, checkpoints).  Buffers passed in
+ *    are owned by the caller, are copied, and are never retained after the
+ *    call returns.  With on_device = 1 a pointer is device memory of the
+ *    context's device; the copy is ordered on the context's stream.  With
+ *    on_device = 0 it is host memory and the call returns after the copy.
+ *  - Errors: every call returns a bfvm_status; nothing is thrown across the
+ *    ABI.  bfvm_last_error() gives a text for the last failure of a context.
+ *    Arguments are checked on the host before any launch.  Kernels that wait
+ *    on device flags give up after a bounded number of polls and report
+ *    BFVM_ETIMEOUT instead of hanging.
+ *  - Streams: cuda_stream is a cudaStream_t (NULL = the legacy default
+ *    stream).  All work of a context is ordered on it.
+ */
+#ifndef BFVM_H
+#define BFVM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    BFVM_OK = 0,
+    BFVM_EINVAL = 1,      /* bad argument (sizes, signs, non-finite, range) */
+    BFVM_ENOMEM = 2,      /* a device or host allocation failed */
+    BFVM_ECUDA = 3,       /* a CUDA runtime or driver call failed */
+    BFVM_ESTATE = 4,      /* call not valid in the context's current state */
+    BFVM_ETIMEOUT = 5,    /* a bounded device wait gave up */
+    BFVM_ENONFINITE = 6   /* a NaN or Inf was found where it is not allowed */
+} bfvm_status;
+
+enum { BFVM_BC_ZERO_FLUX = 0, BFVM_BC_DIRICHLET = 1 };
+
+typedef struct bfvm_ctx bfvm_ctx;
+typedef struct bfvm_batch bfvm_batch;
+
+/*
+ * Create a simulation context (the device-side counterpart of the paper's
+ * transfer-3D: allocate the field and the solver constants on the GPU once).
+ *   nx, ny, nz    grid edges in voxels, each >= 1
+ *   dx_um         voxel edge (micrometres), > 0; V_vox = dx^3
+ *   dt_min        time step (minutes), > 0
+ *   n_sub         number of substrates, >= 1
+ *   D[n_sub]      diffusion coefficients (um^2/min), >= 0, finite
+ *   lambda[n_sub] decay rates (1/min), >= 0, finite
+ *   bc_kind[n_sub]  BFVM_BC_ZERO_FLUX or BFVM_BC_DIRICHLET (outer voxel
+ *                 shell on all six faces held at bc_value)
+ *   bc_value[n_sub] Dirichlet value (ignored for zero-flux), finite
+ *   precision     64 (FP64 field and sweeps) or 32 (FP32 field and sweeps;
+ *                 coefficient tables are still built in FP64, then rounded)
+ *   cuda_stream   cudaStream_t for all of the context's work
+ * The field starts at zero and there are no cells.  *out is set to NULL on
+ * failure.  Host pointers are read during the call only.
+ */
+bfvm_status bfvm_create(bfvm_ctx** out, int32_t nx, int32_t ny, int32_t nz,
+                        double dx_um, double dt_min, int32_t n_sub,
+                        const double* D, const double* lambda,
+                        const int32_t* bc_kind, const double* bc_value,
+                        int32_t precision, void* cuda_stream);
+
+/* Release every resource of the context (NULL is allowed). */
+void bfvm_destroy(bfvm_ctx* ctx);
+
+/*
+ * Replace the whole field (paper: transfer-3D / translate-vector-to-array).
+ *   rho  [n_sub][nz][ny][nx] of the context's element type, finite.
+ * Resets any recorded forward run.
+ */
+bfvm_status bfvm_set_density(bfvm_ctx* ctx, const void* rho, int32_t on_device);
+
+/*
+ * Copy the field out (paper: translate-array-to-vector), same layout and
+ * element type as bfvm_set_density.
+ */
+bfvm_status bfvm_get_density(bfvm_ctx* ctx, void* out, int32_t on_device);
+
+/*
+ * Set the cell agents that act as sources and sinks (the delta term of
+ * Eq. 1).  All arrays are FP64, in cell-index order:
+ *   pos[n][3]          position (um), each coordinate in [0, n_a * dx]
+ *   vol[n]             volume V_i (um^3), > 0
+ *   S[n][n_sub]        secretion rate (1/min), >= 0
+ *   U[n][n_sub]        uptake rate (1/min), >= 0
+ *   rho_star[n][n_sub] target density rho*_i, finite
+ * n_cells = 0 removes all cells.  The cells are binned to voxels, stably
+ * sorted by voxel (cell index order kept inside a voxel), and each voxel's
+ * cells are composed, in index order and in FP64, into one affine map
+ * rho <- alpha rho + beta per substrate.  Resets any recorded forward run.
+ */
+bfvm_status bfvm_set_cells(bfvm_ctx* ctx, int64_t n_cells, const double* pos,
+                           const double* vol, const double* S, const double* U,
+                           const double* rho_star, int32_t on_device);
+
+/* Advance n_steps >= 0 full steps (prologue, x, y, z, sources) on the
+ * context's stream.  Asynchronous: errors of the kernels themselves surface
+ * at the next synchronising call (bfvm_sync, bfvm_get_density with a host
+ * pointer, bfvm_backward). */
+bfvm_status bfvm_step(bfvm_ctx* ctx, int32_t n_steps);
+
+/* Block until the context's stream is idle; reports device-side errors. */
+bfvm_status bfvm_sync(bfvm_ctx* ctx);
+
+/*
+ * Enable (checkpoint_every >= 1) or disable (0) recording for the adjoint.
+ * While enabled, each bfvm_step(n) stores the field at the start of steps
+ * 0, k, 2k, ... of that call (ceil(n/k) fields of device memory) and
+ * bfvm_backward then differentiates that call.
+ */
+bfvm_status bfvm_record(bfvm_ctx* ctx, int32_t checkpoint_every);
+
+/*
+ * Reverse mode of the last recorded bfvm_step(n) call.
+ *   dL_drho_final  [n_sub][nz][ny][nx] FP64 gradient of the loss with
+ *                  respect to the field after that call
+ *   checkpoint_every  must equal the recorded interval (or 0 for "as
+ *                  recorded")
+ *   dD[n_sub], dlambda[n_sub]           FP64 outputs
+ *   dS[n][n_sub], dU[n][n_sub]          FP64 outputs, cell-index order
+ *   dL_drho0       optional (may be NULL) FP64 gradient with respect to the
+ *                  field before the call
+ * Every segment of k steps is replayed from its checkpoint; the adjoint of
+ * each step runs the sources' adjoint, then the z, y, x solves (the line
+ * matrices are symmetric), each after zeroing the Dirichlet shell's
+ * adjoint.  Only FP64 contexts.  BFVM_ESTATE if nothing was recorded.
+ * Output pointers follow on_device like the input.
+ */
+bfvm_status bfvm_backward(bfvm_ctx* ctx, const double* dL_drho_final,
+                          int32_t checkpoint_every, double* dD, double* dlambda,
+                          double* dS, double* dU, double* dL_drho0,
+                          int32_t on_device);
+
+/* Text of the last failure on this context ("" if none; ctx may be NULL,
+ * then the text of the last failed bfvm_create of this thread). */
+const char* bfvm_last_error(const bfvm_ctx* ctx);
+
+/* Name of a status code. */
+const char* bfvm_status_string(int32_t status);
+
+/*
+ * Introspection, for tests and benchmarks.  info[16] receives:
+ *  0 precision, 1 nx, 2 ny, 3 nz, 4 n_sub, 5 row pitch (elements),
+ *  6 number of source voxels, 7 steps taken since create,
+ *  8 sweep variant in use (0 plain, 1 rescaled), 9 rescale period,
+ *  10 device kernel launches issued since create, 11 recorded steps,
+ *  12..15 reserved (0).
+ */
+bfvm_status bfvm_get_info(const bfvm_ctx* ctx, int64_t* info);
+
+/*
+ * Options (set before the first step; each returns BFVM_EINVAL for an
+ * unknown key or value):
+ *   key 1  sweep variant: 0 plain Thomas (3 flops per element per axis),
+ *          1 rescaled Thomas (2 FMA per element per axis, FP64 only; the
+ *          default for FP64)
+ *   key 2  rescale period override (1..64; 0 = automatic)
+ *   key 3  fuse cell sources into the z sweep: 0 no, 1 yes
+ *   key 4  use CUDA graphs for bfvm_step: 0 no, 1 yes (default)
+ */
+bfvm_status bfvm_set_option(bfvm_ctx* ctx, int32_t key, int64_t value);
+
+/*
+ * Batched form: many independent contexts advanced together, one launch
+ * per sweep phase over a flat list of line blocks of all members (captured
+ * in a CUDA graph).  Members keep their own state; set and read them with
+ * the single-context calls.  All members must use the same precision and
+ * must not be stepped individually while the batch exists.
+ */
+bfvm_status bfvm_batch_create(bfvm_batch** out, bfvm_ctx* const* members,
+                              int32_t n_members, void* cuda_stream);
+bfvm_status bfvm_batch_step(bfvm_batch* batch, int32_t n_steps);
+bfvm_status bfvm_batch_sync(bfvm_batch* batch);
+void bfvm_batch_destroy(bfvm_batch* batch);
+const char* bfvm_batch_last_error(const bfvm_batch* batch);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BFVM_H */

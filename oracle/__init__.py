@@ -1,0 +1,239 @@
+"""Plain FP64 CPU oracle of the LOD diffusion-decay-source step (Eq. 1).
+
+TEST INFRASTRUCTURE ONLY.  Only the tests, the package's ``smoke()`` check and
+the CPU-baseline leg of ``bench.py`` import this module.  The library path
+never does, and this module imports nothing from the library.
+
+The arithmetic lives in ``oracle.c`` (plain C, FP64, every operation rounded
+on its own: the build disables floating-point contraction so that x86 and Arm
+hosts give the same bits).  This file builds it with gcc and wraps it with
+ctypes.
+
+Functions and the passages they follow:
+
+* ``line_matrix``     -- the per-axis implicit diffusion-decay matrix of Eq. 1
+                         (zero-flux cell-centred finite volumes, LOD decay
+                         share lambda*dt/3).
+* ``tridiag_solve``   -- textbook Thomas algorithm (the x/y/z diffusion
+                         sweeps of "Using OpenACC programming model").
+* ``apply_dirichlet`` -- the Dirichlet condition of "Elements of Parallelism".
+* ``axis_solve``      -- one LOD sweep along one axis.
+* ``cell_voxel``      -- voxel of a cell (cell-centred grid, origin 0).
+* ``apply_sources``   -- the delta source term of Eq. 1, implicit, cells in
+                         ascending index order.
+* ``run``             -- n full steps.
+* ``adjoint``         -- literal reverse of ``run`` (gradients of a loss with
+                         respect to D, lambda, per-cell S and U).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+_dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int)
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c into _build/liboracle.so (gcc, OpenMP if present)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    base = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
+            "-shared", _SRC, "-o", tmp, "-lm"]
+    try:
+        subprocess.run(base[:1] + ["-fopenmp"] + base[1:], check=True,
+                       capture_output=True)
+    except subprocess.CalledProcessError:
+        subprocess.run(base, check=True, capture_output=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            lib.oracle_line_matrix.argtypes = [ctypes.c_int, ctypes.c_double,
+                                               ctypes.c_double, _dp, _dp, _dp]
+            lib.oracle_line_matrix.restype = None
+            lib.oracle_tridiag_solve.argtypes = [ctypes.c_int, _dp, _dp, _dp,
+                                                 _dp, _dp, _dp]
+            lib.oracle_tridiag_solve.restype = None
+            lib.oracle_apply_dirichlet.argtypes = [ctypes.c_int] * 4 + [_ip, _dp, _dp]
+            lib.oracle_apply_dirichlet.restype = None
+            lib.oracle_axis_solve.argtypes = ([ctypes.c_int] * 5 + [ctypes.c_double] * 2
+                                              + [_dp, _dp, _dp, ctypes.c_int])
+            lib.oracle_axis_solve.restype = None
+            lib.oracle_cell_voxel.argtypes = [ctypes.c_int] * 3 + [ctypes.c_double, _dp]
+            lib.oracle_cell_voxel.restype = ctypes.c_int64
+            lib.oracle_apply_sources.argtypes = ([ctypes.c_int] * 4 + [ctypes.c_double] * 2
+                                                 + [ctypes.c_int64] + [_dp] * 6)
+            lib.oracle_apply_sources.restype = None
+            common = ([ctypes.c_int] * 3 + [ctypes.c_double] * 2 + [ctypes.c_int]
+                      + [_dp, _dp, _ip, _dp, ctypes.c_int64, _dp, _dp, _dp, _dp, _dp])
+            lib.oracle_run.argtypes = common + [ctypes.c_int, ctypes.c_int, _dp]
+            lib.oracle_run.restype = ctypes.c_int
+            lib.oracle_adjoint.argtypes = common + [ctypes.c_int] * 3 + [_dp] * 8
+            lib.oracle_adjoint.restype = ctypes.c_int
+            lib.oracle_max_threads.argtypes = []
+            lib.oracle_max_threads.restype = ctypes.c_int
+            _lib = lib
+    return _lib
+
+
+def _d(a):
+    return a.ctypes.data_as(_dp)
+
+
+def _f64(a, shape=None):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if shape is not None:
+        a = a.reshape(shape)
+    return a
+
+
+def max_threads() -> int:
+    return int(_load().oracle_max_threads())
+
+
+def line_matrix(n: int, c: float, ell: float):
+    """(lower, diag, upper) of the line matrix along one axis."""
+    lib = _load()
+    lo, di, up = (np.zeros(n) for _ in range(3))
+    lib.oracle_line_matrix(n, c, ell, _d(lo), _d(di), _d(up))
+    return lo, di, up
+
+
+def tridiag_solve(lower, diag, upper, rhs):
+    lib = _load()
+    lower, diag, upper, rhs = (_f64(v) for v in (lower, diag, upper, rhs))
+    n = rhs.shape[0]
+    x = np.zeros(n)
+    work = np.zeros(n)
+    lib.oracle_tridiag_solve(n, _d(lower), _d(diag), _d(upper), _d(rhs), _d(x), _d(work))
+    return x
+
+
+class _Cells:
+    def __init__(self, p, n_sub):
+        n = 0 if p.pos is None else int(p.pos.shape[0])
+        self.n = n
+        if n == 0:
+            z = np.zeros(1)
+            self.pos = np.zeros(3)
+            self.vol = z
+            self.S = z.copy()
+            self.U = z.copy()
+            self.rho_star = z.copy()
+        else:
+            self.pos = _f64(p.pos, (n, 3))
+            self.vol = _f64(p.vol, (n,))
+            self.S = _f64(p.S, (n, n_sub))
+            self.U = _f64(p.U, (n, n_sub))
+            self.rho_star = _f64(p.rho_star, (n, n_sub))
+
+
+def _common(p):
+    n_sub = int(len(p.D))
+    D = _f64(p.D)
+    lam = _f64(p.lam)
+    kind = np.ascontiguousarray(p.bc_kind, dtype=np.int32)
+    val = _f64(p.bc_value)
+    cells = _Cells(p, n_sub)
+    keep = (D, lam, kind, val, cells)
+    args = [int(p.nx), int(p.ny), int(p.nz), float(p.dx), float(p.dt), n_sub,
+            _d(D), _d(lam), kind.ctypes.data_as(_ip), _d(val), ctypes.c_int64(cells.n),
+            _d(cells.pos), _d(cells.vol), _d(cells.S), _d(cells.U), _d(cells.rho_star)]
+    return args, keep
+
+
+def run(p, rho0=None, n_steps=None, n_threads: int = 0):
+    """Field after n_steps (default p.steps) full steps from rho0 (default p.rho0)."""
+    lib = _load()
+    rho = _f64(p.rho0 if rho0 is None else rho0).copy()
+    steps = int(p.steps if n_steps is None else n_steps)
+    args, keep = _common(p)
+    rc = lib.oracle_run(*args, steps, int(n_threads or max_threads()), _d(rho))
+    if rc != 0:
+        raise ValueError(f"oracle_run failed ({rc})")
+    del keep
+    return rho
+
+
+def adjoint(p, g_final, rho0=None, n_steps=None, checkpoint_every: int = 20,
+            n_threads: int = 0):
+    """Gradients of L given dL/drho_final; returns dict with dD, dlambda, dS, dU, g0, rho_final."""
+    lib = _load()
+    rho0 = _f64(p.rho0 if rho0 is None else rho0)
+    steps = int(p.steps if n_steps is None else n_steps)
+    n_sub = len(p.D)
+    n = 0 if p.pos is None else int(p.pos.shape[0])
+    g_final = _f64(g_final)
+    dD = np.zeros(n_sub)
+    dl = np.zeros(n_sub)
+    dS = np.zeros(max(n, 1) * n_sub)
+    dU = np.zeros(max(n, 1) * n_sub)
+    g0 = np.zeros_like(rho0)
+    fin = np.zeros_like(rho0)
+    args, keep = _common(p)
+    rc = lib.oracle_adjoint(*args, steps, int(checkpoint_every),
+                            int(n_threads or max_threads()), _d(rho0), _d(g_final),
+                            _d(dD), _d(dl), _d(dS), _d(dU), _d(g0), _d(fin))
+    if rc != 0:
+        raise ValueError(f"oracle_adjoint failed ({rc})")
+    del keep
+    return {"dD": dD, "dlambda": dl, "dS": dS[: n * n_sub].reshape(n, n_sub),
+            "dU": dU[: n * n_sub].reshape(n, n_sub), "g0": g0, "rho_final": fin}
+
+
+def apply_dirichlet(p, rho):
+    lib = _load()
+    rho = _f64(rho).copy()
+    kind = np.ascontiguousarray(p.bc_kind, dtype=np.int32)
+    val = _f64(p.bc_value)
+    lib.oracle_apply_dirichlet(int(p.nx), int(p.ny), int(p.nz), len(p.D),
+                               kind.ctypes.data_as(_ip), _d(val), _d(rho))
+    return rho
+
+
+def axis_solve(p, rho, axis: int, n_threads: int = 1):
+    lib = _load()
+    rho = _f64(rho).copy()
+    D = _f64(p.D)
+    lam = _f64(p.lam)
+    lib.oracle_axis_solve(int(axis), int(p.nx), int(p.ny), int(p.nz), len(p.D),
+                          float(p.dx), float(p.dt), _d(D), _d(lam), _d(rho), int(n_threads))
+    return rho
+
+
+def cell_voxel(p, pos) -> int:
+    lib = _load()
+    pos = _f64(pos, (3,))
+    return int(lib.oracle_cell_voxel(int(p.nx), int(p.ny), int(p.nz), float(p.dx), _d(pos)))
+
+
+def apply_sources(p, rho):
+    lib = _load()
+    rho = _f64(rho).copy()
+    n_sub = len(p.D)
+    cells = _Cells(p, n_sub)
+    lib.oracle_apply_sources(int(p.nx), int(p.ny), int(p.nz), n_sub, float(p.dx),
+                             float(p.dt), ctypes.c_int64(cells.n), _d(cells.pos),
+                             _d(cells.vol), _d(cells.S), _d(cells.U),
+                             _d(cells.rho_star), _d(rho))
+    return rho
