@@ -1,0 +1,339 @@
+"""Thin ctypes binding of libbfvm (include/bfvm.h), same names as the C ABI.
+
+Argument marshalling only: every step of the transport path runs in the
+library's CUDA kernels.  PyTorch supplies device memory and streams.  If the
+compiled library is missing the import of a binding function raises; there is
+no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libbfvm.so")
+
+BFVM_OK = 0
+STATUS_NAMES = {0: "BFVM_OK", 1: "BFVM_EINVAL", 2: "BFVM_ENOMEM", 3: "BFVM_ECUDA",
+                4: "BFVM_ESTATE", 5: "BFVM_ETIMEOUT", 6: "BFVM_ENONFINITE"}
+BC_ZERO_FLUX = 0
+BC_DIRICHLET = 1
+
+OPT_VARIANT = 1
+OPT_PERIOD = 2
+OPT_FUSE_SOURCES = 3
+OPT_GRAPHS = 4
+
+EXPORTED = ["bfvm_create", "bfvm_destroy", "bfvm_set_density", "bfvm_get_density",
+            "bfvm_set_cells", "bfvm_step", "bfvm_sync", "bfvm_record", "bfvm_backward",
+            "bfvm_last_error", "bfvm_status_string", "bfvm_get_info", "bfvm_set_option",
+            "bfvm_batch_create", "bfvm_batch_step", "bfvm_batch_sync", "bfvm_batch_destroy",
+            "bfvm_batch_last_error"]
+
+
+class BfvmError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lock = threading.Lock()
+_lib = None
+
+_vp = ctypes.c_void_p
+_dp = ctypes.POINTER(ctypes.c_double)
+_i32 = ctypes.c_int32
+_i64 = ctypes.c_int64
+
+
+def load_library(path: Optional[str] = None):
+    """Load libbfvm.so (built by paper_2110_13368_gb300.build)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise RuntimeError(f"libbfvm is not built ({p} missing); run "
+                               "paper_2110_13368_gb300.build.build() first")
+        lib = ctypes.CDLL(p)
+        lib.bfvm_create.argtypes = [ctypes.POINTER(_vp), _i32, _i32, _i32, ctypes.c_double,
+                                    ctypes.c_double, _i32, _dp, _dp,
+                                    ctypes.POINTER(_i32), _dp, _i32, _vp]
+        lib.bfvm_destroy.argtypes = [_vp]
+        lib.bfvm_destroy.restype = None
+        lib.bfvm_set_density.argtypes = [_vp, _vp, _i32]
+        lib.bfvm_get_density.argtypes = [_vp, _vp, _i32]
+        lib.bfvm_set_cells.argtypes = [_vp, _i64, _vp, _vp, _vp, _vp, _vp, _i32]
+        lib.bfvm_step.argtypes = [_vp, _i32]
+        lib.bfvm_sync.argtypes = [_vp]
+        lib.bfvm_record.argtypes = [_vp, _i32]
+        lib.bfvm_backward.argtypes = [_vp, _vp, _i32, _vp, _vp, _vp, _vp, _vp, _i32]
+        lib.bfvm_last_error.argtypes = [_vp]
+        lib.bfvm_last_error.restype = ctypes.c_char_p
+        lib.bfvm_status_string.argtypes = [_i32]
+        lib.bfvm_status_string.restype = ctypes.c_char_p
+        lib.bfvm_get_info.argtypes = [_vp, ctypes.POINTER(_i64)]
+        lib.bfvm_set_option.argtypes = [_vp, _i32, _i64]
+        lib.bfvm_batch_create.argtypes = [ctypes.POINTER(_vp), ctypes.POINTER(_vp), _i32, _vp]
+        lib.bfvm_batch_step.argtypes = [_vp, _i32]
+        lib.bfvm_batch_sync.argtypes = [_vp]
+        lib.bfvm_batch_destroy.argtypes = [_vp]
+        lib.bfvm_batch_destroy.restype = None
+        lib.bfvm_batch_last_error.argtypes = [_vp]
+        lib.bfvm_batch_last_error.restype = ctypes.c_char_p
+        for name in ("bfvm_create", "bfvm_set_density", "bfvm_get_density", "bfvm_set_cells",
+                     "bfvm_step", "bfvm_sync", "bfvm_record", "bfvm_backward", "bfvm_get_info",
+                     "bfvm_set_option", "bfvm_batch_create", "bfvm_batch_step",
+                     "bfvm_batch_sync"):
+            getattr(lib, name).restype = ctypes.c_int
+        _lib = lib
+        return lib
+
+
+def _check(status: int, handle=None, batch=False):
+    if status != BFVM_OK:
+        lib = load_library()
+        if batch:
+            msg = lib.bfvm_batch_last_error(handle)
+        else:
+            msg = lib.bfvm_last_error(handle)
+        raise BfvmError(status, (msg or b"").decode())
+
+
+def _f64(a, n=None):
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+    if n is not None and a.size != n:
+        raise ValueError(f"expected {n} values, got {a.size}")
+    return a
+
+
+def _ptr(buf):
+    """(pointer, on_device, keepalive) for a torch tensor or numpy array."""
+    try:
+        import torch
+        if isinstance(buf, torch.Tensor):
+            if not buf.is_contiguous():
+                raise ValueError("tensor must be contiguous")
+            return ctypes.c_void_p(buf.data_ptr()), int(buf.is_cuda), buf
+    except ImportError:  # pragma: no cover
+        pass
+    arr = np.ascontiguousarray(buf)
+    return ctypes.c_void_p(arr.ctypes.data), 0, arr
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+# ------------------------------------------------------------------ C names
+def bfvm_create(nx, ny, nz, dx_um, dt_min, D, lam, bc_kind, bc_value, precision=64,
+                stream=None):
+    lib = load_library()
+    n_sub = len(D)
+    D = _f64(D, n_sub)
+    lam = _f64(lam, n_sub)
+    kind = np.ascontiguousarray(np.asarray(bc_kind, dtype=np.int32))
+    val = _f64(bc_value, n_sub)
+    if kind.size != n_sub:
+        raise ValueError("bc_kind length")
+    h = _vp()
+    st = lib.bfvm_create(ctypes.byref(h), int(nx), int(ny), int(nz), float(dx_um),
+                         float(dt_min), n_sub, D.ctypes.data_as(_dp), lam.ctypes.data_as(_dp),
+                         kind.ctypes.data_as(ctypes.POINTER(_i32)), val.ctypes.data_as(_dp),
+                         int(precision), _stream_handle(stream))
+    _check(st, None)
+    return h
+
+
+def bfvm_destroy(h):
+    load_library().bfvm_destroy(h)
+
+
+def bfvm_set_density(h, rho):
+    p, dev, keep = _ptr(rho)
+    _check(load_library().bfvm_set_density(h, p, dev), h)
+    del keep
+
+
+def bfvm_get_density(h, out):
+    p, dev, keep = _ptr(out)
+    _check(load_library().bfvm_get_density(h, p, dev), h)
+    return out
+
+
+def bfvm_set_cells(h, pos, vol, S, U, rho_star):
+    n = 0 if pos is None else int(np.shape(pos)[0])
+    if n == 0:
+        _check(load_library().bfvm_set_cells(h, 0, None, None, None, None, None, 0), h)
+        return
+    ps = [_ptr(a) for a in (pos, vol, S, U, rho_star)]
+    devs = {d for _, d, _ in ps}
+    if len(devs) != 1:
+        raise ValueError("cell arrays must all be on the host or all on the device")
+    _check(load_library().bfvm_set_cells(h, n, *[p for p, _, _ in ps], devs.pop()), h)
+    del ps
+
+
+def bfvm_step(h, n_steps):
+    _check(load_library().bfvm_step(h, int(n_steps)), h)
+
+
+def bfvm_sync(h):
+    _check(load_library().bfvm_sync(h), h)
+
+
+def bfvm_record(h, checkpoint_every):
+    _check(load_library().bfvm_record(h, int(checkpoint_every)), h)
+
+
+def bfvm_backward(h, g_final, checkpoint_every, dD, dlambda, dS, dU, g0=None):
+    ptrs = [_ptr(a) for a in (g_final, dD, dlambda)]
+    dev = ptrs[0][1]
+    extra = [_ptr(a) if a is not None else (None, dev, None) for a in (dS, dU, g0)]
+    for _, d, _ in ptrs + extra:
+        if d != dev:
+            raise ValueError("all gradient buffers must be on the same side (host or device)")
+    _check(load_library().bfvm_backward(h, ptrs[0][0], int(checkpoint_every), ptrs[1][0],
+                                        ptrs[2][0], extra[0][0], extra[1][0], extra[2][0], dev), h)
+    del ptrs, extra
+
+
+def bfvm_get_info(h):
+    info = (_i64 * 16)()
+    _check(load_library().bfvm_get_info(h, info), h)
+    keys = ["precision", "nx", "ny", "nz", "n_sub", "pitch", "n_source_voxels",
+            "steps_taken", "variant", "period", "launches", "recorded_steps"]
+    return {k: int(info[i]) for i, k in enumerate(keys)}
+
+
+def bfvm_set_option(h, key, value):
+    _check(load_library().bfvm_set_option(h, int(key), int(value)), h)
+
+
+def bfvm_status_string(status):
+    return load_library().bfvm_status_string(int(status)).decode()
+
+
+def bfvm_last_error(h=None):
+    return (load_library().bfvm_last_error(h) or b"").decode()
+
+
+def bfvm_batch_create(handles, stream=None):
+    lib = load_library()
+    arr = (_vp * len(handles))(*[h.value if isinstance(h, _vp) else h for h in handles])
+    b = _vp()
+    st = lib.bfvm_batch_create(ctypes.byref(b), arr, len(handles), _stream_handle(stream))
+    if st != BFVM_OK:
+        raise BfvmError(st, "bfvm_batch_create failed: " + bfvm_last_error(None))
+    return b
+
+
+def bfvm_batch_step(b, n_steps):
+    _check(load_library().bfvm_batch_step(b, int(n_steps)), b, batch=True)
+
+
+def bfvm_batch_sync(b):
+    _check(load_library().bfvm_batch_sync(b), b, batch=True)
+
+
+def bfvm_batch_destroy(b):
+    load_library().bfvm_batch_destroy(b)
+
+
+# ---------------------------------------------------------- convenience
+class Sim:
+    """One simulation context with torch-owned buffers.
+
+    ``Sim.from_problem(p)`` creates the context for a Problem of
+    ``paper_2110_13368_gb300.inputs`` and uploads its field and cells.
+    """
+
+    def __init__(self, nx, ny, nz, dx, dt, D, lam, bc_kind, bc_value, precision=64,
+                 stream=None, device=None):
+        import torch
+        self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else device
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.shape = (len(D), nz, ny, nx)
+        self.precision = int(precision)
+        self.dtype = torch.float64 if precision == 64 else torch.float32
+        self.n_cells = 0
+        self.handle = bfvm_create(nx, ny, nz, dx, dt, D, lam, bc_kind, bc_value, precision,
+                                  self.stream)
+
+    @classmethod
+    def from_problem(cls, p, precision=None, stream=None, cells_on_device=True):
+        import torch
+        prec = p.precision if precision is None else precision
+        s = cls(p.nx, p.ny, p.nz, p.dx, p.dt, p.D, p.lam, p.bc_kind, p.bc_value, prec, stream)
+        s.set_density(torch.as_tensor(p.rho0, dtype=s.dtype, device=s.device))
+        if p.n_cells:
+            arrs = [p.pos, p.vol, p.S, p.U, p.rho_star]
+            if cells_on_device:
+                arrs = [torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64,
+                                        device=s.device) for a in arrs]
+            s.set_cells(*arrs)
+        return s
+
+    def set_density(self, rho):
+        bfvm_set_density(self.handle, rho)
+
+    def get_density(self, out=None):
+        import torch
+        if out is None:
+            out = torch.empty(self.shape, dtype=self.dtype, device=self.device)
+        bfvm_get_density(self.handle, out)
+        return out
+
+    def set_cells(self, pos, vol, S, U, rho_star):
+        bfvm_set_cells(self.handle, pos, vol, S, U, rho_star)
+        self.n_cells = 0 if pos is None else int(pos.shape[0])
+
+    def step(self, n=1):
+        bfvm_step(self.handle, n)
+
+    def sync(self):
+        bfvm_sync(self.handle)
+
+    def record(self, every):
+        bfvm_record(self.handle, every)
+
+    def backward(self, g_final, checkpoint_every=0, want_g0=False):
+        import torch
+        n_sub = self.shape[0]
+        dev = g_final.device
+        dD = torch.zeros(n_sub, dtype=torch.float64, device=dev)
+        dl = torch.zeros(n_sub, dtype=torch.float64, device=dev)
+        dS = torch.zeros((max(self.n_cells, 1), n_sub), dtype=torch.float64, device=dev)
+        dU = torch.zeros_like(dS)
+        g0 = torch.zeros(self.shape, dtype=torch.float64, device=dev) if want_g0 else None
+        bfvm_backward(self.handle, g_final.contiguous(), checkpoint_every, dD, dl, dS, dU, g0)
+        out = {"dD": dD, "dlambda": dl, "dS": dS[: self.n_cells], "dU": dU[: self.n_cells]}
+        if want_g0:
+            out["g0"] = g0
+        return out
+
+    def info(self):
+        return bfvm_get_info(self.handle)
+
+    def set_option(self, key, value):
+        bfvm_set_option(self.handle, key, value)
+
+    def close(self):
+        if getattr(self, "handle", None) is not None:
+            bfvm_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

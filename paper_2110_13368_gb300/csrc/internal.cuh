@@ -1,0 +1,151 @@
+// Internal declarations shared by the CUDA translation units of libbfvm.
+// Nothing here is part of the C ABI (see include/bfvm.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "bfvm.h"
+
+namespace bfvm {
+
+// ---------------------------------------------------------------- tables
+// Per substrate s and axis a (0 = x, 1 = y, 2 = z), the line matrix of that
+// axis has diagonal b_i = 1 + ell + c (ends) / 1 + ell + 2c (inside), off
+// diagonals -c, c = D dt / dx^2, ell = lambda dt / 3 (a line of length 1 has
+// only 1 + ell).  Thomas elimination gives pivots den_0 = b_0,
+// den_i = b_i - c^2 / den_{i-1}.  Tables are laid out [s][axis offset + i],
+// axis offsets 0, nx, nx + ny, row length L = nx + ny + nz.
+struct CoefTables {
+    double* r = nullptr;    // 1 / den_i
+    double* cr = nullptr;   // c / den_i
+    double* c = nullptr;    // [n_sub * 3] c per substrate and axis
+    float* r32 = nullptr;   // the same rounded to FP32
+    float* cr32 = nullptr;
+    float* c32 = nullptr;
+    // rescaled-Thomas tables (FP64 only), one set per rescale state p:
+    // [p][s][axis offset + i]
+    double* fa = nullptr;   // forward coefficient of state p
+    double* fb = nullptr;   // backward coefficient of state p
+    double* sc = nullptr;   // [p + 1] axis scale vector entering state p
+    double* isc = nullptr;  // 1 / sc
+    int period = 0;         // number of states p
+    int64_t L = 0;
+};
+
+// Binned cells: every voxel that holds at least one cell, with its cells'
+// affine maps composed in index order.  entry e: field element offset (in
+// elements, pitch layout) and rho <- alpha rho + beta.
+struct SourceTable {
+    int64_t n_entries = 0;
+    int64_t* off = nullptr;
+    double* alpha = nullptr;
+    double* beta = nullptr;
+    int32_t* vox = nullptr;     // voxel (x, y, z) packed as x + nx (y + ny z)
+    int32_t* sub = nullptr;     // substrate of the entry
+    // for the adjoint: cells sorted by (voxel, index)
+    int64_t n_cells = 0;
+    int64_t n_seg = 0;          // number of occupied voxels
+    int64_t* seg_start = nullptr;   // [n_seg + 1] into the sorted cell list
+    int64_t* seg_vox = nullptr;     // [n_seg] voxel linear index (x fastest)
+    int64_t* cell_sorted = nullptr; // [n_cells] original index, sorted order
+    double* ca = nullptr;       // [n_cells][n_sub] a = w S rho*, sorted order
+    double* cb = nullptr;       // [n_cells][n_sub] b = w (S + U)
+    double* cw = nullptr;       // [n_cells] w = dt V / V_vox
+    double* crs = nullptr;      // [n_cells][n_sub] rho*
+    int64_t* seg_of_entry = nullptr;  // [n_entries] segment of each entry
+};
+
+struct Ctx {
+    int nx = 0, ny = 0, nz = 0, n_sub = 0, precision = 64;
+    int64_t pitch = 0;            // row length in elements (>= nx, multiple of 4)
+    int64_t n_field = 0;          // n_sub * nz * ny * pitch
+    double dx = 0, dt = 0;
+    std::vector<double> D, lambda, bc_value;
+    std::vector<int32_t> bc_kind;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    int sm_count = 0;
+    size_t smem_optin = 0;
+
+    void* field = nullptr;        // T[n_field]
+    int32_t* d_bc_kind = nullptr;
+    double* d_bc_value = nullptr;
+    float* d_bc_value32 = nullptr;
+    int* d_err = nullptr;         // device error flags
+    CoefTables coef;
+    SourceTable src;
+
+    int variant = 0;              // 0 plain, 1 rescaled
+    int period_override = 0;
+    int fuse_sources = 0;
+    int use_graphs = 1;
+    int scale_state = 0;          // rescale state p of the stored field
+
+    cudaGraphExec_t period_graph = nullptr;
+    int period_graph_len = 0;
+
+    // recording for the adjoint
+    int record_every = 0;
+    std::vector<void*> checkpoints;
+    int recorded_steps = 0;
+    bool recorded = false;
+
+    int64_t steps_taken = 0;
+    int64_t launches = 0;
+    std::string err;
+};
+
+// ------------------------------------------------------------ helpers
+bfvm_status set_err(Ctx* c, bfvm_status st, const std::string& msg);
+bfvm_status cuda_err(Ctx* c, cudaError_t e, const char* what);
+
+#define BFVM_CUDA(ctx, call)                                  \
+    do {                                                      \
+        cudaError_t e_ = (call);                              \
+        if (e_ != cudaSuccess) return cuda_err(ctx, e_, #call); \
+    } while (0)
+
+// coefficient tables (coeffs.cu)
+bfvm_status build_coefficients(Ctx* c);
+void free_coefficients(Ctx* c);
+
+// sweeps (sweeps.cu): one full step in the plain or rescaled form
+bfvm_status launch_step(Ctx* c, int p, bool renorm);
+bfvm_status launch_unscale_copy(Ctx* c, void* out_dev, int p);
+int sweep_kernel_count_per_step(const Ctx* c);
+
+// sources (sources.cu)
+bfvm_status build_sources(Ctx* c, int64_t n_cells, const double* pos,
+                          const double* vol, const double* S, const double* U,
+                          const double* rho_star);
+void free_sources(Ctx* c);
+bfvm_status launch_sources(Ctx* c, int p_next, bool renormed);
+
+// adjoint (adjoint.cu)
+bfvm_status run_backward(Ctx* c, const double* g_final_dev, double* dD_dev,
+                         double* dl_dev, double* dS_dev, double* dU_dev,
+                         double* g0_dev);
+
+// layout conversion between the caller's dense [s][z][y][x] and the pitched
+// field (layout.cu)
+bfvm_status copy_in_dense(Ctx* c, const void* src, bool on_device);
+bfvm_status copy_out_dense(Ctx* c, void* dst, bool on_device);
+
+inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+}  // namespace bfvm
+
+struct bfvm_ctx {
+    bfvm::Ctx impl;
+};
+
+namespace bfvm {
+// plain FP64 sweep along one axis, in -> out (sweeps.cu); dir_mode 0 step,
+// 1 raw replay, 2 adjoint
+bfvm_status launch_sweep_plain64(Ctx* c, int axis, const double* in, double* out,
+                                 int dir_mode);
+}  // namespace bfvm

@@ -1,0 +1,353 @@
+// Cell sources and sinks: binning cells to voxels, ordering them by
+// (voxel, cell index), and composing each voxel's cells into one affine map.
+//
+// The delta term of Eq. 1 applied implicitly per cell i in index order is
+//   rho_v <- (rho_v + a_i) / (1 + b_i),  a_i = w_i S_i rho*_i,
+//   b_i = w_i (S_i + U_i),  w_i = dt V_i / V_vox,  V_vox = dx^3.
+// Maps of one voxel do not commute, so the cells of a voxel are kept in
+// ascending index: the sort key is (voxel << 31) | index, unique per cell, so
+// any correct sort gives that order.  The composition of the maps in that
+// order is rho <- alpha rho + beta with, cell after cell,
+//   alpha <- alpha / (1 + b_i),  beta <- (beta + a_i) / (1 + b_i),
+// computed once here in FP64 (the paper kept this step on the host, see
+// "Future Work"; here it stays on the device).
+#include <math.h>
+
+#include <algorithm>
+
+#include "internal.cuh"
+
+namespace bfvm {
+
+namespace {
+
+constexpr uint64_t kIdxBits = 31;
+constexpr uint64_t kIdxMask = (1ull << kIdxBits) - 1;
+
+__global__ void k_validate_cells(int64_t n, int n_sub, const double* pos,
+                                 const double* vol, const double* S,
+                                 const double* U, const double* rs, double lx,
+                                 double ly, double lz, int* flag)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int bad = 0;
+    double px = pos[3 * i], py = pos[3 * i + 1], pz = pos[3 * i + 2];
+    if (!(px >= 0.0 && px <= lx) || !(py >= 0.0 && py <= ly) || !(pz >= 0.0 && pz <= lz))
+        bad |= 1;
+    double v = vol[i];
+    if (!(v > 0.0) || !isfinite(v)) bad |= 2;
+    for (int s = 0; s < n_sub; ++s) {
+        double a = S[i * n_sub + s], b = U[i * n_sub + s], c = rs[i * n_sub + s];
+        if (!(a >= 0.0) || !isfinite(a) || !(b >= 0.0) || !isfinite(b)) bad |= 4;
+        if (!isfinite(c)) bad |= 8;
+    }
+    if (bad) atomicOr(flag, bad);
+}
+
+__global__ void k_keys(int64_t n, int64_t n_pad, const double* pos, double dx,
+                       int nx, int ny, int nz, uint64_t* keys)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n_pad) return;
+    if (i >= n) {
+        keys[i] = ~0ull;
+        return;
+    }
+    int ext[3] = {nx, ny, nz};
+    int64_t v[3];
+    for (int a = 0; a < 3; ++a) {
+        double q = floor(pos[3 * i + a] / dx);
+        int64_t qi = (int64_t)q;
+        if (qi > ext[a] - 1) qi = ext[a] - 1;
+        if (qi < 0) qi = 0;
+        v[a] = qi;
+    }
+    uint64_t vox = (uint64_t)((v[2] * ny + v[1]) * (int64_t)nx + v[0]);
+    keys[i] = (vox << kIdxBits) | (uint64_t)i;
+}
+
+// Bitonic sort of a power-of-two array: global passes for large strides,
+// shared-memory passes once the stride fits a block of 2048 keys.
+__global__ void k_bitonic_global(uint64_t* a, int64_t n, int64_t size, int64_t stride)
+{
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= n / 2) return;
+    int64_t i = (t / stride) * 2 * stride + (t % stride);
+    int64_t j = i + stride;
+    bool up = (i & size) == 0;
+    uint64_t x = a[i], y = a[j];
+    if ((x > y) == up) {
+        a[i] = y;
+        a[j] = x;
+    }
+}
+
+constexpr int kSortBlock = 2048;
+
+// Within each block of 2048 keys: for sizes from size_lo to size_hi, strides
+// down to 1 (size_lo == size_hi: only the strides < 2048 of that size).
+__global__ void k_bitonic_shared(uint64_t* a, int64_t size_lo, int64_t size_hi)
+{
+    __shared__ uint64_t s[kSortBlock];
+    int64_t base = (int64_t)blockIdx.x * kSortBlock;
+    for (int k = threadIdx.x; k < kSortBlock; k += blockDim.x) s[k] = a[base + k];
+    __syncthreads();
+    for (int64_t size = size_lo; size <= size_hi; size *= 2) {
+        int64_t st0 = size / 2;
+        if (st0 >= kSortBlock) st0 = kSortBlock / 2;
+        for (int64_t stride = st0; stride >= 1; stride /= 2) {
+            for (int t = threadIdx.x; t < kSortBlock / 2; t += blockDim.x) {
+                int i = (int)((t / stride) * 2 * stride + (t % stride));
+                int j = i + (int)stride;
+                bool up = ((base + i) & size) == 0;
+                uint64_t x = s[i], y = s[j];
+                if ((x > y) == up) {
+                    s[i] = y;
+                    s[j] = x;
+                }
+            }
+            __syncthreads();
+        }
+    }
+    for (int k = threadIdx.x; k < kSortBlock; k += blockDim.x) a[base + k] = s[k];
+}
+
+__global__ void k_heads(int64_t n, const uint64_t* keys, int64_t* flag)
+{
+    int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    flag[j] = (j == 0 || (keys[j] >> kIdxBits) != (keys[j - 1] >> kIdxBits)) ? 1 : 0;
+}
+
+// exclusive scan, 1024 elements per block
+constexpr int kScanBlock = 1024;
+__global__ void k_scan_block(const int64_t* in, int64_t* out, int64_t* sums, int64_t n)
+{
+    __shared__ int64_t s[kScanBlock];
+    int64_t base = (int64_t)blockIdx.x * kScanBlock;
+    for (int k = threadIdx.x; k < kScanBlock; k += blockDim.x)
+        s[k] = (base + k < n) ? in[base + k] : 0;
+    __syncthreads();
+    // Hillis-Steele inclusive scan
+    for (int d = 1; d < kScanBlock; d *= 2) {
+        int64_t vals[kScanBlock / 256];
+        int c = 0;
+        for (int k = threadIdx.x; k < kScanBlock; k += blockDim.x, ++c)
+            vals[c] = (k >= d) ? s[k - d] : 0;
+        __syncthreads();
+        c = 0;
+        for (int k = threadIdx.x; k < kScanBlock; k += blockDim.x, ++c) s[k] += vals[c];
+        __syncthreads();
+    }
+    for (int k = threadIdx.x; k < kScanBlock; k += blockDim.x)
+        if (base + k < n) out[base + k] = (k == 0 ? 0 : s[k - 1]);
+    if (threadIdx.x == 0) sums[blockIdx.x] = s[kScanBlock - 1];
+}
+
+__global__ void k_scan_add(int64_t* out, const int64_t* offs, int64_t n)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) out[i] += offs[i / kScanBlock];
+}
+
+__global__ void k_segments(int64_t n, const uint64_t* keys, const int64_t* flag,
+                           const int64_t* seg_id, int64_t* seg_start, int64_t* seg_vox,
+                           int64_t* cell_sorted)
+{
+    int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    cell_sorted[j] = (int64_t)(keys[j] & kIdxMask);
+    if (flag[j]) {
+        int64_t g = seg_id[j];
+        seg_start[g] = j;
+        seg_vox[g] = (int64_t)(keys[j] >> kIdxBits);
+    }
+}
+
+__global__ void k_cell_terms(int64_t n, int n_sub, double dt, double vvox,
+                             const int64_t* cell_sorted, const double* vol,
+                             const double* S, const double* U, const double* rs,
+                             double* ca, double* cb, double* cw, double* crs)
+{
+    int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    int64_t i = cell_sorted[j];
+    double w = dt * (vol[i] / vvox);
+    cw[j] = w;
+    for (int s = 0; s < n_sub; ++s) {
+        double Si = S[i * n_sub + s], Ui = U[i * n_sub + s], ri = rs[i * n_sub + s];
+        ca[j * n_sub + s] = w * Si * ri;
+        cb[j * n_sub + s] = w * (Si + Ui);
+        crs[j * n_sub + s] = ri;
+    }
+}
+
+__global__ void k_compose(int64_t n_seg, int n_sub, int nx, int ny, int nz,
+                          int64_t pitch, const int64_t* seg_start,
+                          const int64_t* seg_vox, const double* ca,
+                          const double* cb, int64_t* off, double* alpha,
+                          double* beta, int32_t* vox, int32_t* sub,
+                          int64_t* seg_of_entry)
+{
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= n_seg * n_sub) return;
+    int64_t g = e / n_sub;
+    int s = (int)(e % n_sub);
+    double al = 1.0, be = 0.0;
+    for (int64_t j = seg_start[g]; j < seg_start[g + 1]; ++j) {
+        double m = 1.0 / (1.0 + cb[j * n_sub + s]);
+        al = al * m;
+        be = (be + ca[j * n_sub + s]) * m;
+    }
+    int64_t v = seg_vox[g];
+    int x = (int)(v % nx);
+    int y = (int)((v / nx) % ny);
+    int z = (int)(v / ((int64_t)nx * ny));
+    off[e] = (((int64_t)s * nz + z) * ny + y) * pitch + x;
+    alpha[e] = al;
+    beta[e] = be;
+    vox[e] = (int32_t)v;
+    sub[e] = s;
+    seg_of_entry[e] = g;
+}
+
+bfvm_status scan_exclusive(Ctx* c, const int64_t* in, int64_t* out, int64_t n,
+                           int64_t* total_host)
+{
+    int64_t nb = ceil_div(n, kScanBlock);
+    int64_t* sums = nullptr;
+    int64_t* sums_scan = nullptr;
+    BFVM_CUDA(c, cudaMalloc(&sums, sizeof(int64_t) * (nb + 1)));
+    BFVM_CUDA(c, cudaMalloc(&sums_scan, sizeof(int64_t) * (nb + 1)));
+    k_scan_block<<<(unsigned)nb, 256, 0, c->stream>>>(in, out, sums, n);
+    c->launches += 1;
+    bfvm_status st = BFVM_OK;
+    if (nb > 1) {
+        int64_t dummy = 0;
+        st = scan_exclusive(c, sums, sums_scan, nb, &dummy);
+        if (st == BFVM_OK) {
+            k_scan_add<<<(unsigned)ceil_div(n, 256), 256, 0, c->stream>>>(out, sums_scan, n);
+            c->launches += 1;
+        }
+    }
+    if (st == BFVM_OK && total_host) {
+        int64_t last_in = 0, last_out = 0;
+        cudaMemcpyAsync(&last_in, in + n - 1, sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream);
+        cudaMemcpyAsync(&last_out, out + n - 1, sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream);
+        cudaError_t e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) st = cuda_err(c, e, "scan total");
+        *total_host = last_in + last_out;
+    }
+    cudaFree(sums);
+    cudaFree(sums_scan);
+    return st;
+}
+
+bfvm_status sort_keys(Ctx* c, uint64_t* keys, int64_t n_pad)
+{
+    // n_pad is a power of two >= kSortBlock
+    unsigned blocks = (unsigned)(n_pad / kSortBlock);
+    k_bitonic_shared<<<blocks, 512, 0, c->stream>>>(keys, 2, kSortBlock);
+    c->launches += 1;
+    for (int64_t size = 2 * kSortBlock; size <= n_pad; size *= 2) {
+        for (int64_t stride = size / 2; stride >= kSortBlock; stride /= 2) {
+            k_bitonic_global<<<(unsigned)ceil_div(n_pad / 2, 256), 256, 0, c->stream>>>(
+                keys, n_pad, size, stride);
+            c->launches += 1;
+        }
+        k_bitonic_shared<<<blocks, 512, 0, c->stream>>>(keys, size, size);
+        c->launches += 1;
+    }
+    BFVM_CUDA(c, cudaGetLastError());
+    return BFVM_OK;
+}
+
+}  // namespace
+
+void free_sources(Ctx* c)
+{
+    SourceTable& S = c->src;
+    void* ptrs[] = {S.off, S.alpha, S.beta, S.vox, S.sub, S.seg_start, S.seg_vox,
+                    S.cell_sorted, S.ca, S.cb, S.cw, S.crs, S.seg_of_entry};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    S = SourceTable();
+}
+
+// pos, vol, S, U, rho_star are device pointers here.
+bfvm_status build_sources(Ctx* c, int64_t n, const double* pos, const double* vol,
+                          const double* Sr, const double* Ur, const double* rs)
+{
+    free_sources(c);
+    if (n == 0) return BFVM_OK;
+    if (n > (int64_t)kIdxMask)
+        return set_err(c, BFVM_EINVAL, "too many cells (limit 2^31 - 1)");
+    const int n_sub = c->n_sub;
+    BFVM_CUDA(c, cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
+    k_validate_cells<<<(unsigned)ceil_div(n, 256), 256, 0, c->stream>>>(
+        n, n_sub, pos, vol, Sr, Ur, rs, c->nx * c->dx, c->ny * c->dx, c->nz * c->dx, c->d_err);
+    c->launches += 1;
+    int flag = 0;
+    BFVM_CUDA(c, cudaMemcpyAsync(&flag, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    BFVM_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (flag & 1) return set_err(c, BFVM_EINVAL, "cell position outside [0, n*dx] on some axis");
+    if (flag & 2) return set_err(c, BFVM_EINVAL, "cell volume must be finite and > 0");
+    if (flag & 4) return set_err(c, BFVM_EINVAL, "secretion/uptake rates must be finite and >= 0");
+    if (flag & 8) return set_err(c, BFVM_EINVAL, "rho_star must be finite");
+
+    int64_t n_pad = kSortBlock;
+    while (n_pad < n) n_pad *= 2;
+    uint64_t* keys = nullptr;
+    int64_t *flags = nullptr, *seg_id = nullptr;
+    BFVM_CUDA(c, cudaMalloc(&keys, sizeof(uint64_t) * n_pad));
+    BFVM_CUDA(c, cudaMalloc(&flags, sizeof(int64_t) * n));
+    BFVM_CUDA(c, cudaMalloc(&seg_id, sizeof(int64_t) * n));
+    k_keys<<<(unsigned)ceil_div(n_pad, 256), 256, 0, c->stream>>>(
+        n, n_pad, pos, c->dx, c->nx, c->ny, c->nz, keys);
+    c->launches += 1;
+    bfvm_status st = sort_keys(c, keys, n_pad);
+    if (st != BFVM_OK) return st;
+    k_heads<<<(unsigned)ceil_div(n, 256), 256, 0, c->stream>>>(n, keys, flags);
+    c->launches += 1;
+    int64_t n_seg = 0;
+    st = scan_exclusive(c, flags, seg_id, n, &n_seg);
+    if (st != BFVM_OK) return st;
+
+    SourceTable& S = c->src;
+    S.n_cells = n;
+    S.n_seg = n_seg;
+    S.n_entries = n_seg * n_sub;
+    BFVM_CUDA(c, cudaMalloc(&S.seg_start, sizeof(int64_t) * (n_seg + 1)));
+    BFVM_CUDA(c, cudaMalloc(&S.seg_vox, sizeof(int64_t) * n_seg));
+    BFVM_CUDA(c, cudaMalloc(&S.cell_sorted, sizeof(int64_t) * n));
+    BFVM_CUDA(c, cudaMalloc(&S.ca, sizeof(double) * n * n_sub));
+    BFVM_CUDA(c, cudaMalloc(&S.cb, sizeof(double) * n * n_sub));
+    BFVM_CUDA(c, cudaMalloc(&S.crs, sizeof(double) * n * n_sub));
+    BFVM_CUDA(c, cudaMalloc(&S.cw, sizeof(double) * n));
+    BFVM_CUDA(c, cudaMalloc(&S.off, sizeof(int64_t) * S.n_entries));
+    BFVM_CUDA(c, cudaMalloc(&S.alpha, sizeof(double) * S.n_entries));
+    BFVM_CUDA(c, cudaMalloc(&S.beta, sizeof(double) * S.n_entries));
+    BFVM_CUDA(c, cudaMalloc(&S.vox, sizeof(int32_t) * S.n_entries));
+    BFVM_CUDA(c, cudaMalloc(&S.sub, sizeof(int32_t) * S.n_entries));
+    BFVM_CUDA(c, cudaMalloc(&S.seg_of_entry, sizeof(int64_t) * S.n_entries));
+    BFVM_CUDA(c, cudaMemcpyAsync(S.seg_start + n_seg, &n, sizeof(int64_t),
+                                 cudaMemcpyHostToDevice, c->stream));
+    k_segments<<<(unsigned)ceil_div(n, 256), 256, 0, c->stream>>>(
+        n, keys, flags, seg_id, S.seg_start, S.seg_vox, S.cell_sorted);
+    k_cell_terms<<<(unsigned)ceil_div(n, 256), 256, 0, c->stream>>>(
+        n, n_sub, c->dt, c->dx * c->dx * c->dx, S.cell_sorted, vol, Sr, Ur, rs,
+        S.ca, S.cb, S.cw, S.crs);
+    k_compose<<<(unsigned)ceil_div(S.n_entries, 128), 128, 0, c->stream>>>(
+        n_seg, n_sub, c->nx, c->ny, c->nz, c->pitch, S.seg_start, S.seg_vox, S.ca,
+        S.cb, S.off, S.alpha, S.beta, S.vox, S.sub, S.seg_of_entry);
+    c->launches += 3;
+    BFVM_CUDA(c, cudaGetLastError());
+    BFVM_CUDA(c, cudaStreamSynchronize(c->stream));
+    cudaFree(keys);
+    cudaFree(flags);
+    cudaFree(seg_id);
+    return BFVM_OK;
+}
+
+}  // namespace bfvm

@@ -1,0 +1,484 @@
+// LOD line sweeps (the x-, y- and z-diffusion of the paper's "Using OpenACC
+// programming model for PhysiCell", one implicit tridiagonal solve per line)
+// with the Dirichlet condition of "Elements of Parallelism" fused in.
+//
+// Work decomposition: one thread per line, one warp per 32 consecutive
+// lines of a flattened line index (substrate-major, then the two other
+// coordinates with x fastest for the y and z sweeps).  For the y and z
+// sweeps adjacent lanes therefore touch adjacent x, so every per-element
+// access of a warp is one coalesced row.  Each thread copies its whole line
+// into a private column of shared memory with cp.async before solving, so
+// the line is read from HBM once and written once; the forward elimination
+// runs in place in shared memory and the back substitution writes the
+// result straight to the field.
+//
+// Lines too long for shared memory fall back to keeping the forward
+// intermediates in the field itself (the field is overwritten in place).
+#include <math.h>
+
+#include "internal.cuh"
+
+namespace bfvm {
+
+namespace {
+
+constexpr int kGroups = 8;   // cp.async commit groups per line
+
+__device__ __forceinline__ void cp_async_elem(double* dst, const double* src)
+{
+    unsigned s = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_elem(float* dst, const float* src)
+{
+    unsigned s = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit()
+{
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait()
+{
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+// wait until at most `pending` of this thread's newest groups are in flight
+__device__ __forceinline__ void cp_async_wait_dyn(int pending)
+{
+    switch (pending) {
+        case 0: cp_async_wait<0>(); break;
+        case 1: cp_async_wait<1>(); break;
+        case 2: cp_async_wait<2>(); break;
+        case 3: cp_async_wait<3>(); break;
+        case 4: cp_async_wait<4>(); break;
+        case 5: cp_async_wait<5>(); break;
+        case 6: cp_async_wait<6>(); break;
+        default: cp_async_wait<7>(); break;
+    }
+}
+
+template <typename T>
+struct SweepArgs {
+    const T* in;           // field read (may equal out)
+    T* field;              // field written
+    int64_t pitch;
+    int nx, ny, nz, n_sub;
+    int n;                 // line length (extent of the swept axis)
+    int64_t n_lines;       // n_sub * (product of the two other extents)
+    int64_t L;             // coefficient row length nx + ny + nz
+    int axis_off;          // offset of this axis in a coefficient row
+    int off_x, off_y, off_z;
+    // plain form
+    const T* r;            // [s][L] 1/den
+    const T* cr;           // [s][L] c/den
+    const T* cvec;         // [s][3]
+    // rescaled form (FP64): state p tables
+    const double* fa;      // [s][L]
+    const double* fb;
+    const double* sc_p;    // [s][L] scales of state p
+    const double* sc_p1;   // [s][L] scales of state p + 1
+    const double* isc_p1;  // [s][L] inverses of state p + 1
+    const int32_t* bc_kind;
+    const double* bc_value;
+};
+
+// MODE 0: plain Thomas (3 flops per element: FMA + MUL forward, FMA back).
+// MODE 1: rescaled Thomas (one FMA forward, one FMA back).
+// MODE 2: rescaled, and the z sweep divides the accumulated scale out.
+// DIR 0: Dirichlet shell set before and after the solve (the step itself).
+// DIR 1: shell set before the solve only; the raw solution is kept (the
+//        replay of a step for the adjoint needs it).
+// DIR 2: shell of the input zeroed, raw solution kept (the adjoint solve:
+//        the Dirichlet projection's Jacobian is zero on the shell).
+template <typename T, int AXIS, int MODE, int DIR, bool SMEM>
+__global__ void __launch_bounds__(256) k_sweep(SweepArgs<T> A)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int64_t line = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (line >= A.n_lines) return;
+
+    const int n = A.n;
+    int s, ox, oy, oz;   // substrate and the two fixed coordinates (third = -1)
+    int64_t base, stride;
+    bool other_shell;
+    if (AXIS == 0) {
+        int64_t t = line;
+        oy = (int)(t % A.ny); t /= A.ny;
+        oz = (int)(t % A.nz); s = (int)(t / A.nz);
+        ox = -1;
+        base = (((int64_t)s * A.nz + oz) * A.ny + oy) * A.pitch;
+        stride = 1;
+        other_shell = (oy == 0 || oy == A.ny - 1 || oz == 0 || oz == A.nz - 1);
+    } else if (AXIS == 1) {
+        int64_t t = line;
+        ox = (int)(t % A.nx); t /= A.nx;
+        oz = (int)(t % A.nz); s = (int)(t / A.nz);
+        oy = -1;
+        base = (((int64_t)s * A.nz + oz) * A.ny) * A.pitch + ox;
+        stride = A.pitch;
+        other_shell = (ox == 0 || ox == A.nx - 1 || oz == 0 || oz == A.nz - 1);
+    } else {
+        int64_t t = line;
+        ox = (int)(t % A.nx); t /= A.nx;
+        oy = (int)(t % A.ny); s = (int)(t / A.ny);
+        oz = -1;
+        base = ((int64_t)s * A.nz * A.ny + oy) * A.pitch + ox;
+        stride = (int64_t)A.ny * A.pitch;
+        other_shell = (ox == 0 || ox == A.nx - 1 || oy == 0 || oy == A.ny - 1);
+    }
+    const bool dir = A.bc_kind[s] == BFVM_BC_DIRICHLET;
+    const double v = (DIR == 2) ? 0.0 : A.bc_value[s];
+    const T* fin = A.in + base;
+    T* f = A.field + base;
+    const int64_t row = (int64_t)s * A.L;
+
+    // Scale bookkeeping of the rescaled form.  At the sweep of AXIS in state
+    // p the axes before it are already in state p + 1, the others in p.
+    double kline = 1.0;      // Dirichlet value times the other axes' scales
+    double inv_other = 1.0;  // inverse of the other axes' scales (MODE 2)
+    const double* own_in = nullptr;
+    const double* own_out = nullptr;
+    if (MODE >= 1) {
+        own_in = A.sc_p + row + A.axis_off;
+        own_out = A.sc_p1 + row + A.axis_off;
+        if (AXIS == 0) {
+            kline = v * A.sc_p[row + A.off_y + oy] * A.sc_p[row + A.off_z + oz];
+        } else if (AXIS == 1) {
+            kline = v * A.sc_p1[row + A.off_x + ox] * A.sc_p[row + A.off_z + oz];
+        } else {
+            kline = v * A.sc_p1[row + A.off_x + ox] * A.sc_p1[row + A.off_y + oy];
+            if (MODE == 2)
+                inv_other = A.isc_p1[row + A.off_x + ox] * A.isc_p1[row + A.off_y + oy];
+        }
+    }
+
+    if (dir && other_shell && DIR != 1) {
+        // the whole line is on the Dirichlet shell: no solve, just the value
+        // (the adjoint's zeroed input solves to zero)
+        for (int k = 0; k < n; ++k) {
+            double val;
+            if (MODE == 0 || MODE == 2) val = v;
+            else val = kline * own_out[k];
+            f[k * stride] = (T)val;
+        }
+        return;
+    }
+
+    T* w;
+    int64_t wstride;
+    if (SMEM) {
+        w = reinterpret_cast<T*>(smem_raw) + (int64_t)warp * 32 * n + lane;
+        wstride = 32;
+        const int gs = (n + kGroups - 1) / kGroups;
+        for (int g = 0; g < kGroups; ++g) {
+            int k0 = g * gs, k1 = min(n, k0 + gs);
+            for (int k = k0; k < k1; ++k) cp_async_elem(w + k * 32, fin + k * stride);
+            cp_async_commit();
+        }
+    } else {
+        // forward intermediates kept in the output field itself
+        w = f;
+        wstride = stride;
+        if (A.in != A.field)
+            for (int k = 0; k < n; ++k) f[k * stride] = fin[k * stride];
+    }
+    // on a Dirichlet shell line every input element is the shell value
+    const bool all_in = dir && other_shell;
+
+    // Dirichlet prologue value of the two line ends
+    auto end_in = [&](int k) -> T {
+        if (MODE == 0) return (T)v;
+        return (T)(kline * own_in[k]);
+    };
+
+    // forward elimination (in place)
+    T prev = (T)0;
+    if (MODE == 0) {
+        const T c = A.cvec[s * 3 + AXIS];
+        const T* __restrict__ r = A.r + row + A.axis_off;
+        const int gs = (n + kGroups - 1) / kGroups;
+        for (int g = 0; g < kGroups; ++g) {
+            if (SMEM) cp_async_wait_dyn(kGroups - 1 - g);
+            int k0 = g * gs, k1 = min(n, k0 + gs);
+            for (int k = k0; k < k1; ++k) {
+                T d = w[k * wstride];
+                if (all_in || (dir && (k == 0 || k == n - 1))) d = end_in(k);
+                prev = fma(c, prev, d) * r[k];
+                w[k * wstride] = prev;
+            }
+        }
+    } else {
+        const double* __restrict__ fa = A.fa + row + A.axis_off;
+        const int gs = (n + kGroups - 1) / kGroups;
+        for (int g = 0; g < kGroups; ++g) {
+            if (SMEM) cp_async_wait_dyn(kGroups - 1 - g);
+            int k0 = g * gs, k1 = min(n, k0 + gs);
+            for (int k = k0; k < k1; ++k) {
+                T d = w[k * wstride];
+                if (all_in || (dir && (k == 0 || k == n - 1))) d = end_in(k);
+                prev = fma((T)fa[k], prev, d);
+                w[k * wstride] = prev;
+            }
+        }
+    }
+
+    // back substitution, result written to the field
+    auto emit = [&](int k, T x) {
+        T out;
+        if (DIR == 0 && dir && (k == 0 || k == n - 1)) {
+            if (MODE == 0 || MODE == 2) out = (T)v;
+            else out = (T)(kline * own_out[k]);
+        } else if (MODE == 2) {
+            out = (T)((x * A.isc_p1[row + A.axis_off + k]) * inv_other);
+        } else {
+            out = x;
+        }
+        f[k * stride] = out;
+    };
+    T x = prev;
+    emit(n - 1, x);
+    if (MODE == 0) {
+        const T* __restrict__ cr = A.cr + row + A.axis_off;
+        for (int k = n - 2; k >= 0; --k) {
+            x = fma(cr[k], x, w[k * wstride]);
+            emit(k, x);
+        }
+    } else {
+        const double* __restrict__ fb = A.fb + row + A.axis_off;
+        for (int k = n - 2; k >= 0; --k) {
+            x = fma((T)fb[k], x, w[k * wstride]);
+            emit(k, x);
+        }
+    }
+}
+
+// rho <- alpha rho + beta over the occupied voxels (cell sources and sinks,
+// the delta term of Eq. 1, with every voxel's cells composed in index order).
+// In the rescaled form the field carries the scale X(x) Y(y) Z(z) of the
+// current state, so beta is scaled alike.
+template <typename T, bool SCALED>
+__global__ void k_sources(T* __restrict__ field, int64_t n_entries,
+                          const int64_t* __restrict__ off,
+                          const double* __restrict__ alpha,
+                          const double* __restrict__ beta,
+                          const int32_t* __restrict__ vox,
+                          const int32_t* __restrict__ sub, int nx, int ny,
+                          int64_t L, int off_y, int off_z,
+                          const double* __restrict__ sc)
+{
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= n_entries) return;
+    int64_t o = off[e];
+    double b = beta[e];
+    if (SCALED) {
+        int32_t vv = vox[e];
+        int x = vv % nx;
+        int y = (vv / nx) % ny;
+        int z = vv / (nx * ny);
+        const double* t = sc + (int64_t)sub[e] * L;
+        b *= t[x] * t[off_y + y] * t[off_z + z];
+    }
+    double r = (double)field[o];
+    field[o] = (T)fma(alpha[e], r, b);
+}
+
+template <typename T>
+SweepArgs<T> make_args(Ctx* c, int axis, int p, const T* r, const T* cr,
+                       const T* cvec)
+{
+    SweepArgs<T> A{};
+    A.field = reinterpret_cast<T*>(c->field);
+    A.in = A.field;
+    A.pitch = c->pitch;
+    A.nx = c->nx; A.ny = c->ny; A.nz = c->nz; A.n_sub = c->n_sub;
+    int ext[3] = {c->nx, c->ny, c->nz};
+    A.n = ext[axis];
+    int64_t other = (int64_t)ext[0] * ext[1] * ext[2] / ext[axis];
+    A.n_lines = other * c->n_sub;
+    A.L = c->coef.L;
+    A.off_x = 0; A.off_y = c->nx; A.off_z = c->nx + c->ny;
+    A.axis_off = axis == 0 ? 0 : (axis == 1 ? A.off_y : A.off_z);
+    A.r = r; A.cr = cr; A.cvec = cvec;
+    if (c->coef.fa) {
+        int64_t per_state = (int64_t)c->n_sub * c->coef.L;
+        A.fa = c->coef.fa + (int64_t)p * per_state;
+        A.fb = c->coef.fb + (int64_t)p * per_state;
+        A.sc_p = c->coef.sc + (int64_t)p * per_state;
+        A.sc_p1 = c->coef.sc + (int64_t)(p + 1) * per_state;
+        A.isc_p1 = c->coef.isc + (int64_t)(p + 1) * per_state;
+    }
+    A.bc_kind = c->d_bc_kind;
+    A.bc_value = c->d_bc_value;
+    return A;
+}
+
+template <typename T, int AXIS, int MODE, int DIR = 0>
+bfvm_status launch_axis(Ctx* c, const SweepArgs<T>& A)
+{
+    size_t per_warp = (size_t)32 * A.n * sizeof(T);
+    int max_warps = sizeof(T) == 8 ? 4 : 8;
+    int warps = (int)((c->smem_optin) / per_warp);
+    if (warps > max_warps) warps = max_warps;
+    int64_t blocks;
+    if (warps >= 1) {
+        size_t smem = per_warp * warps;
+        auto kern = k_sweep<T, AXIS, MODE, DIR, true>;
+        BFVM_CUDA(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)smem));
+        int threads = 32 * warps;
+        blocks = ceil_div(A.n_lines, threads);
+        kern<<<(unsigned)blocks, threads, smem, c->stream>>>(A);
+    } else {
+        auto kern = k_sweep<T, AXIS, MODE, DIR, false>;
+        blocks = ceil_div(A.n_lines, 128);
+        kern<<<(unsigned)blocks, 128, 0, c->stream>>>(A);
+    }
+    c->launches += 1;
+    BFVM_CUDA(c, cudaGetLastError());
+    return BFVM_OK;
+}
+
+template <typename T, int MODE_Z>
+bfvm_status launch_xyz(Ctx* c, int p, const T* r, const T* cr, const T* cv)
+{
+    constexpr int M = MODE_Z == 0 ? 0 : 1;
+    bfvm_status st;
+    if ((st = launch_axis<T, 0, M>(c, make_args<T>(c, 0, p, r, cr, cv))) != BFVM_OK) return st;
+    if ((st = launch_axis<T, 1, M>(c, make_args<T>(c, 1, p, r, cr, cv))) != BFVM_OK) return st;
+    return launch_axis<T, 2, MODE_Z>(c, make_args<T>(c, 2, p, r, cr, cv));
+}
+
+}  // namespace
+
+// Plain FP64 sweep along one axis from `in` to `out` (pitched layout), with
+// Dirichlet mode dir_mode (see k_sweep).  Used by the adjoint.
+bfvm_status launch_sweep_plain64(Ctx* c, int axis, const double* in, double* out,
+                                 int dir_mode)
+{
+    SweepArgs<double> A = make_args<double>(c, axis, 0, c->coef.r, c->coef.cr, c->coef.c);
+    A.in = in;
+    A.field = out;
+    if (axis == 0) {
+        if (dir_mode == 1) return launch_axis<double, 0, 0, 1>(c, A);
+        if (dir_mode == 2) return launch_axis<double, 0, 0, 2>(c, A);
+        return launch_axis<double, 0, 0, 0>(c, A);
+    }
+    if (axis == 1) {
+        if (dir_mode == 1) return launch_axis<double, 1, 0, 1>(c, A);
+        if (dir_mode == 2) return launch_axis<double, 1, 0, 2>(c, A);
+        return launch_axis<double, 1, 0, 0>(c, A);
+    }
+    if (dir_mode == 1) return launch_axis<double, 2, 0, 1>(c, A);
+    if (dir_mode == 2) return launch_axis<double, 2, 0, 2>(c, A);
+    return launch_axis<double, 2, 0, 0>(c, A);
+}
+
+bfvm_status launch_sources(Ctx* c, int p_next, bool renormed)
+{
+    const SourceTable& S = c->src;
+    if (S.n_entries == 0) return BFVM_OK;
+    int blk = 256;
+    unsigned grid = (unsigned)ceil_div(S.n_entries, blk);
+    int off_y = c->nx, off_z = c->nx + c->ny;
+    bool scaled = (c->variant == 1 && c->precision == 64 && !renormed);
+    if (c->precision == 64) {
+        double* f = reinterpret_cast<double*>(c->field);
+        if (scaled) {
+            const double* sc = c->coef.sc + (int64_t)p_next * c->n_sub * c->coef.L;
+            k_sources<double, true><<<grid, blk, 0, c->stream>>>(
+                f, S.n_entries, S.off, S.alpha, S.beta, S.vox, S.sub, c->nx, c->ny,
+                c->coef.L, off_y, off_z, sc);
+        } else {
+            k_sources<double, false><<<grid, blk, 0, c->stream>>>(
+                f, S.n_entries, S.off, S.alpha, S.beta, S.vox, S.sub, c->nx, c->ny,
+                c->coef.L, off_y, off_z, nullptr);
+        }
+    } else {
+        float* f = reinterpret_cast<float*>(c->field);
+        k_sources<float, false><<<grid, blk, 0, c->stream>>>(
+            f, S.n_entries, S.off, S.alpha, S.beta, S.vox, S.sub, c->nx, c->ny,
+            c->coef.L, off_y, off_z, nullptr);
+    }
+    c->launches += 1;
+    BFVM_CUDA(c, cudaGetLastError());
+    return BFVM_OK;
+}
+
+// One full step in rescale state p (0 <= p < period).  With renorm the z
+// sweep returns the field to plain values.
+bfvm_status launch_step(Ctx* c, int p, bool renorm)
+{
+    bfvm_status st;
+    if (c->precision == 32) {
+        st = launch_xyz<float, 0>(c, 0, c->coef.r32, c->coef.cr32, c->coef.c32);
+        if (st != BFVM_OK) return st;
+        return launch_sources(c, 0, true);
+    }
+    if (c->variant == 0) {
+        st = launch_xyz<double, 0>(c, 0, c->coef.r, c->coef.cr, c->coef.c);
+        if (st != BFVM_OK) return st;
+        return launch_sources(c, 0, true);
+    }
+    if (renorm) st = launch_xyz<double, 2>(c, p, c->coef.r, c->coef.cr, c->coef.c);
+    else st = launch_xyz<double, 1>(c, p, c->coef.r, c->coef.cr, c->coef.c);
+    if (st != BFVM_OK) return st;
+    return launch_sources(c, p + 1, renorm);
+}
+
+int sweep_kernel_count_per_step(const Ctx* c)
+{
+    return 3 + (c->src.n_entries > 0 ? 1 : 0);
+}
+
+// ---------------------------------------------------------------- layout
+namespace {
+
+template <typename T>
+__global__ void k_unscale_copy(const T* __restrict__ field, T* __restrict__ out,
+                               int nx, int ny, int nz, int n_sub, int64_t pitch,
+                               int64_t L, const double* __restrict__ isc)
+{
+    int64_t n = (int64_t)nx * ny * nz * n_sub;
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    int x = (int)(e % nx);
+    int64_t t = e / nx;
+    int y = (int)(t % ny); t /= ny;
+    int z = (int)(t % nz);
+    int s = (int)(t / nz);
+    int64_t src = (((int64_t)s * nz + z) * ny + y) * pitch + x;
+    double val = (double)field[src];
+    if (isc) {
+        const double* q = isc + (int64_t)s * L;
+        val = val * (q[x] * q[nx + y] * q[nx + ny + z]);
+    }
+    out[e] = (T)val;
+}
+
+}  // namespace
+
+// Copy the field into a dense device buffer, removing the rescale of state p.
+bfvm_status launch_unscale_copy(Ctx* c, void* out_dev, int p)
+{
+    int64_t n = (int64_t)c->nx * c->ny * c->nz * c->n_sub;
+    if (n == 0) return BFVM_OK;
+    const double* isc = nullptr;
+    if (p != 0) isc = c->coef.isc + (int64_t)p * c->n_sub * c->coef.L;
+    unsigned grid = (unsigned)ceil_div(n, 256);
+    if (c->precision == 64)
+        k_unscale_copy<double><<<grid, 256, 0, c->stream>>>(
+            reinterpret_cast<const double*>(c->field), reinterpret_cast<double*>(out_dev),
+            c->nx, c->ny, c->nz, c->n_sub, c->pitch, c->coef.L, isc);
+    else
+        k_unscale_copy<float><<<grid, 256, 0, c->stream>>>(
+            reinterpret_cast<const float*>(c->field), reinterpret_cast<float*>(out_dev),
+            c->nx, c->ny, c->nz, c->n_sub, c->pitch, c->coef.L, nullptr);
+    c->launches += 1;
+    BFVM_CUDA(c, cudaGetLastError());
+    return BFVM_OK;
+}
+
+}  // namespace bfvm

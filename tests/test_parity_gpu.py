@@ -1,0 +1,223 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 CPU oracle.
+
+Tolerance: per-substrate infinity-norm relative error <= 1e-12 for FP64 and
+<= 1e-5 for the FP32 field.  Sizes span several 32-line warp blocks with
+ragged tails, lines of length 1 and 2, lines longer than the shared-memory
+staging, both sweep forms (plain and rescaled), mid-period reads of the
+rescaled field, and Dirichlet and zero-flux substrates side by side.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2110_13368_gb300 import inputs
+from tests.helpers import need_gpu, rel_inf, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+TOL32 = 1e-5
+
+
+@pytest.fixture(scope="module")
+def bf():
+    need_gpu()
+    from paper_2110_13368_gb300 import build, bfvm
+    build.build()
+    return bfvm
+
+
+def run_gpu(bf, p, steps=None, precision=None, variant=None, period=None, graphs=None,
+            cells_on_device=True):
+    sim = bf.Sim.from_problem(p, precision=precision, cells_on_device=cells_on_device)
+    if variant is not None:
+        sim.set_option(bf.OPT_VARIANT, variant)
+    if period is not None:
+        sim.set_option(bf.OPT_PERIOD, period)
+    if graphs is not None:
+        sim.set_option(bf.OPT_GRAPHS, graphs)
+    sim.step(p.steps if steps is None else steps)
+    out = sim.get_density().double().cpu().numpy()
+    info = sim.info()
+    sim.close()
+    return out, info
+
+
+def mixed(nx, ny, nz, n_cells=200, steps=6, seed=1, **kw):
+    args = dict(n_sub=2, D=[1e5, 2e3], lam=[0.1, 0.01], bc_kind=[1, 0],
+                bc_value=[38.0, 0.0], n_cells=n_cells, U=[10.0, 0.5], S=[0.0, 10.0],
+                rho_star=[1.0, 3.0], steps=steps, seed=seed)
+    args.update(kw)
+    return inputs.make_problem(nx, ny, nz, **args)
+
+
+CASES = {
+    "ragged_37x45x50": lambda: mixed(37, 45, 50),
+    "cube_33": lambda: mixed(33, 33, 33, n_cells=500, steps=9),
+    "thin_1x1x7": lambda: mixed(1, 1, 7, n_cells=3),
+    "thin_2x3x1": lambda: mixed(2, 3, 1, n_cells=4),
+    "thin_5x1x3": lambda: mixed(5, 1, 3, n_cells=4),
+    "flat_64x2x40": lambda: mixed(64, 2, 40),
+    "long_x_300": lambda: mixed(300, 6, 5, n_cells=50, steps=3),
+    "long_z_260": lambda: mixed(9, 7, 260, n_cells=50, steps=3),
+    "no_cells_3sub": lambda: inputs.make_problem(23, 17, 29, n_sub=3, D=[1e5, 3e2, 4e4],
+                                                 lam=[0.1, 0.0, 0.9], bc_kind=[1, 0, 1],
+                                                 bc_value=[38.0, 0.0, 5.0], steps=5, seed=2),
+    "plain_50_fullsteps": lambda: inputs.plain_50(),
+}
+
+
+@pytest.mark.parametrize("variant", [0, 1])
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_fp64_matches_oracle(bf, case, variant):
+    p = CASES[case]()
+    ref = oracle.run(p)
+    got, info = run_gpu(bf, p, variant=variant)
+    assert info["variant"] == variant
+    err = rel_inf(got, ref)
+    assert np.all(err <= TOL64), (case, variant, err)
+
+
+def test_rescaled_across_periods_and_mid_period_reads(bf):
+    """Short rescale period: the renormalising z sweep runs several times and
+    the field is read while it still carries a scale."""
+    p = mixed(30, 26, 22, n_cells=300, steps=11)
+    for steps in (1, 2, 3, 7, 11):
+        ref = oracle.run(p, n_steps=steps)
+        got, info = run_gpu(bf, p, steps=steps, variant=1, period=3)
+        assert info["period"] == 3
+        assert np.all(rel_inf(got, ref) <= TOL64), (steps, rel_inf(got, ref))
+
+
+def test_step_calls_compose(bf):
+    """bfvm_step(a); bfvm_step(b) equals bfvm_step(a + b) of the oracle."""
+    p = mixed(20, 19, 18, n_cells=100, steps=10)
+    ref = oracle.run(p, n_steps=10)
+    sim = bf.Sim.from_problem(p)
+    sim.set_option(bf.OPT_PERIOD, 4)
+    for n in (3, 1, 4, 2):
+        sim.step(n)
+    got = sim.get_density().cpu().numpy()
+    sim.close()
+    assert np.all(rel_inf(got, ref) <= TOL64)
+
+
+def test_graphs_off_matches_graphs_on(bf):
+    p = mixed(25, 24, 23, n_cells=150, steps=40)
+    a, _ = run_gpu(bf, p, graphs=1)
+    b, _ = run_gpu(bf, p, graphs=0)
+    np.testing.assert_array_equal(a, b)
+
+
+def test_deterministic_repeat(bf):
+    p = mixed(31, 30, 29, n_cells=400, steps=8)
+    a, _ = run_gpu(bf, p)
+    b, _ = run_gpu(bf, p)
+    np.testing.assert_array_equal(a, b)
+
+
+def test_host_cells_equal_device_cells(bf):
+    p = mixed(19, 21, 17, n_cells=250, steps=4)
+    a, _ = run_gpu(bf, p, cells_on_device=True)
+    b, _ = run_gpu(bf, p, cells_on_device=False)
+    np.testing.assert_array_equal(a, b)
+
+
+def test_checkpoint_resume_is_bitwise(bf):
+    """get_density / set_density round trip is an exact resume (plain form)."""
+    p = mixed(24, 22, 20, n_cells=120, steps=6)
+    whole, _ = run_gpu(bf, p, variant=0)
+    s1 = bf.Sim.from_problem(p)
+    s1.set_option(bf.OPT_VARIANT, 0)
+    s1.step(2)
+    mid = s1.get_density().cpu().numpy()
+    s1.close()
+    s2 = bf.Sim.from_problem(p.with_(rho0=mid))
+    s2.set_option(bf.OPT_VARIANT, 0)
+    s2.step(4)
+    resumed = s2.get_density().cpu().numpy()
+    s2.close()
+    np.testing.assert_array_equal(whole, resumed)
+
+
+def test_co_located_cells_keep_index_order(bf):
+    """Many cells in few voxels: the composed maps must follow cell index."""
+    p = mixed(6, 5, 4, n_cells=0, steps=3)
+    rng = np.random.default_rng(9)
+    n = 400
+    vox = rng.integers(0, 3, size=(n, 3))
+    p.pos = (vox + 0.5) * p.dx
+    p.vol = np.full(n, 2494.0)
+    p.U = rng.uniform(0, 10, size=(n, 2))
+    p.S = rng.uniform(0, 10, size=(n, 2))
+    p.rho_star = rng.uniform(0, 40, size=(n, 2))
+    ref = oracle.run(p)
+    got, _ = run_gpu(bf, p)
+    assert np.all(rel_inf(got, ref) <= TOL64)
+
+
+def test_cells_on_faces_and_domain_max(bf):
+    p = mixed(10, 9, 8, n_cells=0, steps=2)
+    pos = np.array([[0.0, 0.0, 0.0], [20.0, 40.0, 60.0], [200.0, 180.0, 160.0],
+                    [199.999, 0.0, 159.9999], [100.0, 100.0, 100.0]])
+    n = len(pos)
+    p.pos = pos
+    p.vol = np.full(n, 3000.0)
+    p.U = np.full((n, 2), 4.0)
+    p.S = np.full((n, 2), 2.0)
+    p.rho_star = np.full((n, 2), 7.0)
+    ref = oracle.run(p)
+    got, _ = run_gpu(bf, p)
+    assert np.all(rel_inf(got, ref) <= TOL64)
+
+
+@pytest.mark.parametrize("case", ["ragged_37x45x50", "cube_33", "thin_1x1x7", "long_x_300",
+                                  "plain_50_fullsteps"])
+def test_fp32_matches_fp64_oracle(bf, case):
+    p = CASES[case]()
+    ref = oracle.run(p)
+    got, info = run_gpu(bf, p, precision=32)
+    assert info["precision"] == 32
+    err = rel_inf(got, ref)
+    assert np.all(err <= TOL32), (case, err, rel_l2(got, ref))
+
+
+def test_zero_steps_and_empty_cells(bf):
+    p = mixed(12, 11, 10, n_cells=0, steps=0)
+    got, _ = run_gpu(bf, p, steps=0)
+    np.testing.assert_array_equal(got, p.rho0)
+    got1, _ = run_gpu(bf, p, steps=2)
+    assert np.all(rel_inf(got1, oracle.run(p, n_steps=2)) <= TOL64)
+
+
+def test_invalid_cells_rejected(bf):
+    p = mixed(8, 8, 8, n_cells=5, steps=1)
+    sim = bf.Sim.from_problem(p.with_(pos=None))
+    bad = p.pos.copy()
+    bad[2, 1] = 8 * 20.0 + 1.0
+    with pytest.raises(bf.BfvmError) as ei:
+        sim.set_cells(bad, p.vol, p.S, p.U, p.rho_star)
+    assert ei.value.status == 1
+    vol = p.vol.copy()
+    vol[0] = 0.0
+    with pytest.raises(bf.BfvmError):
+        sim.set_cells(p.pos, vol, p.S, p.U, p.rho_star)
+    S = p.S.copy()
+    S[1, 0] = np.nan
+    with pytest.raises(bf.BfvmError):
+        sim.set_cells(p.pos, p.vol, S, p.U, p.rho_star)
+    rho = p.rho0.copy()
+    rho[0, 1, 2, 3] = np.inf
+    with pytest.raises(bf.BfvmError) as ei:
+        sim.set_density(rho)
+    assert ei.value.status == 6
+    with pytest.raises(bf.BfvmError) as ei:
+        bf.bfvm_backward(sim.handle, np.zeros(p.rho0.shape), 0, np.zeros(2), np.zeros(2),
+                         None, None)
+    assert ei.value.status == 4
+    # the context still works after the rejected calls
+    sim.set_cells(p.pos, p.vol, p.S, p.U, p.rho_star)
+    sim.step(1)
+    got = sim.get_density().cpu().numpy()
+    sim.close()
+    assert np.all(rel_inf(got, oracle.run(p)) <= TOL64)
