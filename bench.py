@@ -1,0 +1,402 @@
+#!/usr/bin/env python3
+"""Benchmark of the LOD diffusion-decay-source step (Eq. 1) on GB300.
+
+Default workload: the 200^3 x 2 tumour problem in FP64 (oxygen with a
+Dirichlet shell plus a secreted factor, 250 000 cells in a central sphere;
+see paper_2110_13368_gb300.inputs).  One bench step is one full LOD step
+(Dirichlet prologue, x, y, z sweeps, cell sources) over the whole grid.
+
+Timing: W untimed warm-up steps, then K timed steps.  Before every timed
+step a 512 MB buffer is written to flush the 135 MB L2; each step is timed
+with CUDA events on the library's stream, and the per-kernel device times
+come from the library's own event brackets (option 5).  value = voxel-
+substrate updates per second over the K steps (max over ranks; for N > 1
+each rank runs an independent replica: the single grid does not shard).
+
+Prints one JSON line.  --impl reference times the CPU oracle (the plain FP64
+reference) on the host cores instead, on the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+HBM_FALLBACK_GBS = 6800.0
+FP64_PEAK_TFLOPS = 1.25       # 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
+L2_FLUSH_BYTES = 512 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="tumour_200",
+                    choices=["tumour_200", "tumour_200_fp32", "plain_50"])
+    ap.add_argument("--variant", type=int, default=None, help="FP64 sweep form: 0 plain, 1 rescaled")
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--skip-extras", action="store_true",
+                    help="timed steps only: no e2e, continuous run or CPU baseline (profiling runs)")
+    return ap.parse_args()
+
+
+def make_problem(name):
+    from paper_2110_13368_gb300 import inputs
+    if name == "tumour_200":
+        return inputs.tumour_200(steps=1000, precision=64)
+    if name == "tumour_200_fp32":
+        return inputs.tumour_200(steps=1000, precision=32)
+    if name == "plain_50":
+        return inputs.plain_50()
+    raise ValueError(name)
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return HBM_FALLBACK_GBS, "fallback"
+
+
+def sweep_traffic(workload):
+    """DRAM bytes per sweep launch from the committed ncu summary, if it was
+    taken on the current sweep source; else None."""
+    src = os.path.join(ROOT, "paper_2110_13368_gb300", "csrc", "sweeps.cu")
+    digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    path = os.path.join(ROOT, "profiles", f"traffic_{workload}.txt")
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    for line in open(path):
+        line = line.strip()
+        if not line or line.startswith("#") or ":" not in line:
+            continue
+        k, v = line.split(":", 1)
+        vals[k.strip()] = v.strip()
+    if vals.get("sweeps_sha256_16") != digest:
+        return None
+    out = {}
+    for k in ("x", "y", "z", "sources"):
+        if k in vals:
+            out[k] = float(vals[k])
+    return out
+
+
+class Clocks:
+    """nvidia-smi sampled every 200 ms while the timed region runs."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.index), "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is None:
+            return
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def cpu_baseline(p, seconds):
+    """The oracle as it stands, on this host's cores, on a bounded sample of
+    the workload: whole steps of the full grid until `seconds` have passed."""
+    import oracle
+    oracle.build()
+    threads = oracle.max_threads()
+    rho = p.rho0
+    steps = 0
+    t0 = time.perf_counter()
+    while True:
+        rho = oracle.run(p, rho0=rho, n_steps=1, n_threads=threads)
+        steps += 1
+        el = time.perf_counter() - t0
+        if el >= seconds or steps >= 50:
+            break
+    ups = p.updates_per_step * steps / el
+    return {"value": ups, "unit": "voxel-substrate updates/s", "cores": threads,
+            "kind": "oracle",
+            "sample": f"{steps} full step(s) of the {p.nx}x{p.ny}x{p.nz}x{p.n_sub} workload "
+                      f"from its initial field, {el:.1f} s, {threads} OpenMP threads"}
+
+
+def metric_name():
+    return "voxel-substrate LOD updates/s at 200^3x2 FP64 + % HBM roofline"
+
+
+def run_reference(args):
+    world, rank, local = dist_setup(args)
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    p = make_problem(args.workload)
+    threads = oracle.max_threads()
+    rho = p.rho0
+    for _ in range(args.warmup):
+        rho = oracle.run(p, rho0=rho, n_steps=1, n_threads=threads)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        rho = oracle.run(p, rho0=rho, n_steps=1, n_threads=threads)
+    el = time.perf_counter() - t0
+    ups = p.updates_per_step * args.steps / el
+    line = {"metric": metric_name(), "value": ups, "unit": "voxel-substrate updates/s",
+            "impl": "reference", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": p.name, "grid": [p.nx, p.ny, p.nz], "n_sub": p.n_sub,
+                       "cells": p.n_cells, "l2": "n/a (host)"},
+            "cpu_baseline": {"value": ups, "unit": "voxel-substrate updates/s", "cores": threads,
+                             "kind": "oracle",
+                             "sample": f"{args.steps} timed full steps after {args.warmup} warm-up"},
+            "e2e": {"value": ups, "unit": "voxel-substrate updates/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    world, rank, local = dist_setup(args)
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    from paper_2110_13368_gb300 import build as pbuild
+    from paper_2110_13368_gb300 import bfvm
+    pbuild.build()
+    p = make_problem(args.workload)
+    prec = p.precision
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream(dev)
+    sim = bfvm.Sim.from_problem(p)
+    if args.variant is not None:
+        sim.set_option(bfvm.OPT_VARIANT, args.variant)
+    sim.set_option(bfvm.OPT_TIME_KERNELS, 1)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    for _ in range(max(args.warmup, 3)):
+        flush.fill_(1.0)
+        sim.step(1)
+    torch.cuda.synchronize()
+    bfvm.bfvm_kernel_times(sim.handle, reset=True)
+    info0 = sim.info()
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    barrier()
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        t_wall0 = time.perf_counter()
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            starts[i].record(stream)
+            sim.step(1)
+            ends[i].record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        t_wall = time.perf_counter() - t_wall0
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    total_ms = float(sum(step_ms))
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    kms, kn = bfvm.bfvm_kernel_times(sim.handle, reset=True)
+    info1 = sim.info()
+    launches = info1["launches"] - info0["launches"]
+
+    N = p.updates_per_step
+    ups = N * args.steps * world / (total_ms / 1e3)
+    ms_per_step = total_ms / args.steps
+    es = 8 if prec == 64 else 4
+    hbm, hbm_src = peaks()
+
+    kinds = ["x", "y", "z", "sources"]
+    kernels = {}
+    for k, name in enumerate(kinds):
+        if kn[k]:
+            avg = kms[k] / kn[k]
+            bytes_per_launch = 2 * es * N if k < 3 else None
+            kernels[name] = {"launches": kn[k], "avg_ms": avg, "share": kms[k] / max(sum(kms), 1e-12)}
+            if bytes_per_launch:
+                kernels[name]["gbs"] = bytes_per_launch / (avg / 1e3) / 1e9
+    dom = max(range(3), key=lambda k: kms[k])
+    dom_avg = kms[dom] / max(kn[dom], 1)
+    traffic = sweep_traffic(p.name)
+    info = sim.info()
+    rescaled = prec == 64 and info["variant"] == 1
+    if prec == 64:
+        flops_per_elem = 4 if rescaled else 5
+        achieved = flops_per_elem * N / (dom_avg / 1e3) / 1e12
+        roof = {"bound": "alu", "kernel": f"{kinds[dom]} sweep", "achieved": achieved,
+                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                "peak_source": "FP64 pipe: 152 SMs x 2 DFMA/clk x 2.07 GHz (nominal 1.25 TFLOP/s)",
+                "flops_per_element": flops_per_elem,
+                "traffic": traffic.get(kinds[dom]) if traffic else None,
+                "hbm_view": {"achieved": 2 * es * N / (dom_avg / 1e3) / 1e9, "peak": hbm,
+                             "unit": "GB/s", "frac": 2 * es * N / (dom_avg / 1e3) / 1e9 / hbm,
+                             "peak_source": hbm_src}}
+    else:
+        achieved = 2 * es * N / (dom_avg / 1e3) / 1e9
+        roof = {"bound": "hbm", "kernel": f"{kinds[dom]} sweep", "achieved": achieved,
+                "peak": hbm, "unit": "GB/s", "frac": achieved / hbm, "peak_source": hbm_src,
+                "traffic": traffic.get(kinds[dom]) if traffic else None}
+
+    if args.skip_extras:
+        sim.close()
+        if rank == 0:
+            print(json.dumps({"metric": metric_name(), "value": ups, "unit": "voxel-substrate updates/s",
+                              "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                              "ms_per_step": ms_per_step, "roofline": roof, "kernels": kernels,
+                              "gpu_launches": launches, "note": "--skip-extras"}), flush=True)
+        return 0
+
+    # end to end through the C ABI with host buffers: upload the field,
+    # one step, read the field back, every step
+    host_in = torch.empty(p.rho0.shape, dtype=sim.dtype).pin_memory()
+    host_in.copy_(torch.as_tensor(p.rho0, dtype=sim.dtype))
+    host_out = torch.empty_like(host_in).pin_memory()
+    sim.set_option(bfvm.OPT_TIME_KERNELS, 0)
+    h = sim.handle
+    bfvm.bfvm_set_density(h, host_in)
+    bfvm.bfvm_step(h, 1)
+    bfvm.bfvm_get_density(h, host_out)
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        bfvm.bfvm_set_density(h, host_in)
+        bfvm.bfvm_step(h, 1)
+        bfvm.bfvm_get_density(h, host_out)
+    torch.cuda.synchronize()
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    nbytes = host_in.numel() * host_in.element_size()
+    e2e = {"value": N * args.e2e_steps * world / e2e_s, "unit": "voxel-substrate updates/s",
+           "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
+           "steps": args.e2e_steps,
+           "call": "bfvm_set_density(host) + bfvm_step(1) + bfvm_get_density(host)"}
+
+    # continuous run for context: 1000 steps in one call (graphs, no flush)
+    sim.set_option(bfvm.OPT_TIME_KERNELS, 0)
+    sim.set_density(torch.as_tensor(p.rho0, dtype=sim.dtype, device=dev))
+    sim.step(info["period"] if rescaled else 16)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sim.step(p.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    cont_ms = e0.elapsed_time(e1)
+    continuous = {"value": N * p.steps / (cont_ms / 1e3), "steps": p.steps,
+                  "ms_per_step": cont_ms / p.steps,
+                  "note": "one bfvm_step(n) call, CUDA graphs, no L2 flush between steps"}
+    sim.close()
+
+    if rank == 0:
+        line = {"metric": metric_name(), "value": ups, "unit": "voxel-substrate updates/s",
+                "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64" if prec == 64 else "f32", "data": "synthetic",
+                "config": {"workload": p.name, "grid": [p.nx, p.ny, p.nz], "n_sub": p.n_sub,
+                           "cells": p.n_cells, "sweep": "rescaled" if rescaled else "plain",
+                           "l2": "512 MB buffer written before every timed step",
+                           "parallelism": "replicas" if world > 1 else "single"},
+                "hbm_frac_step": ups / world * 6 * es / 1e9 / hbm,
+                "roofline": roof, "kernels": kernels, "gpu_launches": launches,
+                "wall_s_timed_region": t_wall, "e2e": e2e, "continuous": continuous}
+        clocks = clk.summary()
+        line["clocks"] = clocks
+        if world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(p, args.cpu_seconds)
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -189,8 +189,20 @@ bfvm_status bfvm_get_info(const bfvm_ctx* ctx, int64_t* info);
  *   key 2  rescale period override (1..64; 0 = automatic)
  *   key 3  fuse cell sources into the z sweep: 0 no, 1 yes
  *   key 4  use CUDA graphs for bfvm_step: 0 no, 1 yes (default)
+ *   key 5  per-kernel timing: 0 off (default), 1 each sweep and source
+ *          launch is bracketed by CUDA events on the context's stream
+ *          (bfvm_step then launches kernels one by one, without graphs)
  */
 bfvm_status bfvm_set_option(bfvm_ctx* ctx, int32_t key, int64_t value);
+
+/*
+ * Device time of the kernels timed under option 5, accumulated since the
+ * last reset.  ms[4] (milliseconds) and counts[4] (launches) are host
+ * arrays indexed by kind: 0 x sweep, 1 y sweep, 2 z sweep, 3 cell sources;
+ * either may be NULL.  Synchronises the context's stream.  reset != 0 zeroes
+ * the totals after reading them.
+ */
+bfvm_status bfvm_kernel_times(bfvm_ctx* ctx, double* ms, int64_t* counts, int32_t reset);
 
 /*
  * Batched form: many independent contexts advanced together, one launch

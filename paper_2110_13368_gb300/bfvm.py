@@ -27,10 +27,12 @@ OPT_VARIANT = 1
 OPT_PERIOD = 2
 OPT_FUSE_SOURCES = 3
 OPT_GRAPHS = 4
+OPT_TIME_KERNELS = 5
 
 EXPORTED = ["bfvm_create", "bfvm_destroy", "bfvm_set_density", "bfvm_get_density",
             "bfvm_set_cells", "bfvm_step", "bfvm_sync", "bfvm_record", "bfvm_backward",
             "bfvm_last_error", "bfvm_status_string", "bfvm_get_info", "bfvm_set_option",
+            "bfvm_kernel_times",
             "bfvm_batch_create", "bfvm_batch_step", "bfvm_batch_sync", "bfvm_batch_destroy",
             "bfvm_batch_last_error"]
 
@@ -79,6 +81,7 @@ def load_library(path: Optional[str] = None):
         lib.bfvm_status_string.restype = ctypes.c_char_p
         lib.bfvm_get_info.argtypes = [_vp, ctypes.POINTER(_i64)]
         lib.bfvm_set_option.argtypes = [_vp, _i32, _i64]
+        lib.bfvm_kernel_times.argtypes = [_vp, _vp, _vp, _i32]
         lib.bfvm_batch_create.argtypes = [ctypes.POINTER(_vp), ctypes.POINTER(_vp), _i32, _vp]
         lib.bfvm_batch_step.argtypes = [_vp, _i32]
         lib.bfvm_batch_sync.argtypes = [_vp]
@@ -88,7 +91,7 @@ def load_library(path: Optional[str] = None):
         lib.bfvm_batch_last_error.restype = ctypes.c_char_p
         for name in ("bfvm_create", "bfvm_set_density", "bfvm_get_density", "bfvm_set_cells",
                      "bfvm_step", "bfvm_sync", "bfvm_record", "bfvm_backward", "bfvm_get_info",
-                     "bfvm_set_option", "bfvm_batch_create", "bfvm_batch_step",
+                     "bfvm_set_option", "bfvm_kernel_times", "bfvm_batch_create", "bfvm_batch_step",
                      "bfvm_batch_sync"):
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
@@ -217,6 +220,14 @@ def bfvm_get_info(h):
 
 def bfvm_set_option(h, key, value):
     _check(load_library().bfvm_set_option(h, int(key), int(value)), h)
+
+
+def bfvm_kernel_times(h, reset=True):
+    """(ms[4], launches[4]) per kernel kind: x, y, z sweep, sources."""
+    ms = (ctypes.c_double * 4)()
+    n = (_i64 * 4)()
+    _check(load_library().bfvm_kernel_times(h, ms, n, int(bool(reset))), h)
+    return list(ms), list(n)
 
 
 def bfvm_status_string(status):

@@ -250,6 +250,8 @@ void bfvm_destroy(bfvm_ctx* h)
     if (c->stream || c->field) cudaStreamSynchronize(c->stream);
     drop_graphs(c);
     drop_recording(c);
+    for (cudaEvent_t e : c->ev_start) cudaEventDestroy(e);
+    for (cudaEvent_t e : c->ev_stop) cudaEventDestroy(e);
     free_sources(c);
     free_coefficients(c);
     if (c->field) cudaFree(c->field);
@@ -362,10 +364,11 @@ bfvm_status bfvm_step(bfvm_ctx* h, int32_t n_steps)
         return st;
     }
     int remaining = n_steps;
+    const bool graphs = c->use_graphs && !c->time_kernels;
     // graph blocks: a whole rescale period (FP64 rescaled) or 16 steps
     const int block = rescaled(c) ? m : 16;
     while (remaining > 0 && st == BFVM_OK) {
-        if (c->use_graphs && c->scale_state == 0 && remaining >= block) {
+        if (graphs && c->scale_state == 0 && remaining >= block) {
             st = launch_graph_block(c, block);
             remaining -= block;
             c->steps_taken += block;
@@ -445,6 +448,34 @@ bfvm_status bfvm_backward(bfvm_ctx* h, const double* g_final, int32_t checkpoint
     return st;
 }
 
+bfvm_status bfvm_kernel_times(bfvm_ctx* h, double* ms, int64_t* counts, int32_t reset)
+{
+    if (!h) return BFVM_EINVAL;
+    Ctx* c = &h->impl;
+    BFVM_CUDA(c, cudaStreamSynchronize(c->stream));
+    for (size_t i = 0; i < c->ev_stop.size(); ++i) {
+        float t = 0.f;
+        cudaEventElapsedTime(&t, c->ev_start[i], c->ev_stop[i]);
+        int k = c->ev_kind[i];
+        c->kt_ms[k] += t;
+        c->kt_n[k] += 1;
+    }
+    for (cudaEvent_t e : c->ev_start) cudaEventDestroy(e);
+    for (cudaEvent_t e : c->ev_stop) cudaEventDestroy(e);
+    c->ev_start.clear();
+    c->ev_stop.clear();
+    c->ev_kind.clear();
+    for (int k = 0; k < 4; ++k) {
+        if (ms) ms[k] = c->kt_ms[k];
+        if (counts) counts[k] = c->kt_n[k];
+        if (reset) {
+            c->kt_ms[k] = 0.0;
+            c->kt_n[k] = 0;
+        }
+    }
+    return BFVM_OK;
+}
+
 bfvm_status bfvm_get_info(const bfvm_ctx* h, int64_t* info)
 {
     if (!h || !info) return BFVM_EINVAL;
@@ -491,6 +522,10 @@ bfvm_status bfvm_set_option(bfvm_ctx* h, int32_t key, int64_t value)
             if (value != 0 && value != 1) return set_err(c, BFVM_EINVAL, "graphs must be 0 or 1");
             c->use_graphs = (int)value;
             drop_graphs(c);
+            return BFVM_OK;
+        case 5:
+            if (value != 0 && value != 1) return set_err(c, BFVM_EINVAL, "timing must be 0 or 1");
+            c->time_kernels = (int)value;
             return BFVM_OK;
         default:
             return set_err(c, BFVM_EINVAL, "unknown option key");

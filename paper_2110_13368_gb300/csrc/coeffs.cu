@@ -59,10 +59,14 @@ __global__ void k_pivots(CoefParams P, double* r, double* cr, double* cvec,
     }
 }
 
-__global__ void k_round32(const double* a, float* b, int64_t n)
+// hi/lo float split: b[i] = fl32(a[i]), b[n + i] = fl32(a[i] - b[i])
+__global__ void k_split32(const double* a, float* b, int64_t n)
 {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i < n) b[i] = (float)a[i];
+    if (i >= n) return;
+    float hi = (float)a[i];
+    b[i] = hi;
+    b[n + i] = (float)(a[i] - (double)hi);
 }
 
 // One thread per (substrate, axis, position): scale vectors of all states.
@@ -150,16 +154,16 @@ bfvm_status build_coefficients(Ctx* c)
     BFVM_CUDA(c, cudaMalloc(&T.cr, sizeof(double) * n_tab));
     BFVM_CUDA(c, cudaMalloc(&T.c, sizeof(double) * c->n_sub * 3));
     BFVM_CUDA(c, cudaMalloc(&den, sizeof(double) * n_tab));
-    BFVM_CUDA(c, cudaMalloc(&T.r32, sizeof(float) * n_tab));
-    BFVM_CUDA(c, cudaMalloc(&T.cr32, sizeof(float) * n_tab));
-    BFVM_CUDA(c, cudaMalloc(&T.c32, sizeof(float) * c->n_sub * 3));
+    BFVM_CUDA(c, cudaMalloc(&T.r32, sizeof(float) * 2 * n_tab));
+    BFVM_CUDA(c, cudaMalloc(&T.cr32, sizeof(float) * 2 * n_tab));
+    BFVM_CUDA(c, cudaMalloc(&T.c32, sizeof(float) * 2 * c->n_sub * 3));
     int nt = c->n_sub * 3;
     k_pivots<<<(nt + 63) / 64, 64, 0, c->stream>>>(P, T.r, T.cr, T.c, den);
     BFVM_CUDA(c, cudaGetLastError());
     int blk = 256;
-    k_round32<<<ceil_div(n_tab, blk), blk, 0, c->stream>>>(T.r, T.r32, n_tab);
-    k_round32<<<ceil_div(n_tab, blk), blk, 0, c->stream>>>(T.cr, T.cr32, n_tab);
-    k_round32<<<1, 64, 0, c->stream>>>(T.c, T.c32, c->n_sub * 3);
+    k_split32<<<ceil_div(n_tab, blk), blk, 0, c->stream>>>(T.r, T.r32, n_tab);
+    k_split32<<<ceil_div(n_tab, blk), blk, 0, c->stream>>>(T.cr, T.cr32, n_tab);
+    k_split32<<<1, 64, 0, c->stream>>>(T.c, T.c32, c->n_sub * 3);
     BFVM_CUDA(c, cudaGetLastError());
     c->launches += 4;
 

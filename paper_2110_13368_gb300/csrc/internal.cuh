@@ -23,9 +23,12 @@ struct CoefTables {
     double* r = nullptr;    // 1 / den_i
     double* cr = nullptr;   // c / den_i
     double* c = nullptr;    // [n_sub * 3] c per substrate and axis
-    float* r32 = nullptr;   // the same rounded to FP32
-    float* cr32 = nullptr;
-    float* c32 = nullptr;
+    // FP32 form: each coefficient as an unevaluated sum hi + lo of two
+    // floats (hi = fl32(v), lo = fl32(v - hi)), so that the rounding of the
+    // coefficients adds no same-sign bias to every sweep
+    float* r32 = nullptr;   // [2][s][L]: hi block then lo block
+    float* cr32 = nullptr;  // [2][s][L]
+    float* c32 = nullptr;   // [2][s][3]
     // rescaled-Thomas tables (FP64 only), one set per rescale state p:
     // [p][s][axis offset + i]
     double* fa = nullptr;   // forward coefficient of state p
@@ -97,6 +100,37 @@ struct Ctx {
     int64_t steps_taken = 0;
     int64_t launches = 0;
     std::string err;
+
+    // optional per-kernel CUDA-event timing (kinds: 0 x, 1 y, 2 z sweep,
+    // 3 sources)
+    int time_kernels = 0;
+    std::vector<cudaEvent_t> ev_start, ev_stop;
+    std::vector<int> ev_kind;
+    double kt_ms[4] = {0, 0, 0, 0};
+    int64_t kt_n[4] = {0, 0, 0, 0};
+};
+
+// Brackets one kernel launch with CUDA events when timing is enabled.
+struct KernelTimer {
+    Ctx* c;
+    int kind;
+    cudaEvent_t stop = nullptr;
+    KernelTimer(Ctx* ctx, int k) : c(ctx), kind(k)
+    {
+        if (!c->time_kernels) return;
+        cudaEvent_t a;
+        if (cudaEventCreate(&a) != cudaSuccess) return;
+        if (cudaEventCreate(&stop) != cudaSuccess) { cudaEventDestroy(a); stop = nullptr; return; }
+        cudaEventRecord(a, c->stream);
+        c->ev_start.push_back(a);
+    }
+    ~KernelTimer()
+    {
+        if (!stop) return;
+        cudaEventRecord(stop, c->stream);
+        c->ev_stop.push_back(stop);
+        c->ev_kind.push_back(kind);
+    }
 };
 
 // ------------------------------------------------------------ helpers

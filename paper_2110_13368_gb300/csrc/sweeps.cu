@@ -73,6 +73,10 @@ struct SweepArgs {
     const T* r;            // [s][L] 1/den
     const T* cr;           // [s][L] c/den
     const T* cvec;         // [s][3]
+    // FP32 form: low parts of the hi + lo coefficient pairs (null for FP64)
+    const T* r_lo;
+    const T* cr_lo;
+    const T* cvec_lo;
     // rescaled form (FP64): state p tables
     const double* fa;      // [s][L]
     const double* fb;
@@ -196,7 +200,7 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs<T> A)
 
     // forward elimination (in place)
     T prev = (T)0;
-    if (MODE == 0) {
+    if (MODE == 0 && sizeof(T) == 8) {
         const T c = A.cvec[s * 3 + AXIS];
         const T* __restrict__ r = A.r + row + A.axis_off;
         const int gs = (n + kGroups - 1) / kGroups;
@@ -207,6 +211,24 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs<T> A)
                 T d = w[k * wstride];
                 if (all_in || (dir && (k == 0 || k == n - 1))) d = end_in(k);
                 prev = fma(c, prev, d) * r[k];
+                w[k * wstride] = prev;
+            }
+        }
+    } else if (MODE == 0) {
+        // FP32: coefficients as hi + lo pairs
+        const T c = A.cvec[s * 3 + AXIS];
+        const T c_lo = A.cvec_lo[s * 3 + AXIS];
+        const T* __restrict__ r = A.r + row + A.axis_off;
+        const T* __restrict__ r_lo = A.r_lo + row + A.axis_off;
+        const int gs = (n + kGroups - 1) / kGroups;
+        for (int g = 0; g < kGroups; ++g) {
+            if (SMEM) cp_async_wait_dyn(kGroups - 1 - g);
+            int k0 = g * gs, k1 = min(n, k0 + gs);
+            for (int k = k0; k < k1; ++k) {
+                T d = w[k * wstride];
+                if (all_in || (dir && (k == 0 || k == n - 1))) d = end_in(k);
+                T t = fma(c_lo, prev, fma(c, prev, d));
+                prev = fma(t, r[k], t * r_lo[k]);
                 w[k * wstride] = prev;
             }
         }
@@ -240,10 +262,17 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs<T> A)
     };
     T x = prev;
     emit(n - 1, x);
-    if (MODE == 0) {
+    if (MODE == 0 && sizeof(T) == 8) {
         const T* __restrict__ cr = A.cr + row + A.axis_off;
         for (int k = n - 2; k >= 0; --k) {
             x = fma(cr[k], x, w[k * wstride]);
+            emit(k, x);
+        }
+    } else if (MODE == 0) {
+        const T* __restrict__ cr = A.cr + row + A.axis_off;
+        const T* __restrict__ cr_lo = A.cr_lo + row + A.axis_off;
+        for (int k = n - 2; k >= 0; --k) {
+            x = fma(cr_lo[k], x, fma(cr[k], x, w[k * wstride]));
             emit(k, x);
         }
     } else {
@@ -302,6 +331,12 @@ SweepArgs<T> make_args(Ctx* c, int axis, int p, const T* r, const T* cr,
     A.off_x = 0; A.off_y = c->nx; A.off_z = c->nx + c->ny;
     A.axis_off = axis == 0 ? 0 : (axis == 1 ? A.off_y : A.off_z);
     A.r = r; A.cr = cr; A.cvec = cvec;
+    if (sizeof(T) == 4) {
+        int64_t n_tab = (int64_t)c->n_sub * c->coef.L;
+        A.r_lo = r + n_tab;
+        A.cr_lo = cr + n_tab;
+        A.cvec_lo = cvec + (int64_t)c->n_sub * 3;
+    }
     if (c->coef.fa) {
         int64_t per_state = (int64_t)c->n_sub * c->coef.L;
         A.fa = c->coef.fa + (int64_t)p * per_state;
@@ -323,6 +358,7 @@ bfvm_status launch_axis(Ctx* c, const SweepArgs<T>& A)
     int warps = (int)((c->smem_optin) / per_warp);
     if (warps > max_warps) warps = max_warps;
     int64_t blocks;
+    KernelTimer timer(c, AXIS);
     if (warps >= 1) {
         size_t smem = per_warp * warps;
         auto kern = k_sweep<T, AXIS, MODE, DIR, true>;
@@ -384,6 +420,7 @@ bfvm_status launch_sources(Ctx* c, int p_next, bool renormed)
     unsigned grid = (unsigned)ceil_div(S.n_entries, blk);
     int off_y = c->nx, off_z = c->nx + c->ny;
     bool scaled = (c->variant == 1 && c->precision == 64 && !renormed);
+    KernelTimer timer(c, 3);
     if (c->precision == 64) {
         double* f = reinterpret_cast<double*>(c->field);
         if (scaled) {
