@@ -314,6 +314,14 @@ __global__ void k_sources(T* __restrict__ field, int64_t n_entries,
     field[o] = (T)fma(alpha[e], r, b);
 }
 
+}  // namespace
+}  // namespace bfvm
+
+#include "sweep_persistent.cuh"
+
+namespace bfvm {
+namespace {
+
 template <typename T>
 SweepArgs<T> make_args(Ctx* c, int axis, int p, const T* r, const T* cr,
                        const T* cvec)
@@ -353,23 +361,27 @@ SweepArgs<T> make_args(Ctx* c, int axis, int p, const T* r, const T* cr,
 template <typename T, int AXIS, int MODE, int DIR = 0>
 bfvm_status launch_axis(Ctx* c, const SweepArgs<T>& A)
 {
-    size_t per_warp = (size_t)32 * A.n * sizeof(T);
+    constexpr int G = persistent::Groups<T>::G;
+    const int ns = (int)ceil_div(A.n, G) * G;
+    size_t per_warp = (size_t)32 * ns * sizeof(T);
     int max_warps = sizeof(T) == 8 ? 4 : 8;
     int warps = (int)((c->smem_optin) / per_warp);
     if (warps > max_warps) warps = max_warps;
-    int64_t blocks;
     KernelTimer timer(c, AXIS);
     if (warps >= 1) {
+        // persistent, software-pipelined form: one CTA per SM
         size_t smem = per_warp * warps;
-        auto kern = k_sweep<T, AXIS, MODE, DIR, true>;
+        auto kern = persistent::k_sweep_persistent<T, AXIS, MODE, DIR>;
         BFVM_CUDA(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)smem));
-        int threads = 32 * warps;
-        blocks = ceil_div(A.n_lines, threads);
-        kern<<<(unsigned)blocks, threads, smem, c->stream>>>(A);
+        int64_t n_blocks = ceil_div(A.n_lines, 32);
+        int64_t grid = ceil_div(n_blocks, warps);
+        if (grid > c->sm_count) grid = c->sm_count;
+        kern<<<(unsigned)grid, 32 * warps, smem, c->stream>>>(A, n_blocks, ns);
     } else {
+        // lines too long for shared memory: intermediates kept in the field
         auto kern = k_sweep<T, AXIS, MODE, DIR, false>;
-        blocks = ceil_div(A.n_lines, 128);
+        int64_t blocks = ceil_div(A.n_lines, 128);
         kern<<<(unsigned)blocks, 128, 0, c->stream>>>(A);
     }
     c->launches += 1;
