@@ -39,6 +39,7 @@ struct LaneLine {
     bool valid;        // a real line (the tail of the last block is padding)
     bool dir;          // Dirichlet substrate
     bool shell;        // the whole line lies on the Dirichlet shell
+    double v;          // Dirichlet value (0 in the adjoint)
     double kline;      // Dirichlet value times the other axes' scales
     double inv_other;  // inverse of the other axes' scales (MODE 2)
 };
@@ -69,6 +70,7 @@ __device__ __forceinline__ LaneLine lane_line(const SweepArgs<T>& A, int64_t lin
     }
     L.dir = A.bc_kind[L.s] == BFVM_BC_DIRICHLET;
     double v = (DIR == 2) ? 0.0 : A.bc_value[L.s];
+    L.v = v;
     L.kline = v;
     L.inv_other = 1.0;
     if (MODE >= 1) {
@@ -279,7 +281,7 @@ __global__ void __launch_bounds__(256, 1) k_sweep_persistent(SweepArgs<T> A, int
                         if (ov) {
                             if (DIR == 2) out = (T)0;
                             else if (MODE == 1) out = (T)(cur.kline * so0[u]);
-                            else out = (T)cur.kline;
+                            else out = (T)cur.v;   // plain, or renormalised back to plain
                         } else if (MODE == 2) {
                             out = (T)(((double)x * so0[u]) * cur.inv_other);
                         } else {
