@@ -239,6 +239,7 @@ bfvm_status bfvm_create(bfvm_ctx** out, int32_t nx, int32_t ny, int32_t nz, doub
     cudaMemcpyAsync(c->d_bc_value, bc_value, sizeof(double) * n_sub, cudaMemcpyHostToDevice, c->stream);
     bfvm_status st = build_coefficients(c);
     if (st != BFVM_OK) return fail(st);
+    if ((st = build_line_tables(c)) != BFVM_OK) return fail(st);
     *out = h;
     return BFVM_OK;
 }
@@ -254,6 +255,7 @@ void bfvm_destroy(bfvm_ctx* h)
     for (cudaEvent_t e : c->ev_stop) cudaEventDestroy(e);
     free_sources(c);
     free_coefficients(c);
+    c->free_line_tables();
     if (c->field) cudaFree(c->field);
     if (c->d_bc_kind) cudaFree(c->d_bc_kind);
     if (c->d_bc_value) cudaFree(c->d_bc_value);

@@ -101,6 +101,46 @@ struct Ctx {
     int64_t launches = 0;
     std::string err;
 
+    // line sets of the persistent sweeps (per axis, per substrate)
+    int lines_lo_a[3][64] = {}, lines_cnt_a[3][64] = {}, lines_lo_b[3][64] = {};
+    int64_t lines_first[3][65] = {};
+    int64_t* d_first[3] = {nullptr, nullptr, nullptr};
+    int* d_lo_a[3] = {nullptr, nullptr, nullptr};
+    int* d_cnt_a[3] = {nullptr, nullptr, nullptr};
+    int* d_lo_b[3] = {nullptr, nullptr, nullptr};
+    bool line_tables_ready[3] = {false, false, false};
+    cudaError_t ensure_line_tables(int axis, const int64_t* first)
+    {
+        if (line_tables_ready[axis]) return cudaSuccess;
+        cudaError_t e;
+        if ((e = cudaMalloc(&d_first[axis], sizeof(int64_t) * (n_sub + 1))) != cudaSuccess) return e;
+        if ((e = cudaMalloc(&d_lo_a[axis], sizeof(int) * n_sub)) != cudaSuccess) return e;
+        if ((e = cudaMalloc(&d_cnt_a[axis], sizeof(int) * n_sub)) != cudaSuccess) return e;
+        if ((e = cudaMalloc(&d_lo_b[axis], sizeof(int) * n_sub)) != cudaSuccess) return e;
+        // synchronous copies: the tables are built once, outside any capture
+        if ((e = cudaMemcpy(d_first[axis], first, sizeof(int64_t) * (n_sub + 1),
+                            cudaMemcpyHostToDevice)) != cudaSuccess) return e;
+        if ((e = cudaMemcpy(d_lo_a[axis], lines_lo_a[axis], sizeof(int) * n_sub,
+                            cudaMemcpyHostToDevice)) != cudaSuccess) return e;
+        if ((e = cudaMemcpy(d_cnt_a[axis], lines_cnt_a[axis], sizeof(int) * n_sub,
+                            cudaMemcpyHostToDevice)) != cudaSuccess) return e;
+        if ((e = cudaMemcpy(d_lo_b[axis], lines_lo_b[axis], sizeof(int) * n_sub,
+                            cudaMemcpyHostToDevice)) != cudaSuccess) return e;
+        line_tables_ready[axis] = true;
+        return cudaSuccess;
+    }
+    void free_line_tables()
+    {
+        for (int a = 0; a < 3; ++a) {
+            if (d_first[a]) cudaFree(d_first[a]);
+            if (d_lo_a[a]) cudaFree(d_lo_a[a]);
+            if (d_cnt_a[a]) cudaFree(d_cnt_a[a]);
+            if (d_lo_b[a]) cudaFree(d_lo_b[a]);
+            d_first[a] = nullptr; d_lo_a[a] = d_cnt_a[a] = d_lo_b[a] = nullptr;
+            line_tables_ready[a] = false;
+        }
+    }
+
     // optional per-kernel CUDA-event timing (kinds: 0 x, 1 y, 2 z sweep,
     // 3 sources)
     int time_kernels = 0;
@@ -149,6 +189,8 @@ void free_coefficients(Ctx* c);
 
 // sweeps (sweeps.cu): one full step in the plain or rescaled form
 bfvm_status launch_step(Ctx* c, int p, bool renorm);
+bfvm_status launch_shell_fill(Ctx* c, int p_scale);
+bfvm_status build_line_tables(Ctx* c);
 bfvm_status launch_unscale_copy(Ctx* c, void* out_dev, int p);
 int sweep_kernel_count_per_step(const Ctx* c);
 

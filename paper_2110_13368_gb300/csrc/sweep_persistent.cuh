@@ -1,4 +1,15 @@
-// Persistent, software-pipelined line sweep (included by sweeps.cu).
+// Persistent, software-pipelined line sweep for the step itself (included by
+// sweeps.cu).
+//
+// Work: the lines of one axis that need a solve.  On a Dirichlet substrate
+// a line whose other two coordinates touch the boundary lies entirely on the
+// Dirichlet shell; its values are overwritten after every sweep and no later
+// sweep reads them (the next sweep's lines through a shell voxel are either
+// shell lines themselves or have that voxel as an end, whose input is
+// replaced by the Dirichlet value).  Those lines are skipped here and the
+// shell is written once per step, after the z sweep, by k_shell_fill.  For
+// the same reason the two end outputs of a Dirichlet line are not
+// overwritten here.
 //
 // Each warp owns a column buffer of n_slots x 32 elements in shared memory
 // (one column per lane, one lane per line) and walks a static list of
@@ -6,22 +17,22 @@
 //   1. wait for the block's elements (copied in by cp.async while the
 //      previous block was being back-substituted);
 //   2. forward elimination in place, eight elements at a time with the next
-//      eight already loaded into registers (the chain is one dependent FMA
-//      per element in the rescaled FP64 form);
-//   3. back substitution four elements (one group) at a time; each finished
-//      group is written out, and its shared-memory slots are immediately
-//      refilled with the next block's elements.
-// The slot of element k alternates between k and n_slots-1-k from one block
-// to the next.  The back substitution frees slots from the end of the line
-// towards its start, and with the alternation those are exactly the slots
-// of the *first* elements of the next block, so the data needed first
-// arrives first and the forward pass of the next block rarely waits.
+//      eight already in registers (in the rescaled FP64 form the chain is
+//      one dependent FMA per element);
+//   3. back substitution one group of G elements at a time; each finished
+//      group is written out and its slots immediately refilled with the next
+//      block's elements.
+// The slot of element k alternates between k and n_slots-1-k from block to
+// block (parity Q, a template parameter so that all shared-memory offsets
+// are immediates).  The back substitution frees slots from the end of the
+// line towards its start, which under the alternation are the slots of the
+// first elements of the next block, so the data needed first arrives first.
 //
-// Global access patterns: for the y and z sweeps adjacent lanes hold
-// adjacent x, so each per-element access of a warp is one coalesced row.
-// For the x sweep the 32 lanes hold 32 consecutive rows; copies and stores
-// are transposed so that each instruction moves (32/G) rows x G consecutive
-// elements = whole 32-byte sectors (G = 32 bytes / element size).
+// Global access: for the y and z sweeps adjacent lanes hold adjacent x, so
+// each per-element access of a warp is one coalesced row.  For the x sweep
+// the lanes hold 32 rows; copies and stores are transposed so that each
+// instruction moves (32/G) rows x G consecutive elements, i.e. whole 32-byte
+// sectors (G = 32 bytes / element size).
 #pragma once
 
 namespace bfvm {
@@ -33,57 +44,69 @@ struct Groups {
     static constexpr int ROWS = 32 / G;             // rows per transposed instruction
 };
 
-struct LaneLine {
-    int64_t base;      // first element of the line (pitched layout)
+// Lines of one axis that need a solve, substrate by substrate: for a
+// Dirichlet substrate the interior range of both other coordinates, else
+// the full range.  first[s] is the index of substrate s's first line.
+struct LineSet {
+    int n_sub;
+    const int64_t* first;   // [n_sub + 1]
+    const int* lo_a;        // [n_sub] first value of the fast other coordinate
+    const int* cnt_a;       // [n_sub] its count
+    const int* lo_b;        // [n_sub] first value of the slow other coordinate
+};
+
+struct Line {
+    int64_t base;      // first element (pitched layout)
     int s;             // substrate
     bool valid;        // a real line (the tail of the last block is padding)
-    bool dir;          // Dirichlet substrate
-    bool shell;        // the whole line lies on the Dirichlet shell
-    double v;          // Dirichlet value (0 in the adjoint)
-    double kline;      // Dirichlet value times the other axes' scales
+    bool dir;          // Dirichlet substrate: both ends take the shell value
+    double end0, end1; // input values of the two ends (Dirichlet)
     double inv_other;  // inverse of the other axes' scales (MODE 2)
 };
 
-template <typename T, int AXIS, int MODE, int DIR>
-__device__ __forceinline__ LaneLine lane_line(const SweepArgs<T>& A, int64_t line)
+template <typename T, int AXIS, int MODE>
+__device__ __forceinline__ Line make_line(const SweepArgs<T>& A, const LineSet& S,
+                                          const int64_t* first_s, int64_t line)
 {
-    LaneLine L;
-    L.valid = line < A.n_lines;
-    if (!L.valid) line = A.n_lines - 1;
+    Line L;
+    L.valid = line < S.first[S.n_sub];
+    if (!L.valid) line = S.first[S.n_sub] - 1;
+    int s = 0;
+    while (s + 1 < S.n_sub && line >= first_s[s + 1]) ++s;
+    L.s = s;
+    int64_t t = line - first_s[s];
+    const int ca = S.cnt_a[s];
+    const int a = S.lo_a[s] + (int)(t % ca);
+    const int b = S.lo_b[s] + (int)(t / ca);
     int ox = 0, oy = 0, oz = 0;
-    int64_t t = line;
     if (AXIS == 0) {
-        oy = (int)(t % A.ny); t /= A.ny;
-        oz = (int)(t % A.nz); L.s = (int)(t / A.nz);
-        L.base = line * A.pitch;
-        L.shell = (oy == 0 || oy == A.ny - 1 || oz == 0 || oz == A.nz - 1);
+        oy = a; oz = b;
+        L.base = (((int64_t)s * A.nz + oz) * A.ny + oy) * A.pitch;
     } else if (AXIS == 1) {
-        ox = (int)(t % A.nx); t /= A.nx;
-        oz = (int)(t % A.nz); L.s = (int)(t / A.nz);
-        L.base = (((int64_t)L.s * A.nz + oz) * A.ny) * A.pitch + ox;
-        L.shell = (ox == 0 || ox == A.nx - 1 || oz == 0 || oz == A.nz - 1);
+        ox = a; oz = b;
+        L.base = (((int64_t)s * A.nz + oz) * A.ny) * A.pitch + ox;
     } else {
-        ox = (int)(t % A.nx); t /= A.nx;
-        oy = (int)(t % A.ny); L.s = (int)(t / A.ny);
-        L.base = ((int64_t)L.s * A.nz * A.ny + oy) * A.pitch + ox;
-        L.shell = (ox == 0 || ox == A.nx - 1 || oy == 0 || oy == A.ny - 1);
+        ox = a; oy = b;
+        L.base = ((int64_t)s * A.nz * A.ny + oy) * A.pitch + ox;
     }
-    L.dir = A.bc_kind[L.s] == BFVM_BC_DIRICHLET;
-    double v = (DIR == 2) ? 0.0 : A.bc_value[L.s];
-    L.v = v;
-    L.kline = v;
+    L.dir = A.bc_kind[s] == BFVM_BC_DIRICHLET;
+    const double v = A.bc_value[s];
+    L.end0 = v;
+    L.end1 = v;
     L.inv_other = 1.0;
     if (MODE >= 1) {
-        const int64_t row = (int64_t)L.s * A.L;
+        const int64_t row = (int64_t)s * A.L;
+        double kline;
         if (AXIS == 0)
-            L.kline = v * A.sc_p[row + A.off_y + oy] * A.sc_p[row + A.off_z + oz];
+            kline = v * A.sc_p[row + A.off_y + oy] * A.sc_p[row + A.off_z + oz];
         else if (AXIS == 1)
-            L.kline = v * A.sc_p1[row + A.off_x + ox] * A.sc_p[row + A.off_z + oz];
-        else {
-            L.kline = v * A.sc_p1[row + A.off_x + ox] * A.sc_p1[row + A.off_y + oy];
-            if (MODE == 2)
-                L.inv_other = A.isc_p1[row + A.off_x + ox] * A.isc_p1[row + A.off_y + oy];
-        }
+            kline = v * A.sc_p1[row + A.off_x + ox] * A.sc_p[row + A.off_z + oz];
+        else
+            kline = v * A.sc_p1[row + A.off_x + ox] * A.sc_p1[row + A.off_y + oy];
+        L.end0 = kline * A.sc_p[row + A.axis_off];
+        L.end1 = kline * A.sc_p[row + A.axis_off + A.n - 1];
+        if (MODE == 2 && AXIS == 2)
+            L.inv_other = A.isc_p1[row + A.off_x + ox] * A.isc_p1[row + A.off_y + oy];
     }
     return L;
 }
@@ -103,235 +126,319 @@ __device__ __forceinline__ float comp_axpy(float a_hi, float a_lo, float u, floa
     return __fadd_rn(s, corr);
 }
 
+// Shared-memory coefficient rows of one substrate (this axis only).
 template <typename T>
-__device__ __forceinline__ void cp8(T* dst, const T* src);
-template <>
-__device__ __forceinline__ void cp8<double>(double* dst, const double* src)
-{
-    cp_async_elem(dst, src);
-}
-template <>
-__device__ __forceinline__ void cp8<float>(float* dst, const float* src)
-{
-    cp_async_elem(dst, src);
-}
+struct CoefRow {
+    const T* a;      // forward: r (plain) or fa (rescaled)
+    const T* a_lo;   // FP32 low parts of r
+    const T* b;      // backward: cr (plain) or fb (rescaled)
+    const T* b_lo;   // FP32 low parts of cr
+    const double* o; // MODE 2: inverse output scale of this axis
+    T c, c_lo;       // plain form: c
+};
 
-template <typename T, int AXIS, int MODE, int DIR>
-__global__ void __launch_bounds__(256, 1) k_sweep_persistent(SweepArgs<T> A, int64_t n_blocks,
-                                                             int n_slots)
+template <typename T, int AXIS, int MODE>
+struct Sweeper {
+    static constexpr int G = Groups<T>::G;
+    static constexpr int ROWS = Groups<T>::ROWS;
+    static constexpr int FC = 8;
+
+    const SweepArgs<T>& A;
+    const LineSet& S;
+    const int64_t* first_s;
+    T* W;                 // this warp's column buffer
+    int64_t* rowbase;     // [2][32] line bases of the current / next block (x sweep)
+    const T* fin;
+    T* fout;
+    int64_t stride;
+    int n, ns, lane;
+
+    template <int Q>
+    __device__ __forceinline__ T* col(int k) const
+    {
+        return W + (Q ? (ns - 1 - k) : k) * 32;
+    }
+
+    // copy elements [gG, gG+G) of block bb's lines into the slots of parity Q
+    template <int Q>
+    __device__ __forceinline__ void prefetch_group(const Line& ln, const int64_t* rb, int g) const
+    {
+        if (AXIS == 0) {
+            const int rsub = lane / G;
+            const int e = g * G + (lane % G);
+            if (e < n) {
+#pragma unroll
+                for (int t = 0; t < G; ++t) {
+                    const int r = t * ROWS + rsub;
+                    cp_async_elem(col<Q>(e) + r, fin + rb[r] + e);
+                }
+            }
+        } else {
+            const T* src = fin + ln.base + (int64_t)g * G * stride;
+#pragma unroll
+            for (int u = 0; u < G; ++u)
+                if (g * G + u < n) cp_async_elem(col<Q>(g * G + u) + lane, src + u * stride);
+        }
+    }
+
+    template <int Q>
+    __device__ __forceinline__ void prefetch_all(const Line& ln, const int64_t* rb) const
+    {
+        for (int g = 0; g < ns / G; ++g) prefetch_group<Q>(ln, rb, g);
+    }
+
+    __device__ __forceinline__ T step_fwd(const CoefRow<T>& C, T prev, T d, int k) const
+    {
+        if (MODE == 0) {
+            if (sizeof(T) == 8) return fma(C.c, prev, d) * C.a[k];
+            float t = comp_axpy((float)C.c, (float)C.c_lo, (float)prev, (float)d);
+            return (T)__fmaf_rn(t, (float)C.a[k], __fmul_rn(t, (float)C.a_lo[k]));
+        }
+        return fma(C.a[k], prev, d);
+    }
+
+    __device__ __forceinline__ T step_bwd(const CoefRow<T>& C, T x, T w, int k) const
+    {
+        if (MODE == 0 && sizeof(T) == 4)
+            return (T)comp_axpy((float)C.b[k], (float)C.b_lo[k], (float)x, (float)w);
+        return fma(C.b[k], x, w);
+    }
+
+    // Solve the current block (parity Q) and prefetch the next one into
+    // parity !Q.
+    template <int Q>
+    __device__ __forceinline__ void block(const Line& cur, const CoefRow<T>& C, bool has_next,
+                                          const Line& nxt, const int64_t* rb_cur,
+                                          const int64_t* rb_nxt) const
+    {
+        // ---------------------------------------------------- forward
+        T prev;
+        {
+            T d0 = *(col<Q>(0) + lane);
+            if (cur.dir) d0 = (T)cur.end0;
+            prev = (MODE == 0) ? step_fwd(C, (T)0, d0, 0) : d0;   // fa[0] = 0
+            if (n > 1) *(col<Q>(0) + lane) = prev;
+            // elements 1 .. n-2
+            T buf[FC];
+#pragma unroll
+            for (int u = 0; u < FC; ++u)
+                if (1 + u < n - 1) buf[u] = *(col<Q>(1 + u) + lane);
+            for (int k0 = 1; k0 < n - 1; k0 += FC) {
+                T nb[FC];
+#pragma unroll
+                for (int u = 0; u < FC; ++u)
+                    if (k0 + FC + u < n - 1) nb[u] = *(col<Q>(k0 + FC + u) + lane);
+#pragma unroll
+                for (int u = 0; u < FC; ++u) {
+                    const int k = k0 + u;
+                    if (k < n - 1) {
+                        prev = step_fwd(C, prev, buf[u], k);
+                        *(col<Q>(k) + lane) = prev;
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < FC; ++u) buf[u] = nb[u];
+            }
+            if (n > 1) {
+                T dl = *(col<Q>(n - 1) + lane);
+                if (cur.dir) dl = (T)cur.end1;
+                prev = step_fwd(C, prev, dl, n - 1);
+            }
+        }
+        // ---------------------------------------------------- backward
+        const int h_top = (n - 1) / G;
+        T x = prev;
+        T wv[G];
+#pragma unroll
+        for (int u = 0; u < G; ++u) {
+            const int k = h_top * G + u;
+            if (k < n - 1) wv[u] = *(col<Q>(k) + lane);
+        }
+        for (int h = h_top; h >= 0; --h) {
+            T wn[G];
+#pragma unroll
+            for (int u = 0; u < G; ++u)
+                if (h > 0) wn[u] = *(col<Q>((h - 1) * G + u) + lane);
+            T o[G];
+#pragma unroll
+            for (int u = G - 1; u >= 0; --u) {
+                const int k = h * G + u;
+                if (k < n) {
+                    if (k < n - 1) x = step_bwd(C, x, wv[u], k);
+                    if (MODE == 2) o[u] = (T)(((double)x * C.o[k]) * cur.inv_other);
+                    else o[u] = x;
+                }
+            }
+            if (AXIS == 0) {
+#pragma unroll
+                for (int u = 0; u < G; ++u)
+                    if (h * G + u < n) *(col<Q>(h * G + u) + lane) = o[u];
+                __syncwarp();
+                const int rsub = lane / G;
+                const int k = h * G + (lane % G);
+                if (k < n) {
+#pragma unroll
+                    for (int t = 0; t < G; ++t) {
+                        const int r = t * ROWS + rsub;
+                        if (rb_cur[r] >= 0) fout[rb_cur[r] + k] = *(col<Q>(k) + r);
+                    }
+                }
+                __syncwarp();
+            } else if (cur.valid) {
+                T* dst = fout + cur.base + (int64_t)h * G * stride;
+#pragma unroll
+                for (int u = 0; u < G; ++u)
+                    if (h * G + u < n) dst[u * stride] = o[u];
+            }
+            if (has_next) prefetch_group<1 - Q>(nxt, rb_nxt, ns / G - 1 - h);
+#pragma unroll
+            for (int u = 0; u < G; ++u) wv[u] = wn[u];
+        }
+    }
+};
+
+// Dynamic shared memory: [coefficients of all substrates for this axis]
+// [per-warp: column buffer, 2 x 32 row bases].
+template <typename T, int AXIS, int MODE>
+__global__ void __launch_bounds__(256, 1) k_sweep_persistent(SweepArgs<T> A, LineSet S,
+                                                             int64_t n_blocks, int n_slots)
 {
     constexpr int G = Groups<T>::G;
-    constexpr int ROWS = Groups<T>::ROWS;
-    constexpr int FC = 8;   // forward chunk (elements)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int warps = blockDim.x >> 5;
     const int n = A.n;
     const int ns = n_slots;
-    T* __restrict__ W = reinterpret_cast<T*>(smem_raw) + (size_t)warp * ns * 32;
+    const int n_sub = A.n_sub;
+
+    // --- coefficient rows of this axis, all substrates
+    const int ncoef = (MODE == 0 ? (sizeof(T) == 4 ? 4 : 2) : 2);
+    T* cbase = reinterpret_cast<T*>(smem_raw);
+    const int per_sub = ncoef * n;
+    size_t coef_bytes = (size_t)n_sub * per_sub * sizeof(T);
+    double* obase = reinterpret_cast<double*>(smem_raw + ((coef_bytes + 15) & ~(size_t)15));
+    size_t o_bytes = (MODE == 2) ? (size_t)n_sub * n * sizeof(double) : 0;
+    int64_t* first_s = reinterpret_cast<int64_t*>(
+        reinterpret_cast<unsigned char*>(obase) + ((o_bytes + 15) & ~(size_t)15));
+    unsigned char* warp_area = reinterpret_cast<unsigned char*>(first_s) +
+                               (((size_t)(n_sub + 1) * 8 + 15) & ~(size_t)15);
+    for (int i = threadIdx.x; i < n_sub * n; i += blockDim.x) {
+        const int s = i / n, k = i % n;
+        const int64_t src = (int64_t)s * A.L + A.axis_off + k;
+        T* dst = cbase + (size_t)s * per_sub;
+        if (MODE == 0) {
+            dst[k] = A.r[src];
+            dst[n + k] = A.cr[src];
+            if (sizeof(T) == 4) {
+                dst[2 * n + k] = A.r_lo[src];
+                dst[3 * n + k] = A.cr_lo[src];
+            }
+        } else {
+            dst[k] = (T)A.fa[src];
+            dst[n + k] = (T)A.fb[src];
+            if (MODE == 2) obase[(size_t)s * n + k] = A.isc_p1[src];
+        }
+    }
+    for (int i = threadIdx.x; i <= n_sub; i += blockDim.x) first_s[i] = S.first[i];
+    __syncthreads();
+
+    const size_t warp_bytes = (size_t)ns * 32 * sizeof(T) + 2 * 32 * sizeof(int64_t);
+    unsigned char* my = warp_area + (size_t)warp * warp_bytes;
+    T* W = reinterpret_cast<T*>(my);
+    int64_t* rowbase = reinterpret_cast<int64_t*>(my + (size_t)ns * 32 * sizeof(T));
+
     const int64_t tw = (int64_t)gridDim.x * warps;
     int64_t b = (int64_t)blockIdx.x * warps + warp;
     if (b >= n_blocks) return;
 
-    const T* __restrict__ fin = A.in;
-    T* __restrict__ fout = A.field;
-    const int64_t stride = AXIS == 0 ? 1 : (AXIS == 1 ? A.pitch : (int64_t)A.ny * A.pitch);
+    Sweeper<T, AXIS, MODE> sw{A, S, first_s, W, rowbase, A.in, A.field,
+                              AXIS == 0 ? 1 : (AXIS == 1 ? A.pitch : (int64_t)A.ny * A.pitch),
+                              n, ns, lane};
+    (void)G;
 
-    auto slot = [&](int q, int k) { return q ? (ns - 1 - k) : k; };
-
-    // copy elements [4g, 4g + G) of the lines of block bb into slots of parity q
-    auto prefetch_group = [&](int64_t bb, const LaneLine& ln, int q, int g) {
-        if (AXIS == 0) {
-            const int rsub = lane / G;
-            const int e = g * G + (lane % G);
-#pragma unroll
-            for (int t = 0; t < G; ++t) {
-                const int row = t * ROWS + rsub;
-                int64_t line = bb * 32 + row;
-                if (line >= A.n_lines) line = A.n_lines - 1;
-                if (e < n) cp8<T>(W + (size_t)slot(q, e) * 32 + row, fin + line * A.pitch + e);
-            }
-        } else {
-#pragma unroll
-            for (int u = 0; u < G; ++u) {
-                const int e = g * G + u;
-                if (e < n) cp8<T>(W + (size_t)slot(q, e) * 32 + lane, fin + ln.base + e * stride);
-            }
-        }
+    auto coef_row = [&](int s) {
+        CoefRow<T> C;
+        const T* r = cbase + (size_t)s * per_sub;
+        C.a = r;
+        C.b = r + n;
+        C.a_lo = r + 2 * n;
+        C.b_lo = r + 3 * n;
+        C.o = obase + (size_t)s * n;
+        C.c = (MODE == 0) ? A.cvec[s * 3 + AXIS] : (T)0;
+        C.c_lo = (MODE == 0 && sizeof(T) == 4) ? A.cvec_lo[s * 3 + AXIS] : (T)0;
+        return C;
     };
 
-    int q = 0;
-    LaneLine cur = lane_line<T, AXIS, MODE, DIR>(A, b * 32 + lane);
-    for (int g = 0; g < ns / G; ++g) prefetch_group(b, cur, 0, g);
+    int par = 0;
+    Line cur = make_line<T, AXIS, MODE>(A, S, first_s, b * 32 + lane);
+    // x sweep: transposed copies need the row base of every line of the
+    // block (padding rows read a valid row; their results are dropped)
+    rowbase[32 + lane] = cur.base;
+    __syncwarp();
+    sw.template prefetch_all<0>(cur, rowbase + 32);
     cp_async_commit();
-
-    const int64_t srow = 0;  // coefficient rows are per lane (substrate)
-    (void)srow;
     for (;;) {
         const int64_t nb = b + tw;
         const bool has_next = nb < n_blocks;
-        LaneLine nxt = has_next ? lane_line<T, AXIS, MODE, DIR>(A, nb * 32 + lane) : cur;
+        Line nxt = has_next ? make_line<T, AXIS, MODE>(A, S, first_s, nb * 32 + lane) : cur;
+        // row bases: [0..31] current block's stores (-1 = padding row),
+        // [32..63] next block's copies
+        if (AXIS == 0) {
+            __syncwarp();
+            rowbase[lane] = cur.valid ? cur.base : -1;
+            rowbase[32 + lane] = nxt.base;
+            __syncwarp();
+        }
         cp_async_wait<0>();
         __syncwarp();
-
-        const int64_t row = (int64_t)cur.s * A.L + A.axis_off;
-        // ------------------------------------------------ forward
-        T prev = (T)0;
-        {
-            T d0[FC], a0[FC], a0l[FC];
-            auto load_chunk = [&](int k0, T* d, T* a, T* al) {
-#pragma unroll
-                for (int u = 0; u < FC; ++u) {
-                    const int k = k0 + u;
-                    if (k < n) {
-                        d[u] = W[(size_t)slot(q, k) * 32 + lane];
-                        if (MODE == 0) {
-                            a[u] = A.r[row + k];
-                            if (sizeof(T) == 4) al[u] = A.r_lo[row + k];
-                        } else {
-                            a[u] = (T)A.fa[row + k];
-                        }
-                    }
-                }
-            };
-            load_chunk(0, d0, a0, a0l);
-            const T c = MODE == 0 ? A.cvec[cur.s * 3 + AXIS] : (T)0;
-            const T c_lo = (MODE == 0 && sizeof(T) == 4) ? A.cvec_lo[cur.s * 3 + AXIS] : (T)0;
-            for (int k0 = 0; k0 < n; k0 += FC) {
-                T d1[FC], a1[FC], a1l[FC];
-                load_chunk(k0 + FC, d1, a1, a1l);
-#pragma unroll
-                for (int u = 0; u < FC; ++u) {
-                    const int k = k0 + u;
-                    if (k < n) {
-                        T d = d0[u];
-                        const bool end = (k == 0 || k == n - 1);
-                        if (cur.dir && (end || (DIR == 1 && cur.shell))) {
-                            if (MODE == 0) d = (T)cur.kline;
-                            else d = (T)(cur.kline * A.sc_p[row + k]);
-                        }
-                        if (MODE == 0) {
-                            if (sizeof(T) == 8) {
-                                prev = fma(c, prev, d) * a0[u];
-                            } else {
-                                float t = comp_axpy((float)c, (float)c_lo, (float)prev, (float)d);
-                                prev = (T)__fmaf_rn(t, (float)a0[u], __fmul_rn(t, (float)a0l[u]));
-                            }
-                        } else {
-                            prev = fma(a0[u], prev, d);
-                        }
-                        W[(size_t)slot(q, k) * 32 + lane] = prev;
-                    }
-                }
-#pragma unroll
-                for (int u = 0; u < FC; ++u) {
-                    d0[u] = d1[u];
-                    a0[u] = a1[u];
-                    a0l[u] = a1l[u];
-                }
-            }
-        }
-
-        // ------------------------------------------------ backward
-        {
-            const int h_top = (n - 1) / G;
-            T wv0[G], b0[G], b0l[G];
-            double so0[G];
-            auto load_group = [&](int h, T* wv, T* bb, T* bl, double* so) {
-#pragma unroll
-                for (int u = 0; u < G; ++u) {
-                    const int k = h * G + u;
-                    if (h >= 0 && k < n) {
-                        wv[u] = W[(size_t)slot(q, k) * 32 + lane];
-                        if (MODE == 0) {
-                            bb[u] = A.cr[row + k];
-                            if (sizeof(T) == 4) bl[u] = A.cr_lo[row + k];
-                        } else {
-                            bb[u] = (T)A.fb[row + k];
-                        }
-                        if (MODE == 1) so[u] = A.sc_p1[row + k];
-                        if (MODE == 2) so[u] = A.isc_p1[row + k];
-                    }
-                }
-            };
-            load_group(h_top, wv0, b0, b0l, so0);
-            T x = prev;
-            for (int h = h_top; h >= 0; --h) {
-                T wv1[G], b1[G], b1l[G];
-                double so1[G];
-                load_group(h - 1, wv1, b1, b1l, so1);
-                T o[G];
-#pragma unroll
-                for (int u = G - 1; u >= 0; --u) {
-                    const int k = h * G + u;
-                    if (k < n) {
-                        if (k < n - 1) {
-                            if (MODE == 0 && sizeof(T) == 4)
-                                x = (T)comp_axpy((float)b0[u], (float)b0l[u], (float)x, (float)wv0[u]);
-                            else
-                                x = fma(b0[u], x, wv0[u]);
-                        }
-                        // output value of element k
-                        const bool end = (k == 0 || k == n - 1);
-                        bool ov = false;
-                        if (DIR == 0) ov = cur.dir && (cur.shell || end);
-                        if (DIR == 2) ov = cur.dir && cur.shell;
-                        T out;
-                        if (ov) {
-                            if (DIR == 2) out = (T)0;
-                            else if (MODE == 1) out = (T)(cur.kline * so0[u]);
-                            else out = (T)cur.v;   // plain, or renormalised back to plain
-                        } else if (MODE == 2) {
-                            out = (T)(((double)x * so0[u]) * cur.inv_other);
-                        } else {
-                            out = x;
-                        }
-                        o[u] = out;
-                    }
-                }
-                // write the group out
-                if (AXIS == 0) {
-#pragma unroll
-                    for (int u = 0; u < G; ++u) {
-                        const int k = h * G + u;
-                        if (k < n) W[(size_t)slot(q, k) * 32 + lane] = o[u];
-                    }
-                    __syncwarp();
-                    const int rsub = lane / G;
-                    const int k = h * G + (lane % G);
-#pragma unroll
-                    for (int t = 0; t < G; ++t) {
-                        const int r = t * ROWS + rsub;
-                        const int64_t line = b * 32 + r;
-                        if (k < n && line < A.n_lines)
-                            fout[line * A.pitch + k] = W[(size_t)slot(q, k) * 32 + r];
-                    }
-                    __syncwarp();
-                } else {
-#pragma unroll
-                    for (int u = 0; u < G; ++u) {
-                        const int k = h * G + u;
-                        if (k < n && cur.valid) fout[cur.base + k * stride] = o[u];
-                    }
-                }
-                // refill the freed slots with the next block's elements
-                if (has_next) prefetch_group(nb, nxt, q ^ 1, ns / G - 1 - h);
-#pragma unroll
-                for (int u = 0; u < G; ++u) {
-                    wv0[u] = wv1[u];
-                    b0[u] = b1[u];
-                    b0l[u] = b1l[u];
-                    so0[u] = so1[u];
-                }
-            }
-        }
+        const CoefRow<T> C = coef_row(cur.s);
+        if (par == 0)
+            sw.template block<0>(cur, C, has_next, nxt, rowbase, rowbase + 32);
+        else
+            sw.template block<1>(cur, C, has_next, nxt, rowbase, rowbase + 32);
         cp_async_commit();
         if (!has_next) break;
         b = nb;
         cur = nxt;
-        q ^= 1;
+        par ^= 1;
     }
+}
+
+// Dirichlet shell after the z sweep: every voxel of the outer layer of a
+// Dirichlet substrate gets the value times the field's current scale (state
+// p + 1 of all three axes), or the plain value when the step renormalised.
+template <typename T>
+__global__ void k_shell_fill(T* __restrict__ field, int nx, int ny, int nz, int n_sub,
+                             int64_t pitch, const int32_t* __restrict__ kind,
+                             const double* __restrict__ value, int64_t L,
+                             const double* __restrict__ sc)
+{
+    // faces enumerated as: z planes (2 nx ny), y rows of the other planes
+    // (2 nx nz), x columns (2 ny nz); overlaps are written twice with the
+    // same value
+    const int64_t fz = 2 * (int64_t)nx * ny, fy = 2 * (int64_t)nx * nz, fx = 2 * (int64_t)ny * nz;
+    const int64_t per = fz + fy + fx;
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= per * n_sub) return;
+    const int s = (int)(e / per);
+    if (kind[s] != BFVM_BC_DIRICHLET) return;
+    int64_t t = e % per;
+    int x, y, z;
+    if (t < fz) {
+        x = (int)(t % nx); y = (int)((t / nx) % ny); z = (t / ((int64_t)nx * ny)) ? nz - 1 : 0;
+    } else if ((t -= fz) < fy) {
+        x = (int)(t % nx); z = (int)((t / nx) % nz); y = (t / ((int64_t)nx * nz)) ? ny - 1 : 0;
+    } else {
+        t -= fy;
+        y = (int)(t % ny); z = (int)((t / ny) % nz); x = (t / ((int64_t)ny * nz)) ? nx - 1 : 0;
+    }
+    double v = value[s];
+    if (sc) {
+        const double* q = sc + (int64_t)s * L;
+        v = v * (q[x] * q[nx + y] * q[nx + ny + z]);
+    }
+    field[(((int64_t)s * nz + z) * ny + y) * pitch + x] = (T)v;
 }
 
 }  // namespace persistent

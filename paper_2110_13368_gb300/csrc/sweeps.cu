@@ -363,26 +363,52 @@ bfvm_status launch_axis(Ctx* c, const SweepArgs<T>& A)
 {
     constexpr int G = persistent::Groups<T>::G;
     const int ns = (int)ceil_div(A.n, G) * G;
-    size_t per_warp = (size_t)32 * ns * sizeof(T);
+    const size_t per_warp = (size_t)32 * ns * sizeof(T) + 2 * 32 * sizeof(int64_t);
+    const int ncoef = (MODE == 0 ? (sizeof(T) == 4 ? 4 : 2) : 2);
+    size_t fixed = (((size_t)A.n_sub * ncoef * A.n * sizeof(T) + 15) & ~(size_t)15) +
+                   (MODE == 2 ? (((size_t)A.n_sub * A.n * 8 + 15) & ~(size_t)15) : 0) +
+                   ((((size_t)A.n_sub + 1) * 8 + 15) & ~(size_t)15);
     int max_warps = sizeof(T) == 8 ? 4 : 8;
-    int warps = (int)((c->smem_optin) / per_warp);
+    int warps = 0;
+    if (DIR == 0 && A.n_sub <= 64 && c->smem_optin > fixed)
+        warps = (int)((c->smem_optin - fixed) / per_warp);
     if (warps > max_warps) warps = max_warps;
     KernelTimer timer(c, AXIS);
     if (warps >= 1) {
-        // persistent, software-pipelined form: one CTA per SM
-        size_t smem = per_warp * warps;
-        auto kern = persistent::k_sweep_persistent<T, AXIS, MODE, DIR>;
+        const int64_t* first = c->lines_first[AXIS];
+        if (first[A.n_sub] == 0) return BFVM_OK;   // every line is on the shell
+        if (!c->line_tables_ready[AXIS]) return set_err(c, BFVM_ESTATE, "line tables missing");
+        persistent::LineSet S;
+        S.n_sub = A.n_sub;
+        S.first = c->d_first[AXIS];
+        S.lo_a = c->d_lo_a[AXIS];
+        S.cnt_a = c->d_cnt_a[AXIS];
+        S.lo_b = c->d_lo_b[AXIS];
+        size_t smem = fixed + per_warp * warps;
+        auto kern = persistent::k_sweep_persistent<T, AXIS, MODE>;
         BFVM_CUDA(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)smem));
-        int64_t n_blocks = ceil_div(A.n_lines, 32);
+        int64_t n_blocks = ceil_div(first[A.n_sub], 32);
         int64_t grid = ceil_div(n_blocks, warps);
         if (grid > c->sm_count) grid = c->sm_count;
-        kern<<<(unsigned)grid, 32 * warps, smem, c->stream>>>(A, n_blocks, ns);
+        kern<<<(unsigned)grid, 32 * warps, smem, c->stream>>>(A, S, n_blocks, ns);
     } else {
-        // lines too long for shared memory: intermediates kept in the field
-        auto kern = k_sweep<T, AXIS, MODE, DIR, false>;
-        int64_t blocks = ceil_div(A.n_lines, 128);
-        kern<<<(unsigned)blocks, 128, 0, c->stream>>>(A);
+        size_t per_warp1 = (size_t)32 * A.n * sizeof(T);
+        int w1 = (int)(c->smem_optin / per_warp1);
+        if (w1 > 4) w1 = 4;
+        if (w1 >= 1) {
+            // generic form (adjoint passes): one warp per 32 lines, lines
+            // staged in shared memory
+            size_t smem = per_warp1 * w1;
+            auto kern = k_sweep<T, AXIS, MODE, DIR, true>;
+            BFVM_CUDA(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)smem));
+            kern<<<(unsigned)ceil_div(A.n_lines, 32 * w1), 32 * w1, smem, c->stream>>>(A);
+        } else {
+            // lines too long for shared memory: intermediates kept in the field
+            auto kern = k_sweep<T, AXIS, MODE, DIR, false>;
+            kern<<<(unsigned)ceil_div(A.n_lines, 128), 128, 0, c->stream>>>(A);
+        }
     }
     c->launches += 1;
     BFVM_CUDA(c, cudaGetLastError());
@@ -424,6 +450,33 @@ bfvm_status launch_sweep_plain64(Ctx* c, int axis, const double* in, double* out
     return launch_axis<double, 2, 0, 0>(c, A);
 }
 
+// Lines of each axis that need a solve in the step itself (see
+// sweep_persistent.cuh): per substrate the interior of the two other
+// coordinates on a Dirichlet substrate, else all of them.  Built once at
+// create (the copies are synchronous, so never inside a graph capture).
+bfvm_status build_line_tables(Ctx* c)
+{
+    if (c->n_sub > 64) return BFVM_OK;   // the generic sweep handles these
+    for (int axis = 0; axis < 3; ++axis) {
+        const int ea = axis == 0 ? c->ny : c->nx;   // fast other coordinate
+        const int eb = axis == 2 ? c->ny : c->nz;   // slow other coordinate
+        int64_t* first = c->lines_first[axis];
+        first[0] = 0;
+        for (int s = 0; s < c->n_sub; ++s) {
+            bool dir = c->bc_kind[s] == BFVM_BC_DIRICHLET;
+            int ca = dir ? ea - 2 : ea, cb = dir ? eb - 2 : eb;
+            if (ca < 0) ca = 0;
+            if (cb < 0) cb = 0;
+            c->lines_lo_a[axis][s] = dir ? 1 : 0;
+            c->lines_cnt_a[axis][s] = ca > 0 ? ca : 1;
+            c->lines_lo_b[axis][s] = dir ? 1 : 0;
+            first[s + 1] = first[s] + (int64_t)ca * cb;
+        }
+        BFVM_CUDA(c, c->ensure_line_tables(axis, first));
+    }
+    return BFVM_OK;
+}
+
 bfvm_status launch_sources(Ctx* c, int p_next, bool renormed)
 {
     const SourceTable& S = c->src;
@@ -456,6 +509,32 @@ bfvm_status launch_sources(Ctx* c, int p_next, bool renormed)
     return BFVM_OK;
 }
 
+// Dirichlet shell of all Dirichlet substrates, scaled for rescale state
+// p_scale (-1: plain values).
+bfvm_status launch_shell_fill(Ctx* c, int p_scale)
+{
+    bool any = false;
+    for (int s = 0; s < c->n_sub; ++s) any = any || c->bc_kind[s] == BFVM_BC_DIRICHLET;
+    if (!any) return BFVM_OK;
+    int64_t per = 2 * ((int64_t)c->nx * c->ny + (int64_t)c->nx * c->nz + (int64_t)c->ny * c->nz);
+    int64_t n = per * c->n_sub;
+    unsigned grid = (unsigned)ceil_div(n, 256);
+    const double* sc = nullptr;
+    if (p_scale >= 0) sc = c->coef.sc + (int64_t)p_scale * c->n_sub * c->coef.L;
+    KernelTimer timer(c, 3);
+    if (c->precision == 64)
+        persistent::k_shell_fill<double><<<grid, 256, 0, c->stream>>>(
+            reinterpret_cast<double*>(c->field), c->nx, c->ny, c->nz, c->n_sub, c->pitch,
+            c->d_bc_kind, c->d_bc_value, c->coef.L, sc);
+    else
+        persistent::k_shell_fill<float><<<grid, 256, 0, c->stream>>>(
+            reinterpret_cast<float*>(c->field), c->nx, c->ny, c->nz, c->n_sub, c->pitch,
+            c->d_bc_kind, c->d_bc_value, c->coef.L, nullptr);
+    c->launches += 1;
+    BFVM_CUDA(c, cudaGetLastError());
+    return BFVM_OK;
+}
+
 // One full step in rescale state p (0 <= p < period).  With renorm the z
 // sweep returns the field to plain values.
 bfvm_status launch_step(Ctx* c, int p, bool renorm)
@@ -464,22 +543,27 @@ bfvm_status launch_step(Ctx* c, int p, bool renorm)
     if (c->precision == 32) {
         st = launch_xyz<float, 0>(c, 0, c->coef.r32, c->coef.cr32, c->coef.c32);
         if (st != BFVM_OK) return st;
+        if ((st = launch_shell_fill(c, -1)) != BFVM_OK) return st;
         return launch_sources(c, 0, true);
     }
     if (c->variant == 0) {
         st = launch_xyz<double, 0>(c, 0, c->coef.r, c->coef.cr, c->coef.c);
         if (st != BFVM_OK) return st;
+        if ((st = launch_shell_fill(c, -1)) != BFVM_OK) return st;
         return launch_sources(c, 0, true);
     }
     if (renorm) st = launch_xyz<double, 2>(c, p, c->coef.r, c->coef.cr, c->coef.c);
     else st = launch_xyz<double, 1>(c, p, c->coef.r, c->coef.cr, c->coef.c);
     if (st != BFVM_OK) return st;
+    if ((st = launch_shell_fill(c, renorm ? -1 : p + 1)) != BFVM_OK) return st;
     return launch_sources(c, p + 1, renorm);
 }
 
 int sweep_kernel_count_per_step(const Ctx* c)
 {
-    return 3 + (c->src.n_entries > 0 ? 1 : 0);
+    bool any = false;
+    for (int s = 0; s < c->n_sub; ++s) any = any || c->bc_kind[s] == BFVM_BC_DIRICHLET;
+    return 3 + (any ? 1 : 0) + (c->src.n_entries > 0 ? 1 : 0);
 }
 
 // ---------------------------------------------------------------- layout
