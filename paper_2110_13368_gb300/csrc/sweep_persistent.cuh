@@ -1,37 +1,39 @@
-// Persistent, software-pipelined line sweep for the step itself (included by
-// sweeps.cu).
+// Persistent line sweep for the step itself (included by sweeps.cu).
 //
 // Work: the lines of one axis that need a solve.  On a Dirichlet substrate
 // a line whose other two coordinates touch the boundary lies entirely on the
 // Dirichlet shell; its values are overwritten after every sweep and no later
 // sweep reads them (the next sweep's lines through a shell voxel are either
 // shell lines themselves or have that voxel as an end, whose input is
-// replaced by the Dirichlet value).  Those lines are skipped here and the
-// shell is written once per step, after the z sweep, by k_shell_fill.  For
-// the same reason the two end outputs of a Dirichlet line are not
-// overwritten here.
+// replaced by the Dirichlet value).  Those lines are skipped and the shell is
+// written once per step, after the z sweep, by k_shell_fill.  For the same
+// reason the two end outputs of a Dirichlet line are not overwritten here.
 //
 // Each warp owns a column buffer of n_slots x 32 elements in shared memory
 // (one column per lane, one lane per line) and walks a static list of
-// 32-line blocks.  Per block:
-//   1. wait for the block's elements (copied in by cp.async while the
-//      previous block was being back-substituted);
-//   2. forward elimination in place, eight elements at a time with the next
-//      eight already in registers (in the rescaled FP64 form the chain is
-//      one dependent FMA per element);
-//   3. back substitution one group of G elements at a time; each finished
-//      group is written out and its slots immediately refilled with the next
-//      block's elements.
-// The slot of element k alternates between k and n_slots-1-k from block to
-// block (parity Q, a template parameter so that all shared-memory offsets
-// are immediates).  The back substitution frees slots from the end of the
-// line towards its start, which under the alternation are the slots of the
-// first elements of the next block, so the data needed first arrives first.
+// 32-line blocks b0, b1, ...  The slot of element k alternates between k and
+// n_slots-1-k from block to block (parity Q, a template parameter).  The back
+// substitution of block b frees slots from the end of the line towards its
+// start; under the alternation these are the slots of the *first* elements
+// of block b+1, so:
+//   - as soon as element k of block b has been back-substituted, element
+//     n-1-k of block b+1 is copied (cp.async) into its slot;
+//   - the forward elimination of block b+1 runs in the same loop, LAG
+//     elements behind, on data that has had LAG iterations to arrive.
+// The back substitution of b and the forward elimination of b+1 are two
+// independent FMA chains, so every warp keeps two FP64 operations in flight
+// while it needs no more shared memory than one block.  Only the first block
+// of a warp is eliminated on its own, and only its last one back-substituted
+// on its own.
+//
+// Shared-memory layout: element (slot, lane) sits at column
+// lane ^ ((slot mod G) * ROWS) of row `slot`, so that both a lane's own
+// column and the transposed copies of the x sweep hit every bank evenly.
 //
 // Global access: for the y and z sweeps adjacent lanes hold adjacent x, so
 // each per-element access of a warp is one coalesced row.  For the x sweep
 // the lanes hold 32 rows; copies and stores are transposed so that each
-// instruction moves (32/G) rows x G consecutive elements, i.e. whole 32-byte
+// instruction moves (32/G) rows x G consecutive elements = whole 32-byte
 // sectors (G = 32 bytes / element size).
 #pragma once
 
@@ -42,6 +44,7 @@ template <typename T>
 struct Groups {
     static constexpr int G = 32 / (int)sizeof(T);   // elements per 32-byte sector
     static constexpr int ROWS = 32 / G;             // rows per transposed instruction
+    static constexpr int LAG_GROUPS = sizeof(T) == 8 ? 6 : 4;
 };
 
 // Lines of one axis that need a solve, substrate by substrate: for a
@@ -69,8 +72,9 @@ __device__ __forceinline__ Line make_line(const SweepArgs<T>& A, const LineSet& 
                                           const int64_t* first_s, int64_t line)
 {
     Line L;
-    L.valid = line < S.first[S.n_sub];
-    if (!L.valid) line = S.first[S.n_sub] - 1;
+    const int64_t total = first_s[S.n_sub];
+    L.valid = line < total;
+    if (!L.valid) line = total - 1;
     int s = 0;
     while (s + 1 < S.n_sub && line >= first_s[s + 1]) ++s;
     L.s = s;
@@ -141,53 +145,34 @@ template <typename T, int AXIS, int MODE>
 struct Sweeper {
     static constexpr int G = Groups<T>::G;
     static constexpr int ROWS = Groups<T>::ROWS;
-    static constexpr int FC = 8;
+    static constexpr int LG = Groups<T>::LAG_GROUPS;
 
     const SweepArgs<T>& A;
-    const LineSet& S;
-    const int64_t* first_s;
     T* W;                 // this warp's column buffer
-    int64_t* rowbase;     // [2][32] line bases of the current / next block (x sweep)
     const T* fin;
     T* fout;
     int64_t stride;
     int n, ns, lane;
 
+    // slot of element k under parity Q; since n_slots is a multiple of G the
+    // slot's residue mod G is known from k mod G alone
     template <int Q>
-    __device__ __forceinline__ T* col(int k) const
+    __device__ __forceinline__ int slot(int k) const { return Q ? (ns - 1 - k) : k; }
+    template <int Q>
+    __device__ __forceinline__ static constexpr int res(int kmod) { return Q ? (G - 1 - kmod) : kmod; }
+    // element of lane/row l in slot s whose residue mod G is m
+    __device__ __forceinline__ T* at(int s, int l, int m) const
     {
-        return W + (Q ? (ns - 1 - k) : k) * 32;
+        return W + s * 32 + (l ^ (m * ROWS));
+    }
+    // this lane's element of the slot holding element k (k mod G == u)
+    template <int Q>
+    __device__ __forceinline__ T* own(int k, int u) const
+    {
+        return at(slot<Q>(k), lane, res<Q>(u));
     }
 
-    // copy elements [gG, gG+G) of block bb's lines into the slots of parity Q
-    template <int Q>
-    __device__ __forceinline__ void prefetch_group(const Line& ln, const int64_t* rb, int g) const
-    {
-        if (AXIS == 0) {
-            const int rsub = lane / G;
-            const int e = g * G + (lane % G);
-            if (e < n) {
-#pragma unroll
-                for (int t = 0; t < G; ++t) {
-                    const int r = t * ROWS + rsub;
-                    cp_async_elem(col<Q>(e) + r, fin + rb[r] + e);
-                }
-            }
-        } else {
-            const T* src = fin + ln.base + (int64_t)g * G * stride;
-#pragma unroll
-            for (int u = 0; u < G; ++u)
-                if (g * G + u < n) cp_async_elem(col<Q>(g * G + u) + lane, src + u * stride);
-        }
-    }
-
-    template <int Q>
-    __device__ __forceinline__ void prefetch_all(const Line& ln, const int64_t* rb) const
-    {
-        for (int g = 0; g < ns / G; ++g) prefetch_group<Q>(ln, rb, g);
-    }
-
-    __device__ __forceinline__ T step_fwd(const CoefRow<T>& C, T prev, T d, int k) const
+    __device__ __forceinline__ T fwd(const CoefRow<T>& C, T prev, T d, int k) const
     {
         if (MODE == 0) {
             if (sizeof(T) == 8) return fma(C.c, prev, d) * C.a[k];
@@ -197,113 +182,195 @@ struct Sweeper {
         return fma(C.a[k], prev, d);
     }
 
-    __device__ __forceinline__ T step_bwd(const CoefRow<T>& C, T x, T w, int k) const
+    __device__ __forceinline__ T bwd(const CoefRow<T>& C, T x, T w, int k) const
     {
         if (MODE == 0 && sizeof(T) == 4)
             return (T)comp_axpy((float)C.b[k], (float)C.b_lo[k], (float)x, (float)w);
         return fma(C.b[k], x, w);
     }
 
-    // Solve the current block (parity Q) and prefetch the next one into
-    // parity !Q.
-    template <int Q>
-    __device__ __forceinline__ void block(const Line& cur, const CoefRow<T>& C, bool has_next,
-                                          const Line& nxt, const int64_t* rb_cur,
-                                          const int64_t* rb_nxt) const
+    __device__ __forceinline__ T out_value(const CoefRow<T>& C, const Line& L, T x, int k) const
     {
-        // ---------------------------------------------------- forward
-        T prev;
-        {
-            T d0 = *(col<Q>(0) + lane);
-            if (cur.dir) d0 = (T)cur.end0;
-            prev = (MODE == 0) ? step_fwd(C, (T)0, d0, 0) : d0;   // fa[0] = 0
-            if (n > 1) *(col<Q>(0) + lane) = prev;
-            // elements 1 .. n-2
-            T buf[FC];
+        if (MODE == 2) return (T)(((double)x * C.o[k]) * L.inv_other);
+        return x;
+    }
+
+    // copy elements [gG, gG+G) of a block's lines into the slots of parity Q
+    template <int Q>
+    __device__ __forceinline__ void copy_group(const Line& ln, const int64_t* rb, int g) const
+    {
+        if (g * G >= n) return;
+        if (AXIS == 0) {
+            const int e = g * G + (lane % G);
+            if (e < n) {
+                const int s = slot<Q>(e);
+                const int m = res<Q>(lane % G);
 #pragma unroll
-            for (int u = 0; u < FC; ++u)
-                if (1 + u < n - 1) buf[u] = *(col<Q>(1 + u) + lane);
-            for (int k0 = 1; k0 < n - 1; k0 += FC) {
-                T nb[FC];
-#pragma unroll
-                for (int u = 0; u < FC; ++u)
-                    if (k0 + FC + u < n - 1) nb[u] = *(col<Q>(k0 + FC + u) + lane);
-#pragma unroll
-                for (int u = 0; u < FC; ++u) {
-                    const int k = k0 + u;
-                    if (k < n - 1) {
-                        prev = step_fwd(C, prev, buf[u], k);
-                        *(col<Q>(k) + lane) = prev;
-                    }
+                for (int t = 0; t < G; ++t) {
+                    const int r = t * ROWS + lane / G;
+                    cp_async_elem(at(s, r, m), fin + rb[r] + e);
                 }
-#pragma unroll
-                for (int u = 0; u < FC; ++u) buf[u] = nb[u];
             }
-            if (n > 1) {
-                T dl = *(col<Q>(n - 1) + lane);
-                if (cur.dir) dl = (T)cur.end1;
-                prev = step_fwd(C, prev, dl, n - 1);
-            }
-        }
-        // ---------------------------------------------------- backward
-        const int h_top = (n - 1) / G;
-        T x = prev;
-        T wv[G];
-#pragma unroll
-        for (int u = 0; u < G; ++u) {
-            const int k = h_top * G + u;
-            if (k < n - 1) wv[u] = *(col<Q>(k) + lane);
-        }
-        for (int h = h_top; h >= 0; --h) {
-            T wn[G];
+        } else {
+            const T* src = fin + ln.base + (int64_t)g * G * stride;
 #pragma unroll
             for (int u = 0; u < G; ++u)
-                if (h > 0) wn[u] = *(col<Q>((h - 1) * G + u) + lane);
-            T o[G];
+                if (g * G + u < n) cp_async_elem(own<Q>(g * G + u, u), src + u * stride);
+        }
+    }
+
+    // write out elements [hG, hG+G) of the current block (values in o[])
+    template <int Q>
+    __device__ __forceinline__ void store_group(const Line& L, const int64_t* rb, int h,
+                                                const T* o) const
+    {
+        if (AXIS == 0) {
+#pragma unroll
+            for (int u = 0; u < G; ++u)
+                if (h * G + u < n) *own<Q>(h * G + u, u) = o[u];
+            __syncwarp();
+            const int k = h * G + (lane % G);
+            if (k < n) {
+                const int s = slot<Q>(k);
+                const int m = res<Q>(lane % G);
+#pragma unroll
+                for (int t = 0; t < G; ++t) {
+                    const int r = t * ROWS + lane / G;
+                    if (rb[r] >= 0) fout[rb[r] + k] = *at(s, r, m);
+                }
+            }
+            __syncwarp();
+        } else if (L.valid) {
+            T* dst = fout + L.base + (int64_t)h * G * stride;
+#pragma unroll
+            for (int u = 0; u < G; ++u)
+                if (h * G + u < n) dst[u * stride] = o[u];
+        }
+    }
+
+    // forward elimination of a whole block on its own (first block of a warp)
+    template <int Q>
+    __device__ __forceinline__ T forward_solo(const Line& L, const CoefRow<T>& C) const
+    {
+        T prev = (T)0;
+        for (int g = 0; g * G < n; ++g) {
+            T d[G];
+#pragma unroll
+            for (int u = 0; u < G; ++u)
+                if (g * G + u < n) d[u] = *own<Q>(g * G + u, u);
+#pragma unroll
+            for (int u = 0; u < G; ++u) {
+                const int k = g * G + u;
+                if (k < n) {
+                    T dk = d[u];
+                    if (L.dir && k == 0) dk = (T)L.end0;
+                    if (L.dir && k == n - 1) dk = (T)L.end1;
+                    prev = (k == 0 && MODE != 0) ? dk : fwd(C, prev, dk, k);
+                    if (k < n - 1) *own<Q>(k, u) = prev;
+                }
+            }
+        }
+        return prev;
+    }
+
+    // back substitution of the last block of a warp on its own
+    template <int Q>
+    __device__ __forceinline__ void backward_solo(const Line& L, const CoefRow<T>& C, T x,
+                                                  const int64_t* rb) const
+    {
+        const int h_top = (n - 1) / G;
+        for (int h = h_top; h >= 0; --h) {
+            T w[G], o[G];
+#pragma unroll
+            for (int u = 0; u < G; ++u)
+                if (h * G + u < n - 1) w[u] = *own<Q>(h * G + u, u);
 #pragma unroll
             for (int u = G - 1; u >= 0; --u) {
                 const int k = h * G + u;
                 if (k < n) {
-                    if (k < n - 1) x = step_bwd(C, x, wv[u], k);
-                    if (MODE == 2) o[u] = (T)(((double)x * C.o[k]) * cur.inv_other);
-                    else o[u] = x;
+                    if (k < n - 1) x = bwd(C, x, w[u], k);
+                    o[u] = out_value(C, L, x, k);
                 }
             }
-            if (AXIS == 0) {
+            store_group<Q>(L, rb, h, o);
+        }
+    }
+
+    // Back substitution of block b (parity Q, value x = its last
+    // intermediate) interleaved with the forward elimination of block b+1
+    // (parity !Q), LAG = LG*G elements behind.  Returns b+1's last
+    // intermediate.
+    template <int Q>
+    __device__ __forceinline__ T interleaved(const Line& L, const CoefRow<T>& C, T x,
+                                             const Line& N, const CoefRow<T>& CN,
+                                             const int64_t* rb_cur, const int64_t* rb_nxt) const
+    {
+        constexpr int P = 1 - Q;
+        const int gcount = (n + G - 1) / G;
+        const int h_top = gcount - 1;
+        T prev = (T)0;
+        // iteration group jg: back substitution of group h = h_top - jg of
+        // block b, forward elimination of group g = jg - LG of block b+1.
+        // The group of block b+1 that lands in the slots freed by group h is
+        // e-group ns/G - 1 - h.
+        for (int jg = 0; jg < gcount + LG; ++jg) {
+            const int h = h_top - jg;
+            const int g = jg - LG;
+            // copies of e-groups <= g are complete once at most LG - 1 of the
+            // newest commit groups are still pending
+            if (g >= 0) {
+                cp_async_wait<LG - 1>();
+                __syncwarp();
+            }
+            T w[G], d[G], o[G];
+            if (h >= 0) {
 #pragma unroll
                 for (int u = 0; u < G; ++u)
-                    if (h * G + u < n) *(col<Q>(h * G + u) + lane) = o[u];
-                __syncwarp();
-                const int rsub = lane / G;
-                const int k = h * G + (lane % G);
-                if (k < n) {
+                    if (h * G + u < n - 1) w[u] = *own<Q>(h * G + u, u);
+            }
+            if (g >= 0 && g < gcount) {
 #pragma unroll
-                    for (int t = 0; t < G; ++t) {
-                        const int r = t * ROWS + rsub;
-                        if (rb_cur[r] >= 0) fout[rb_cur[r] + k] = *(col<Q>(k) + r);
+                for (int u = 0; u < G; ++u)
+                    if (g * G + u < n) d[u] = *own<P>(g * G + u, u);
+            }
+#pragma unroll
+            for (int u = 0; u < G; ++u) {
+                // one step of each chain
+                if (h >= 0) {
+                    const int k = h * G + (G - 1 - u);
+                    if (k < n) {
+                        if (k < n - 1) x = bwd(C, x, w[G - 1 - u], k);
+                        o[G - 1 - u] = out_value(C, L, x, k);
                     }
                 }
-                __syncwarp();
-            } else if (cur.valid) {
-                T* dst = fout + cur.base + (int64_t)h * G * stride;
-#pragma unroll
-                for (int u = 0; u < G; ++u)
-                    if (h * G + u < n) dst[u * stride] = o[u];
+                if (g >= 0 && g < gcount) {
+                    const int k = g * G + u;
+                    if (k < n) {
+                        T dk = d[u];
+                        if (N.dir && k == 0) dk = (T)N.end0;
+                        if (N.dir && k == n - 1) dk = (T)N.end1;
+                        prev = (k == 0 && MODE != 0) ? dk : fwd(CN, prev, dk, k);
+                        if (k < n - 1) *own<P>(k, u) = prev;
+                    }
+                }
             }
-            if (has_next) prefetch_group<1 - Q>(nxt, rb_nxt, ns / G - 1 - h);
-#pragma unroll
-            for (int u = 0; u < G; ++u) wv[u] = wn[u];
+            if (h >= 0) {
+                store_group<Q>(L, rb_cur, h, o);
+                copy_group<P>(N, rb_nxt, ns / G - 1 - h);
+            }
+            cp_async_commit();
         }
+        return prev;
     }
 };
 
 // Dynamic shared memory: [coefficients of all substrates for this axis]
-// [per-warp: column buffer, 2 x 32 row bases].
+// [MODE 2 output scales] [line-set prefix] [per warp: column buffer,
+// 2 x 32 row bases].
 template <typename T, int AXIS, int MODE>
 __global__ void __launch_bounds__(256, 1) k_sweep_persistent(SweepArgs<T> A, LineSet S,
                                                              int64_t n_blocks, int n_slots)
 {
-    constexpr int G = Groups<T>::G;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
@@ -312,13 +379,12 @@ __global__ void __launch_bounds__(256, 1) k_sweep_persistent(SweepArgs<T> A, Lin
     const int ns = n_slots;
     const int n_sub = A.n_sub;
 
-    // --- coefficient rows of this axis, all substrates
     const int ncoef = (MODE == 0 ? (sizeof(T) == 4 ? 4 : 2) : 2);
     T* cbase = reinterpret_cast<T*>(smem_raw);
     const int per_sub = ncoef * n;
-    size_t coef_bytes = (size_t)n_sub * per_sub * sizeof(T);
+    const size_t coef_bytes = (size_t)n_sub * per_sub * sizeof(T);
     double* obase = reinterpret_cast<double*>(smem_raw + ((coef_bytes + 15) & ~(size_t)15));
-    size_t o_bytes = (MODE == 2) ? (size_t)n_sub * n * sizeof(double) : 0;
+    const size_t o_bytes = (MODE == 2) ? (size_t)n_sub * n * sizeof(double) : 0;
     int64_t* first_s = reinterpret_cast<int64_t*>(
         reinterpret_cast<unsigned char*>(obase) + ((o_bytes + 15) & ~(size_t)15));
     unsigned char* warp_area = reinterpret_cast<unsigned char*>(first_s) +
@@ -352,11 +418,9 @@ __global__ void __launch_bounds__(256, 1) k_sweep_persistent(SweepArgs<T> A, Lin
     int64_t b = (int64_t)blockIdx.x * warps + warp;
     if (b >= n_blocks) return;
 
-    Sweeper<T, AXIS, MODE> sw{A, S, first_s, W, rowbase, A.in, A.field,
+    Sweeper<T, AXIS, MODE> sw{A, W, A.in, A.field,
                               AXIS == 0 ? 1 : (AXIS == 1 ? A.pitch : (int64_t)A.ny * A.pitch),
                               n, ns, lane};
-    (void)G;
-
     auto coef_row = [&](int s) {
         CoefRow<T> C;
         const T* r = cbase + (size_t)s * per_sub;
@@ -369,38 +433,44 @@ __global__ void __launch_bounds__(256, 1) k_sweep_persistent(SweepArgs<T> A, Lin
         C.c_lo = (MODE == 0 && sizeof(T) == 4) ? A.cvec_lo[s * 3 + AXIS] : (T)0;
         return C;
     };
+    // rowbase[0..31]: stores of the current block (-1 = padding row);
+    // rowbase[32..63]: copies of the block being loaded (padding rows read a
+    // valid row, their results are dropped)
+    int64_t* rb_cur = rowbase;
+    int64_t* rb_nxt = rowbase + 32;
 
-    int par = 0;
     Line cur = make_line<T, AXIS, MODE>(A, S, first_s, b * 32 + lane);
-    // x sweep: transposed copies need the row base of every line of the
-    // block (padding rows read a valid row; their results are dropped)
-    rowbase[32 + lane] = cur.base;
+    rb_nxt[lane] = cur.base;
+    rb_cur[lane] = cur.valid ? cur.base : -1;
     __syncwarp();
-    sw.template prefetch_all<0>(cur, rowbase + 32);
+    for (int g = 0; g * sw.G < n; ++g) sw.template copy_group<0>(cur, rb_nxt, g);
     cp_async_commit();
+    cp_async_wait<0>();
+    __syncwarp();
+    CoefRow<T> C = coef_row(cur.s);
+    T x = sw.template forward_solo<0>(cur, C);
+    int par = 0;
     for (;;) {
         const int64_t nb = b + tw;
-        const bool has_next = nb < n_blocks;
-        Line nxt = has_next ? make_line<T, AXIS, MODE>(A, S, first_s, nb * 32 + lane) : cur;
-        // row bases: [0..31] current block's stores (-1 = padding row),
-        // [32..63] next block's copies
-        if (AXIS == 0) {
-            __syncwarp();
-            rowbase[lane] = cur.valid ? cur.base : -1;
-            rowbase[32 + lane] = nxt.base;
-            __syncwarp();
+        if (nb >= n_blocks) {
+            if (par == 0) sw.template backward_solo<0>(cur, C, x, rb_cur);
+            else sw.template backward_solo<1>(cur, C, x, rb_cur);
+            break;
         }
+        Line nxt = make_line<T, AXIS, MODE>(A, S, first_s, nb * 32 + lane);
+        CoefRow<T> CN = coef_row(nxt.s);
+        __syncwarp();
+        rb_nxt[lane] = nxt.base;
+        __syncwarp();
+        if (par == 0) x = sw.template interleaved<0>(cur, C, x, nxt, CN, rb_cur, rb_nxt);
+        else x = sw.template interleaved<1>(cur, C, x, nxt, CN, rb_cur, rb_nxt);
         cp_async_wait<0>();
         __syncwarp();
-        const CoefRow<T> C = coef_row(cur.s);
-        if (par == 0)
-            sw.template block<0>(cur, C, has_next, nxt, rowbase, rowbase + 32);
-        else
-            sw.template block<1>(cur, C, has_next, nxt, rowbase, rowbase + 32);
-        cp_async_commit();
-        if (!has_next) break;
+        rb_cur[lane] = nxt.valid ? nxt.base : -1;
+        __syncwarp();
         b = nb;
         cur = nxt;
+        C = CN;
         par ^= 1;
     }
 }
