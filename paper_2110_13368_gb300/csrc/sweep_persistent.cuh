@@ -296,6 +296,67 @@ struct Sweeper {
         }
     }
 
+    // One iteration group of the interleaved loop when both groups are
+    // complete interior groups (no line end, no ragged tail): straight-line
+    // code with per-group row pointers and immediate offsets.
+    template <int Q>
+    __device__ __forceinline__ void fast_group(const Line& L, const CoefRow<T>& C, T& x,
+                                               const Line& N, const CoefRow<T>& CN, T& prev,
+                                               int h, int g, const int* lx) const
+    {
+        constexpr int P = 1 - Q;
+        T* rb = W + (Q ? (ns - 1 - h * G) : h * G) * 32;    // row of k = hG (block b)
+        T* rf = W + (P ? (ns - 1 - g * G) : g * G) * 32;    // row of k = gG (block b+1)
+        T w[G], d[G], bb[G], aa[G], bl[G], al[G], o[G], f[G];
+#pragma unroll
+        for (int u = 0; u < G; ++u) {
+            w[u] = rb[(Q ? -u : u) * 32 + lx[res<Q>(u)]];
+            d[u] = rf[(P ? -u : u) * 32 + lx[res<P>(u)]];
+            bb[u] = C.b[h * G + u];
+            aa[u] = CN.a[g * G + u];
+            if (MODE == 0 && sizeof(T) == 4) {
+                bl[u] = C.b_lo[h * G + u];
+                al[u] = CN.a_lo[g * G + u];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < G; ++u) {
+            const int ub = G - 1 - u;
+            if (MODE == 0 && sizeof(T) == 4) {
+                x = (T)comp_axpy((float)bb[ub], (float)bl[ub], (float)x, (float)w[ub]);
+                float t = comp_axpy((float)CN.c, (float)CN.c_lo, (float)prev, (float)d[u]);
+                prev = (T)__fmaf_rn(t, (float)aa[u], __fmul_rn(t, (float)al[u]));
+            } else if (MODE == 0) {
+                x = fma(bb[ub], x, w[ub]);
+                prev = fma(CN.c, prev, d[u]) * aa[u];
+            } else {
+                x = fma(bb[ub], x, w[ub]);
+                prev = fma(aa[u], prev, d[u]);
+            }
+            o[ub] = (MODE == 2) ? (T)(((double)x * C.o[h * G + ub]) * L.inv_other) : x;
+            f[u] = prev;
+        }
+#pragma unroll
+        for (int u = 0; u < G; ++u) rf[(P ? -u : u) * 32 + lx[res<P>(u)]] = f[u];
+        if (AXIS != 0) {
+            if (L.valid) {
+                T* p = fout + L.base + (int64_t)h * G * stride;
+#pragma unroll
+                for (int u = 0; u < G; ++u) {
+                    *p = o[u];
+                    p += stride;
+                }
+            }
+            const T* src = fin + N.base + (int64_t)(ns / G - 1 - h) * G * stride;
+            T* rdst = W + (P ? (ns - 1 - (ns / G - 1 - h) * G) : (ns / G - 1 - h) * G) * 32;
+#pragma unroll
+            for (int u = 0; u < G; ++u) {
+                cp_async_elem(rdst + (P ? -u : u) * 32 + lx[res<P>(u)], src);
+                src += stride;
+            }
+        }
+    }
+
     // Back substitution of block b (parity Q, value x = its last
     // intermediate) interleaved with the forward elimination of block b+1
     // (parity !Q), LAG = LG*G elements behind.  Returns b+1's last
@@ -309,6 +370,9 @@ struct Sweeper {
         const int gcount = (n + G - 1) / G;
         const int h_top = gcount - 1;
         T prev = (T)0;
+        int lx[G];
+#pragma unroll
+        for (int m = 0; m < G; ++m) lx[m] = lane ^ (m * ROWS);
         // iteration group jg: back substitution of group h = h_top - jg of
         // block b, forward elimination of group g = jg - LG of block b+1.
         // The group of block b+1 that lands in the slots freed by group h is
@@ -321,6 +385,15 @@ struct Sweeper {
             if (g >= 0) {
                 cp_async_wait<LG - 1>();
                 __syncwarp();
+            }
+            // complete interior groups: h below the top group (which holds
+            // element n-1 and the ragged tail), g neither the first nor the
+            // last group of block b+1
+            if (AXIS != 0 && h >= 0 && h < h_top && g >= 1 && g < gcount - 1 &&
+                (h + 1) * G <= n - 1 && (g + 1) * G <= n - 1 && (ns / G - h) * G <= n) {
+                fast_group<Q>(L, C, x, N, CN, prev, h, g, lx);
+                cp_async_commit();
+                continue;
             }
             T w[G], d[G], o[G];
             if (h >= 0) {
