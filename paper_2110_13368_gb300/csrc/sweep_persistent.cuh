@@ -296,64 +296,137 @@ struct Sweeper {
         }
     }
 
-    // One iteration group of the interleaved loop when both groups are
-    // complete interior groups (no line end, no ragged tail): straight-line
-    // code with per-group row pointers and immediate offsets.
+    // Iteration groups jg in [j0, j1) of the interleaved loop in which both
+    // groups are complete interior groups (no line end, no ragged tail) and
+    // the copied group is complete: straight-line code with running
+    // pointers, so every per-element offset is an immediate.
     template <int Q>
-    __device__ __forceinline__ void fast_group(const Line& L, const CoefRow<T>& C, T& x,
-                                               const Line& N, const CoefRow<T>& CN, T& prev,
-                                               int h, int g, const int* lx) const
+    __device__ __forceinline__ void fast_run(const Line& L, const CoefRow<T>& C, T& x,
+                                             const Line& N, const CoefRow<T>& CN, T& prev,
+                                             int j0, int j1, int h_top,
+                                             const int64_t* rb_cur, const int64_t* rb_nxt) const
     {
         constexpr int P = 1 - Q;
-        T* rb = W + (Q ? (ns - 1 - h * G) : h * G) * 32;    // row of k = hG (block b)
-        T* rf = W + (P ? (ns - 1 - g * G) : g * G) * 32;    // row of k = gG (block b+1)
-        T w[G], d[G], bb[G], aa[G], bl[G], al[G], o[G], f[G];
+        constexpr int SW = (AXIS == 0);          // swizzled columns (x sweep only)
+        constexpr int RS = 32;                    // elements per slot row
+        if (j0 >= j1) return;
+        int lx[G];
 #pragma unroll
-        for (int u = 0; u < G; ++u) {
-            w[u] = rb[(Q ? -u : u) * 32 + lx[res<Q>(u)]];
-            d[u] = rf[(P ? -u : u) * 32 + lx[res<P>(u)]];
-            bb[u] = C.b[h * G + u];
-            aa[u] = CN.a[g * G + u];
-            if (MODE == 0 && sizeof(T) == 4) {
-                bl[u] = C.b_lo[h * G + u];
-                al[u] = CN.a_lo[g * G + u];
+        for (int m = 0; m < G; ++m) lx[m] = SW ? (lane ^ (m * ROWS)) : lane;
+        // group h of block b occupies rows hb .. hb+G-1 (Q = 0, ascending k)
+        // or ns-1-hb-(G-1) .. ns-1-hb (Q = 1, k descending in rows)
+        int h = h_top - j0;
+        int g = j0 - LG;
+        T* rbw = W + (Q ? (ns - 1 - h * G) : h * G) * RS;   // row of k = hG
+        T* rfd = W + (P ? (ns - 1 - g * G) : g * G) * RS;   // row of k = gG (block b+1)
+        const T* cb = C.b + h * G;
+        const T* ca = CN.a + g * G;
+        const T* cbl = C.b_lo + h * G;
+        const T* cal = CN.a_lo + g * G;
+        const double* co = C.o + h * G;
+        const int64_t sG = (int64_t)G * stride;
+        T* pout = fout + L.base + (int64_t)h * G * stride;
+        const T* psrc = fin + N.base + (int64_t)(ns / G - 1 - h) * sG;
+        // x sweep: this lane's transposed rows and element offset
+        int64_t rcur[G], rnxt[G];
+        if (AXIS == 0) {
+#pragma unroll
+            for (int t = 0; t < G; ++t) {
+                rcur[t] = rb_cur[t * ROWS + lane / G];
+                rnxt[t] = rb_nxt[t * ROWS + lane / G];
             }
         }
-#pragma unroll
-        for (int u = 0; u < G; ++u) {
-            const int ub = G - 1 - u;
-            if (MODE == 0 && sizeof(T) == 4) {
-                x = (T)comp_axpy((float)bb[ub], (float)bl[ub], (float)x, (float)w[ub]);
-                float t = comp_axpy((float)CN.c, (float)CN.c_lo, (float)prev, (float)d[u]);
-                prev = (T)__fmaf_rn(t, (float)aa[u], __fmul_rn(t, (float)al[u]));
-            } else if (MODE == 0) {
-                x = fma(bb[ub], x, w[ub]);
-                prev = fma(CN.c, prev, d[u]) * aa[u];
-            } else {
-                x = fma(bb[ub], x, w[ub]);
-                prev = fma(aa[u], prev, d[u]);
-            }
-            o[ub] = (MODE == 2) ? (T)(((double)x * C.o[h * G + ub]) * L.inv_other) : x;
-            f[u] = prev;
-        }
-#pragma unroll
-        for (int u = 0; u < G; ++u) rf[(P ? -u : u) * 32 + lx[res<P>(u)]] = f[u];
-        if (AXIS != 0) {
-            if (L.valid) {
-                T* p = fout + L.base + (int64_t)h * G * stride;
-#pragma unroll
-                for (int u = 0; u < G; ++u) {
-                    *p = o[u];
-                    p += stride;
-                }
-            }
-            const T* src = fin + N.base + (int64_t)(ns / G - 1 - h) * G * stride;
-            T* rdst = W + (P ? (ns - 1 - (ns / G - 1 - h) * G) : (ns / G - 1 - h) * G) * 32;
+        const int um = lane % G;
+        for (int jg = j0; jg < j1; ++jg) {
+            cp_async_wait<LG - 1>();
+            __syncwarp();
+            T w[G], d[G], bb[G], aa[G], bl[G], al[G], o[G], f[G];
 #pragma unroll
             for (int u = 0; u < G; ++u) {
-                cp_async_elem(rdst + (P ? -u : u) * 32 + lx[res<P>(u)], src);
-                src += stride;
+                w[u] = rbw[(Q ? -u : u) * RS + lx[res<Q>(u)]];
+                d[u] = rfd[(P ? -u : u) * RS + lx[res<P>(u)]];
+                bb[u] = cb[u];
+                aa[u] = ca[u];
+                if (MODE == 0 && sizeof(T) == 4) {
+                    bl[u] = cbl[u];
+                    al[u] = cal[u];
+                }
             }
+#pragma unroll
+            for (int u = 0; u < G; ++u) {
+                const int ub = G - 1 - u;
+                if (MODE == 0 && sizeof(T) == 4) {
+                    x = (T)comp_axpy((float)bb[ub], (float)bl[ub], (float)x, (float)w[ub]);
+                    float t = comp_axpy((float)CN.c, (float)CN.c_lo, (float)prev, (float)d[u]);
+                    prev = (T)__fmaf_rn(t, (float)aa[u], __fmul_rn(t, (float)al[u]));
+                } else if (MODE == 0) {
+                    x = fma(bb[ub], x, w[ub]);
+                    prev = fma(CN.c, prev, d[u]) * aa[u];
+                } else {
+                    x = fma(bb[ub], x, w[ub]);
+                    prev = fma(aa[u], prev, d[u]);
+                }
+                o[ub] = (MODE == 2) ? (T)(((double)x * co[ub]) * L.inv_other) : x;
+                f[u] = prev;
+            }
+#pragma unroll
+            for (int u = 0; u < G; ++u) rfd[(P ? -u : u) * RS + lx[res<P>(u)]] = f[u];
+            // element u of the copied group lands in row hG + (G-1-u) (Q = 0)
+            // or ns-1-hG-(G-1-u) (Q = 1), i.e. rbw + (Q ? u-(G-1) : (G-1)-u) rows
+            if (AXIS != 0) {
+                if (L.valid) {
+                    T* p = pout;
+#pragma unroll
+                    for (int u = 0; u < G; ++u) {
+                        *p = o[u];
+                        p += stride;
+                    }
+                }
+                const T* q = psrc;
+#pragma unroll
+                for (int u = 0; u < G; ++u) {
+                    const int rowoff = Q ? (u - (G - 1)) : ((G - 1) - u);
+                    cp_async_elem(rbw + rowoff * RS + lx[res<P>(u)], q);
+                    q += stride;
+                }
+            } else {
+#pragma unroll
+                for (int u = 0; u < G; ++u) rbw[(Q ? -u : u) * RS + lx[res<Q>(u)]] = o[u];
+                __syncwarp();
+                // transposed store: element k = hG + um of rows t*ROWS + lane/G
+                const int ks = h * G + um;
+                const T* srow = rbw + (Q ? -um : um) * RS;
+#pragma unroll
+                for (int t = 0; t < G; ++t) {
+                    const int r = t * ROWS + lane / G;
+                    const T v = srow[r ^ ((Q ? (G - 1 - um) : um) * ROWS)];
+                    if (rcur[t] >= 0) fout[rcur[t] + ks] = v;
+                }
+                __syncwarp();
+                // transposed copy of e-group eg = ns/G-1-h into the same rows
+                const int e = (ns / G - 1 - h) * G + um;
+                const int rowoff = Q ? (um - (G - 1)) : ((G - 1) - um);
+                T* drow = rbw + rowoff * RS;
+                const int mres = Q ? um : (G - 1 - um);   // residue of that row
+#pragma unroll
+                for (int t = 0; t < G; ++t) {
+                    const int r = t * ROWS + lane / G;
+                    cp_async_elem(drow + (r ^ (mres * ROWS)), fin + rnxt[t] + e);
+                }
+            }
+            cp_async_commit();
+            // advance: h decreases, g increases
+            --h;
+            ++g;
+            rbw += (Q ? G : -G) * RS;
+            rfd += (P ? -G : G) * RS;
+            cb -= G;
+            ca += G;
+            cbl -= G;
+            cal += G;
+            co -= G;
+            pout -= sG;
+            psrc += sG;
         }
     }
 
@@ -370,9 +443,20 @@ struct Sweeper {
         const int gcount = (n + G - 1) / G;
         const int h_top = gcount - 1;
         T prev = (T)0;
-        int lx[G];
-#pragma unroll
-        for (int m = 0; m < G; ++m) lx[m] = lane ^ (m * ROWS);
+        // interior range of iteration groups for the straight-line loop:
+        // h = h_top - jg in [0, h_top) with (h+1)G <= n-1, g = jg - LG in
+        // [1, gcount-1) with (g+1)G <= n-1, copied e-group complete
+        int j_fast0 = LG + 1;
+        int j_fast1 = gcount + LG;
+        {
+            const int hmax = (n - 1) / G - 1;           // (h+1)G <= n-1
+            const int gmax = (n - 1) / G - 1;           // (g+1)G <= n-1
+            const int hmin = ns / G - n / G;            // (ns/G - h) G <= n
+            // jg >= h_top - hmax, jg <= h_top - hmin, jg <= gmax + LG
+            j_fast0 = max(j_fast0, h_top - min(hmax, h_top - 1));
+            j_fast1 = min(j_fast1, min(h_top - max(hmin, 0), gmax + LG) + 1);
+            if (j_fast0 >= j_fast1) j_fast0 = j_fast1 = -1;
+        }
         // iteration group jg: back substitution of group h = h_top - jg of
         // block b, forward elimination of group g = jg - LG of block b+1.
         // The group of block b+1 that lands in the slots freed by group h is
@@ -386,13 +470,9 @@ struct Sweeper {
                 cp_async_wait<LG - 1>();
                 __syncwarp();
             }
-            // complete interior groups: h below the top group (which holds
-            // element n-1 and the ragged tail), g neither the first nor the
-            // last group of block b+1
-            if (AXIS != 0 && h >= 0 && h < h_top && g >= 1 && g < gcount - 1 &&
-                (h + 1) * G <= n - 1 && (g + 1) * G <= n - 1 && (ns / G - h) * G <= n) {
-                fast_group<Q>(L, C, x, N, CN, prev, h, g, lx);
-                cp_async_commit();
+            if (jg == j_fast0) {
+                fast_run<Q>(L, C, x, N, CN, prev, j_fast0, j_fast1, h_top, rb_cur, rb_nxt);
+                jg = j_fast1 - 1;
                 continue;
             }
             T w[G], d[G], o[G];
