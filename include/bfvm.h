@@ -211,12 +211,31 @@ bfvm_status bfvm_kernel_times(bfvm_ctx* ctx, double* ms, int64_t* counts, int32_
  * the single-context calls.  All members must use the same precision and
  * must not be stepped individually while the batch exists.
  */
+/*
+ * Batched form (an extension: the paper motivates many-run workflows such
+ * as model calibration and parameter sweeps in "Introduction and
+ * Motivation").  Create a batch over n_members existing contexts:
+ *   members[i]  contexts of one device, all of the same precision, each at a
+ *               rescale period boundary (fresh, or right after
+ *               bfvm_set_density) and not recording; the batch keeps
+ *               pointers to them, so they must outlive it
+ *   cuda_stream stream of the batched launches
+ * Errors: BFVM_EINVAL (NULL pointers, n_members < 1), BFVM_ESTATE (mixed
+ * precision, a member mid-period or recording), BFVM_ENOMEM / BFVM_ECUDA.
+ */
 bfvm_status bfvm_batch_create(bfvm_batch** out, bfvm_ctx* const* members,
                               int32_t n_members, void* cuda_stream);
+/* n_steps full steps of every member; asynchronous on the batch stream.
+ * FP64 members share the shortest rescale period of the batch. */
 bfvm_status bfvm_batch_step(bfvm_batch* batch, int32_t n_steps);
+/* Block until the batch stream is idle; reports device-side errors. */
 bfvm_status bfvm_batch_sync(bfvm_batch* batch);
+/* Free the batch (the members stay valid). */
 void bfvm_batch_destroy(bfvm_batch* batch);
 const char* bfvm_batch_last_error(const bfvm_batch* batch);
+/* info[8]: members, precision, rescaled (0/1), period, tasks per step over
+ * the three sweeps, source entries, launches issued, current rescale state. */
+bfvm_status bfvm_batch_info(const bfvm_batch* batch, int64_t* info);
 
 #ifdef __cplusplus
 }

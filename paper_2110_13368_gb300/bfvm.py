@@ -34,7 +34,7 @@ EXPORTED = ["bfvm_create", "bfvm_destroy", "bfvm_set_density", "bfvm_get_density
             "bfvm_last_error", "bfvm_status_string", "bfvm_get_info", "bfvm_set_option",
             "bfvm_kernel_times",
             "bfvm_batch_create", "bfvm_batch_step", "bfvm_batch_sync", "bfvm_batch_destroy",
-            "bfvm_batch_last_error"]
+            "bfvm_batch_last_error", "bfvm_batch_info"]
 
 
 class BfvmError(RuntimeError):
@@ -89,6 +89,8 @@ def load_library(path: Optional[str] = None):
         lib.bfvm_batch_destroy.restype = None
         lib.bfvm_batch_last_error.argtypes = [_vp]
         lib.bfvm_batch_last_error.restype = ctypes.c_char_p
+        lib.bfvm_batch_info.argtypes = [_vp, ctypes.POINTER(_i64)]
+        lib.bfvm_batch_info.restype = ctypes.c_int
         for name in ("bfvm_create", "bfvm_set_density", "bfvm_get_density", "bfvm_set_cells",
                      "bfvm_step", "bfvm_sync", "bfvm_record", "bfvm_backward", "bfvm_get_info",
                      "bfvm_set_option", "bfvm_kernel_times", "bfvm_batch_create", "bfvm_batch_step",
@@ -244,7 +246,8 @@ def bfvm_batch_create(handles, stream=None):
     b = _vp()
     st = lib.bfvm_batch_create(ctypes.byref(b), arr, len(handles), _stream_handle(stream))
     if st != BFVM_OK:
-        raise BfvmError(st, "bfvm_batch_create failed: " + bfvm_last_error(None))
+        raise BfvmError(st, "bfvm_batch_create failed (mixed precision, a member mid-period "
+                            "or recording, or out of memory)")
     return b
 
 
@@ -258,6 +261,44 @@ def bfvm_batch_sync(b):
 
 def bfvm_batch_destroy(b):
     load_library().bfvm_batch_destroy(b)
+
+
+def bfvm_batch_info(b):
+    info = (_i64 * 8)()
+    _check(load_library().bfvm_batch_info(b, info), b, batch=True)
+    keys = ["members", "precision", "rescaled", "period", "tasks_per_step", "source_entries",
+            "launches", "state"]
+    return {k: int(info[i]) for i, k in enumerate(keys)}
+
+
+class Batch:
+    """Many Sim members advanced together by the batched launches."""
+
+    def __init__(self, sims, stream=None):
+        import torch
+        self.sims = list(sims)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.handle = bfvm_batch_create([s.handle for s in self.sims], self.stream)
+
+    def step(self, n=1):
+        bfvm_batch_step(self.handle, n)
+
+    def sync(self):
+        bfvm_batch_sync(self.handle)
+
+    def info(self):
+        return bfvm_batch_info(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None) is not None:
+            bfvm_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # ---------------------------------------------------------- convenience

@@ -220,6 +220,35 @@ struct bfvm_ctx {
 };
 
 namespace bfvm {
+
+// Batched form: many contexts advanced by one launch per phase (batch.cu
+// holds the ABI, sweeps.cu the kernels).
+struct BatchImpl {
+    std::vector<Ctx*> members;
+    cudaStream_t stream = nullptr;
+    int precision = 64;
+    bool rescaled = false;
+    int period = 1;
+    int p = 0;                      // common rescale state of all members
+    int max_n = 1;                  // longest line of any member and axis
+    void* d_desc = nullptr;         // device array of per-member descriptors
+    int2* d_tasks[3] = {nullptr, nullptr, nullptr};   // (member, 32-line block)
+    int64_t n_tasks[3] = {0, 0, 0};
+    int64_t* d_entry_prefix = nullptr;  // [members + 1] source entries
+    int64_t n_entries = 0;
+    cudaGraphExec_t graph = nullptr;
+    int graph_len = 0;
+    int64_t launches = 0;
+    std::string err;
+};
+
+bfvm_status batch_build(BatchImpl* b);
+bfvm_status batch_launch_step(BatchImpl* b, int p, bool renorm);
+void batch_free(BatchImpl* b);
+
+}  // namespace bfvm
+
+namespace bfvm {
 // plain FP64 sweep along one axis, in -> out (sweeps.cu); dir_mode 0 step,
 // 1 raw replay, 2 adjoint
 bfvm_status launch_sweep_plain64(Ctx* c, int axis, const double* in, double* out,

@@ -115,21 +115,6 @@ __device__ __forceinline__ Line make_line(const SweepArgs<T>& A, const LineSet& 
     return L;
 }
 
-// fl(a*u + v) for an FP32 coefficient held as a = hi + lo, with one final
-// rounding of an almost exact value: the product error comes from an FMA
-// (TwoProduct) and the sum error from Knuth's TwoSum; explicit _rn
-// intrinsics keep the compiler from contracting them.
-__device__ __forceinline__ float comp_axpy(float a_hi, float a_lo, float u, float v)
-{
-    float p = __fmul_rn(a_hi, u);
-    float pe = __fmaf_rn(a_hi, u, -p);
-    float s = __fadd_rn(p, v);
-    float z = __fsub_rn(s, p);
-    float se = __fadd_rn(__fsub_rn(p, __fsub_rn(s, z)), __fsub_rn(v, z));
-    float corr = __fmaf_rn(a_lo, u, __fadd_rn(pe, se));
-    return __fadd_rn(s, corr);
-}
-
 // Shared-memory coefficient rows of one substrate (this axis only).
 template <typename T>
 struct CoefRow {

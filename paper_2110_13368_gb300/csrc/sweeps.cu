@@ -95,14 +95,28 @@ struct SweepArgs {
 //        replay of a step for the adjoint needs it).
 // DIR 2: shell of the input zeroed, raw solution kept (the adjoint solve:
 //        the Dirichlet projection's Jacobian is zero on the shell).
-template <typename T, int AXIS, int MODE, int DIR, bool SMEM>
-__global__ void __launch_bounds__(256) k_sweep(SweepArgs<T> A)
+// fl(a*u + v) for an FP32 coefficient held as a = hi + lo, with one final
+// rounding of an almost exact value: the product error comes from an FMA
+// (TwoProduct) and the sum error from Knuth's TwoSum; explicit _rn
+// intrinsics keep the compiler from contracting them.
+__device__ __forceinline__ float comp_axpy(float a_hi, float a_lo, float u, float v)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int lane = threadIdx.x & 31;
-    const int warp = threadIdx.x >> 5;
-    const int64_t line = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (line >= A.n_lines) return;
+    float p = __fmul_rn(a_hi, u);
+    float pe = __fmaf_rn(a_hi, u, -p);
+    float s = __fadd_rn(p, v);
+    float z = __fsub_rn(s, p);
+    float se = __fadd_rn(__fsub_rn(p, __fsub_rn(s, z)), __fsub_rn(v, z));
+    float corr = __fmaf_rn(a_lo, u, __fadd_rn(pe, se));
+    return __fadd_rn(s, corr);
+}
+
+// One line per thread: the generic sweep used by the adjoint passes, by the
+// batched form and for lines too long for the persistent kernel.  `wsm` is
+// this warp's shared column buffer (32 x n elements) when SMEM.
+template <typename T, int AXIS, int MODE, int DIR, bool SMEM>
+__device__ __forceinline__ void sweep_one_line(const SweepArgs<T>& A, int64_t line, int lane,
+                                               T* wsm)
+{
 
     const int n = A.n;
     int s, ox, oy, oz;   // substrate and the two fixed coordinates (third = -1)
@@ -174,7 +188,7 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs<T> A)
     T* w;
     int64_t wstride;
     if (SMEM) {
-        w = reinterpret_cast<T*>(smem_raw) + (int64_t)warp * 32 * n + lane;
+        w = wsm + lane;
         wstride = 32;
         const int gs = (n + kGroups - 1) / kGroups;
         for (int g = 0; g < kGroups; ++g) {
@@ -227,8 +241,8 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs<T> A)
             for (int k = k0; k < k1; ++k) {
                 T d = w[k * wstride];
                 if (all_in || (dir && (k == 0 || k == n - 1))) d = end_in(k);
-                T t = fma(c_lo, prev, fma(c, prev, d));
-                prev = fma(t, r[k], t * r_lo[k]);
+                float t = comp_axpy((float)c, (float)c_lo, (float)prev, (float)d);
+                prev = (T)__fmaf_rn(t, (float)r[k], __fmul_rn(t, (float)r_lo[k]));
                 w[k * wstride] = prev;
             }
         }
@@ -272,7 +286,7 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs<T> A)
         const T* __restrict__ cr = A.cr + row + A.axis_off;
         const T* __restrict__ cr_lo = A.cr_lo + row + A.axis_off;
         for (int k = n - 2; k >= 0; --k) {
-            x = fma(cr_lo[k], x, fma(cr[k], x, w[k * wstride]));
+            x = (T)comp_axpy((float)cr[k], (float)cr_lo[k], (float)x, (float)w[k * wstride]);
             emit(k, x);
         }
     } else {
@@ -282,6 +296,18 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs<T> A)
             emit(k, x);
         }
     }
+}
+
+template <typename T, int AXIS, int MODE, int DIR, bool SMEM>
+__global__ void __launch_bounds__(256) k_sweep(SweepArgs<T> A)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int64_t line = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (line >= A.n_lines) return;
+    T* wsm = SMEM ? reinterpret_cast<T*>(smem_raw) + (int64_t)warp * 32 * A.n : nullptr;
+    sweep_one_line<T, AXIS, MODE, DIR, SMEM>(A, line, lane, wsm);
 }
 
 // rho <- alpha rho + beta over the occupied voxels (cell sources and sinks,
@@ -612,6 +638,221 @@ bfvm_status launch_unscale_copy(Ctx* c, void* out_dev, int p)
     c->launches += 1;
     BFVM_CUDA(c, cudaGetLastError());
     return BFVM_OK;
+}
+
+}  // namespace bfvm
+
+// ================================================================ batched
+// Many independent simulations of uneven sizes: one launch per phase walks a
+// flat list of (member, 32-line block) tasks, one warp per task, each warp
+// using the generic one-line-per-thread sweep on that member's descriptor.
+namespace bfvm {
+namespace {
+
+template <typename T>
+struct BatchDesc {
+    SweepArgs<T> ax[3];      // state-0 arguments of the three axes
+    int64_t per_state;       // n_sub * L: stride of the rescaled tables
+    T* field;
+    int64_t n_entries;
+    const int64_t* off;
+    const double* alpha;
+    const double* beta;
+    const int32_t* vox;
+    const int32_t* sub;
+    int nx, ny;
+    int64_t L;
+    const double* sc;        // scale tables (state 0)
+};
+
+template <typename T, int AXIS, int MODE>
+__global__ void __launch_bounds__(256) k_batch_sweep(const BatchDesc<T>* __restrict__ D,
+                                                     const int2* __restrict__ tasks,
+                                                     int64_t n_tasks, int p, int max_n)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int64_t task = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
+    if (task >= n_tasks) return;
+    const int2 t = tasks[task];
+    SweepArgs<T> A = D[t.x].ax[AXIS];
+    if (MODE >= 1) {
+        const int64_t o = (int64_t)p * D[t.x].per_state;
+        A.fa += o;
+        A.fb += o;
+        A.sc_p += o;
+        A.sc_p1 += o;
+        A.isc_p1 += o;
+    }
+    const int64_t line = (int64_t)t.y * 32 + lane;
+    if (line >= A.n_lines) return;
+    T* wsm = reinterpret_cast<T*>(smem_raw) + (int64_t)warp * 32 * max_n;
+    sweep_one_line<T, AXIS, MODE, 0, true>(A, line, lane, wsm);
+}
+
+template <typename T, bool SCALED>
+__global__ void k_batch_sources(const BatchDesc<T>* __restrict__ D,
+                                const int64_t* __restrict__ prefix, int n_members,
+                                int64_t total, int p_next)
+{
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= total) return;
+    int lo = 0, hi = n_members;   // prefix[lo] <= e < prefix[hi]
+    while (hi - lo > 1) {
+        int mid = (lo + hi) / 2;
+        if (prefix[mid] <= e) lo = mid;
+        else hi = mid;
+    }
+    const BatchDesc<T>& d = D[lo];
+    const int64_t i = e - prefix[lo];
+    double b = d.beta[i];
+    if (SCALED) {
+        int32_t vv = d.vox[i];
+        int x = vv % d.nx;
+        int y = (vv / d.nx) % d.ny;
+        int z = vv / (d.nx * d.ny);
+        const double* q = d.sc + (int64_t)p_next * d.per_state + (int64_t)d.sub[i] * d.L;
+        b *= q[x] * q[d.nx + y] * q[d.nx + d.ny + z];
+    }
+    T* f = d.field + d.off[i];
+    *f = (T)fma(d.alpha[i], (double)*f, b);
+}
+
+template <typename T>
+bfvm_status batch_build_t(BatchImpl* b)
+{
+    const int M = (int)b->members.size();
+    std::vector<BatchDesc<T>> desc(M);
+    std::vector<int2> tasks[3];
+    std::vector<int64_t> prefix(M + 1, 0);
+    int max_n = 1;
+    for (int m = 0; m < M; ++m) {
+        Ctx* c = b->members[m];
+        const T* r;
+        const T* cr;
+        const T* cv;
+        if (sizeof(T) == 8) {
+            r = reinterpret_cast<const T*>(c->coef.r);
+            cr = reinterpret_cast<const T*>(c->coef.cr);
+            cv = reinterpret_cast<const T*>(c->coef.c);
+        } else {
+            r = reinterpret_cast<const T*>(c->coef.r32);
+            cr = reinterpret_cast<const T*>(c->coef.cr32);
+            cv = reinterpret_cast<const T*>(c->coef.c32);
+        }
+        BatchDesc<T>& d = desc[m];
+        for (int a = 0; a < 3; ++a) {
+            d.ax[a] = make_args<T>(c, a, 0, r, cr, cv);
+            if (d.ax[a].n > max_n) max_n = d.ax[a].n;
+            int64_t nb = ceil_div(d.ax[a].n_lines, 32);
+            for (int64_t k = 0; k < nb; ++k) tasks[a].push_back(make_int2(m, (int)k));
+        }
+        d.per_state = (int64_t)c->n_sub * c->coef.L;
+        d.field = reinterpret_cast<T*>(c->field);
+        d.n_entries = c->src.n_entries;
+        d.off = c->src.off;
+        d.alpha = c->src.alpha;
+        d.beta = c->src.beta;
+        d.vox = c->src.vox;
+        d.sub = c->src.sub;
+        d.nx = c->nx;
+        d.ny = c->ny;
+        d.L = c->coef.L;
+        d.sc = c->coef.sc;
+        prefix[m + 1] = prefix[m] + c->src.n_entries;
+    }
+    b->max_n = max_n;
+    b->n_entries = prefix[M];
+    cudaError_t e;
+    if ((e = cudaMalloc(&b->d_desc, sizeof(BatchDesc<T>) * M)) != cudaSuccess) return BFVM_ENOMEM;
+    cudaMemcpy(b->d_desc, desc.data(), sizeof(BatchDesc<T>) * M, cudaMemcpyHostToDevice);
+    for (int a = 0; a < 3; ++a) {
+        b->n_tasks[a] = (int64_t)tasks[a].size();
+        if ((e = cudaMalloc(&b->d_tasks[a], sizeof(int2) * (tasks[a].size() + 1))) != cudaSuccess)
+            return BFVM_ENOMEM;
+        cudaMemcpy(b->d_tasks[a], tasks[a].data(), sizeof(int2) * tasks[a].size(),
+                   cudaMemcpyHostToDevice);
+    }
+    if ((e = cudaMalloc(&b->d_entry_prefix, sizeof(int64_t) * (M + 1))) != cudaSuccess)
+        return BFVM_ENOMEM;
+    if ((e = cudaMemcpy(b->d_entry_prefix, prefix.data(), sizeof(int64_t) * (M + 1),
+                        cudaMemcpyHostToDevice)) != cudaSuccess)
+        return BFVM_ECUDA;
+    return BFVM_OK;
+}
+
+template <typename T, int AXIS, int MODE>
+bfvm_status batch_axis(BatchImpl* b, int p)
+{
+    if (b->n_tasks[AXIS] == 0) return BFVM_OK;
+    Ctx* c0 = b->members[0];
+    size_t per_warp = (size_t)32 * b->max_n * sizeof(T);
+    int warps = (int)(c0->smem_optin / per_warp);
+    if (warps > 8) warps = 8;
+    if (warps < 1) return BFVM_EINVAL;
+    size_t smem = per_warp * warps;
+    auto kern = k_batch_sweep<T, AXIS, MODE>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
+        return BFVM_ECUDA;
+    unsigned grid = (unsigned)ceil_div(b->n_tasks[AXIS], warps);
+    kern<<<grid, 32 * warps, smem, b->stream>>>(
+        reinterpret_cast<const BatchDesc<T>*>(b->d_desc), b->d_tasks[AXIS], b->n_tasks[AXIS], p,
+        b->max_n);
+    b->launches += 1;
+    return cudaGetLastError() == cudaSuccess ? BFVM_OK : BFVM_ECUDA;
+}
+
+template <typename T, int MODE_Z>
+bfvm_status batch_step_t(BatchImpl* b, int p)
+{
+    constexpr int M = MODE_Z == 0 ? 0 : 1;
+    bfvm_status st;
+    if ((st = batch_axis<T, 0, M>(b, p)) != BFVM_OK) return st;
+    if ((st = batch_axis<T, 1, M>(b, p)) != BFVM_OK) return st;
+    if ((st = batch_axis<T, 2, MODE_Z>(b, p)) != BFVM_OK) return st;
+    if (b->n_entries > 0) {
+        unsigned grid = (unsigned)ceil_div(b->n_entries, 256);
+        const auto* D = reinterpret_cast<const BatchDesc<T>*>(b->d_desc);
+        if (MODE_Z == 1)
+            k_batch_sources<T, true><<<grid, 256, 0, b->stream>>>(
+                D, b->d_entry_prefix, (int)b->members.size(), b->n_entries, p + 1);
+        else
+            k_batch_sources<T, false><<<grid, 256, 0, b->stream>>>(
+                D, b->d_entry_prefix, (int)b->members.size(), b->n_entries, 0);
+        b->launches += 1;
+        if (cudaGetLastError() != cudaSuccess) return BFVM_ECUDA;
+    }
+    return BFVM_OK;
+}
+
+}  // namespace
+
+bfvm_status batch_build(BatchImpl* b)
+{
+    if (b->precision == 64) return batch_build_t<double>(b);
+    return batch_build_t<float>(b);
+}
+
+bfvm_status batch_launch_step(BatchImpl* b, int p, bool renorm)
+{
+    if (b->precision == 32) return batch_step_t<float, 0>(b, 0);
+    if (!b->rescaled) return batch_step_t<double, 0>(b, 0);
+    if (renorm) return batch_step_t<double, 2>(b, p);
+    return batch_step_t<double, 1>(b, p);
+}
+
+void batch_free(BatchImpl* b)
+{
+    if (b->d_desc) cudaFree(b->d_desc);
+    for (int a = 0; a < 3; ++a)
+        if (b->d_tasks[a]) cudaFree(b->d_tasks[a]);
+    if (b->d_entry_prefix) cudaFree(b->d_entry_prefix);
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    b->d_desc = nullptr;
+    b->d_entry_prefix = nullptr;
+    b->graph = nullptr;
 }
 
 }  // namespace bfvm

@@ -1,0 +1,112 @@
+"""GPU adjoint: gradients of a squared-difference loss with respect to D,
+lambda and per-cell S and U (and the initial field) against the CPU FP64
+oracle adjoint and against central finite differences of the GPU forward."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2110_13368_gb300 import inputs
+from tests.helpers import need_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def bf():
+    need_gpu()
+    from paper_2110_13368_gb300 import build, bfvm
+    build.build()
+    return bfvm
+
+
+def gpu_forward(bf, p, record=0):
+    sim = bf.Sim.from_problem(p)
+    if record:
+        sim.record(record)
+    sim.step(p.steps)
+    out = sim.get_density().cpu().numpy()
+    return sim, out
+
+
+def mixed_adjoint_problem():
+    return inputs.make_problem(19, 14, 11, n_sub=2, D=[3e4, 9e2], lam=[0.2, 0.05],
+                               bc_kind=[1, 0], bc_value=[38.0, 0.0], n_cells=60,
+                               U=[10.0, 2.0], S=[1.0, 6.0], rho_star=[38.0, 3.0], seed=5,
+                               steps=9, dt=0.02)
+
+
+@pytest.mark.parametrize("every", [1, 4, 9])
+def test_adjoint_matches_oracle(bf, every):
+    import torch
+    p = mixed_adjoint_problem()
+    target = p.rho0 * 0.5 + np.random.default_rng(4).uniform(0, 1, p.rho0.shape)
+    sim, fin = gpu_forward(bf, p, record=every)
+    ref_fin = oracle.run(p)
+    g = 2.0 * (fin - target)
+    out = sim.backward(torch.as_tensor(g, device="cuda"), want_g0=True)
+    sim.close()
+    ref = oracle.adjoint(p, 2.0 * (ref_fin - target), checkpoint_every=every)
+    for key in ("dD", "dlambda", "dS", "dU", "g0"):
+        a = out[key].cpu().numpy()
+        b = ref[key]
+        scale = np.abs(b).max()
+        assert np.abs(a - b).max() <= 1e-10 * scale, (key, np.abs(a - b).max() / scale)
+
+
+def test_adjoint_host_buffers_match_device(bf):
+    import torch
+    p = mixed_adjoint_problem()
+    sim, fin = gpu_forward(bf, p, record=3)
+    g = np.ones_like(fin)
+    dev = sim.backward(torch.as_tensor(g, device="cuda"))
+    n = p.n_cells
+    dD, dl = np.zeros(2), np.zeros(2)
+    dS, dU = np.zeros((n, 2)), np.zeros((n, 2))
+    bf.bfvm_backward(sim.handle, g, 0, dD, dl, dS, dU)
+    sim.close()
+    np.testing.assert_array_equal(dD, dev["dD"].cpu().numpy())
+    np.testing.assert_array_equal(dS, dev["dS"].cpu().numpy())
+
+
+def test_adjoint_central_differences(bf):
+    """Adjoint workload shape (one substrate, uniform cells, rho* = 38),
+    reduced grid and steps; FD step h = 1e-6 relative as the workload says,
+    with the FD evaluated by the GPU forward itself."""
+    import torch
+    p, q = inputs.adjoint_problem(n=24, n_cells=400, steps=20)
+    target = oracle.run(q)
+
+    def loss(pp):
+        _, f = gpu_forward(bf, pp)
+        return float(((f - target) ** 2).sum())
+
+    sim, fin = gpu_forward(bf, p, record=5)
+    out = sim.backward(torch.as_tensor(2.0 * (fin - target), device="cuda"))
+    sim.close()
+    for key, attr in (("dD", "D"), ("dlambda", "lam")):
+        base = getattr(p, attr)
+        h = 1e-6 * abs(base[0])
+        lp = loss(p.with_(**{attr: base + h}))
+        lm = loss(p.with_(**{attr: base - h}))
+        est = (lp - lm) / (2 * h)
+        assert out[key].cpu().numpy()[0] == pytest.approx(est, rel=1e-4), key
+    for i in (0, 7, 123):
+        for key, attr in (("dS", "S"), ("dU", "U")):
+            base = getattr(p, attr)
+            h = 1e-6 * max(abs(base[i, 0]), 1e-3) * 1e3
+            v1, v2 = base.copy(), base.copy()
+            v1[i, 0] += h
+            v2[i, 0] -= h
+            est = (loss(p.with_(**{attr: v1})) - loss(p.with_(**{attr: v2}))) / (2 * h)
+            got = out[key].cpu().numpy()[i, 0]
+            assert got == pytest.approx(est, rel=1e-4, abs=1e-7), (key, i, got, est)
+
+
+def test_backward_without_record_is_rejected(bf):
+    p = mixed_adjoint_problem()
+    sim, fin = gpu_forward(bf, p, record=0)
+    import torch
+    with pytest.raises(bf.BfvmError) as ei:
+        sim.backward(torch.zeros(p.rho0.shape, dtype=torch.float64, device="cuda"))
+    assert ei.value.status == 4
+    sim.close()
