@@ -90,16 +90,23 @@ def test_adjoint_central_differences(bf):
         lm = loss(p.with_(**{attr: base - h}))
         est = (lp - lm) / (2 * h)
         assert out[key].cpu().numpy()[0] == pytest.approx(est, rel=1e-4), key
+    l0 = loss(p)
     for i in (0, 7, 123):
         for key, attr in (("dS", "S"), ("dU", "U")):
             base = getattr(p, attr)
-            h = 1e-6 * max(abs(base[i, 0]), 1e-3) * 1e3
+            h = 1e-6 * max(abs(base[i, 0]), 1.0)
             v1, v2 = base.copy(), base.copy()
-            v1[i, 0] += h
-            v2[i, 0] -= h
-            est = (loss(p.with_(**{attr: v1})) - loss(p.with_(**{attr: v2}))) / (2 * h)
+            if base[i, 0] - h >= 0:
+                v1[i, 0] += h
+                v2[i, 0] -= h
+                est = (loss(p.with_(**{attr: v1})) - loss(p.with_(**{attr: v2}))) / (2 * h)
+            else:
+                # S = 0 in this workload: one-sided, second order
+                v1[i, 0] += h
+                v2[i, 0] += 2 * h
+                est = (-3 * l0 + 4 * loss(p.with_(**{attr: v1})) - loss(p.with_(**{attr: v2}))) / (2 * h)
             got = out[key].cpu().numpy()[i, 0]
-            assert got == pytest.approx(est, rel=1e-4, abs=1e-7), (key, i, got, est)
+            assert got == pytest.approx(est, rel=2e-4, abs=1e-6), (key, i, got, est)
 
 
 def test_backward_without_record_is_rejected(bf):
