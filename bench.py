@@ -49,6 +49,9 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--skip-extras", action="store_true",
                     help="timed steps only: no e2e, continuous run or CPU baseline (profiling runs)")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the FP32 / batched / adjoint form measurements")
+    ap.add_argument("--form-steps", type=int, default=10)
     return ap.parse_args()
 
 
@@ -177,6 +180,112 @@ def cpu_baseline(p, seconds):
             "kind": "oracle",
             "sample": f"{steps} full step(s) of the {p.nx}x{p.ny}x{p.nz}x{p.n_sub} workload "
                       f"from its initial field, {el:.1f} s, {threads} OpenMP threads"}
+
+
+def timed_steps(step_fn, k, stream, flush):
+    """Sum of CUDA-event times of k calls of step_fn, L2 flushed before each."""
+    import torch
+    st = [torch.cuda.Event(enable_timing=True) for _ in range(k)]
+    en = [torch.cuda.Event(enable_timing=True) for _ in range(k)]
+    torch.cuda.synchronize()
+    for i in range(k):
+        flush.fill_(float(i))
+        st[i].record(stream)
+        step_fn()
+        en[i].record(stream)
+    torch.cuda.synchronize()
+    return sum(a.elapsed_time(b) for a, b in zip(st, en))
+
+
+def measure_forms(args, plain_ups, dev, stream, flush):
+    """The FP32, batched and adjoint forms against the plain FP64 form."""
+    import numpy as np
+    import torch
+    from paper_2110_13368_gb300 import bfvm, inputs
+    K = args.form_steps
+    out = {}
+    # FP32 form of the tumour workload; its error against the FP64 GPU path
+    p64 = inputs.tumour_200(steps=K)
+    s32 = bfvm.Sim.from_problem(p64, precision=32)
+    s32.step(3)
+    s32.set_density(torch.as_tensor(p64.rho0, dtype=torch.float32, device=dev))
+    ms = timed_steps(lambda: s32.step(1), K, stream, flush)
+    ups32 = p64.updates_per_step * K / (ms / 1e3)
+    s64 = bfvm.Sim.from_problem(p64)
+    s64.step(K)
+    a = s32.get_density().double()
+    b = s64.get_density()
+    err = [float((a[s] - b[s]).abs().max() / b[s].abs().max()) for s in range(p64.n_sub)]
+    out["fp32"] = {"value": ups32, "speedup_vs_fp64": ups32 / plain_ups, "steps": K,
+                   "max_rel_err_vs_fp64_gpu_per_substrate": err,
+                   "accuracy_gate": "<= 1e-5 vs the FP64 oracle (parity tests)"}
+    s32.close()
+    s64.close()
+    # batched: 256 uneven members, one launch per phase, against the same
+    # members stepped one context at a time
+    for prec in (64, 32):
+        probs = inputs.batch_256(seed=0, precision=prec)
+        sims = [bfvm.Sim.from_problem(q) for q in probs]
+        batch = bfvm.Batch(sims)
+        n_upd = sum(q.updates_per_step for q in probs)
+        batch.step(3)
+        msb = timed_steps(lambda: batch.step(1), K, stream, flush)
+        info = batch.info()
+        batch.close()
+        for q, sm in zip(probs, sims):
+            sm.set_density(torch.as_tensor(q.rho0, dtype=sm.dtype, device=dev))
+
+        def one_by_one():
+            for sm in sims:
+                sm.step(1)
+        one_by_one()
+        mss = timed_steps(one_by_one, max(2, K // 2), stream, flush) * K / max(2, K // 2)
+        for sm in sims:
+            sm.close()
+        out[f"batched_fp{prec}"] = {
+            "value": n_upd * K / (msb / 1e3), "members": len(probs),
+            "updates_per_step": n_upd, "launches_per_step": info["launches"] // max(3 + K, 1),
+            "one_by_one_value": n_upd * K / (mss / 1e3),
+            "speedup_vs_one_by_one": mss / msb,
+            "speedup_vs_plain_fp64_tumour": (n_upd * K / (msb / 1e3)) / plain_ups,
+            "steps": K}
+    # adjoint: forward with checkpoints every 20 steps, then the backward
+    p, q = inputs.adjoint_problem()
+    target = None
+    sa = bfvm.Sim.from_problem(q)
+    sa.step(q.steps)
+    target = sa.get_density()
+    sa.close()
+    sim = bfvm.Sim.from_problem(p)
+    sim.step(p.steps)   # warm the graphs and kernels
+    sim.set_density(torch.as_tensor(p.rho0, device=dev))
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sim.step(p.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    fwd_plain_ms = e0.elapsed_time(e1)
+    sim.set_density(torch.as_tensor(p.rho0, device=dev))
+    sim.record(20)
+    t0 = time.perf_counter()
+    sim.step(p.steps)
+    fin = sim.get_density()
+    torch.cuda.synchronize()
+    fwd_rec_s = time.perf_counter() - t0
+    g = 2.0 * (fin - target)
+    t0 = time.perf_counter()
+    grads = sim.backward(g)
+    torch.cuda.synchronize()
+    bwd_s = time.perf_counter() - t0
+    sim.close()
+    out["adjoint"] = {"workload": p.name, "steps": p.steps, "checkpoint_every": 20,
+                      "forward_plain_ms": fwd_plain_ms, "forward_recorded_ms": fwd_rec_s * 1e3,
+                      "backward_ms": bwd_s * 1e3,
+                      "fwd_plus_bwd_over_2x_fwd": (fwd_rec_s + bwd_s) / (2 * fwd_plain_ms / 1e3),
+                      "dD": float(grads["dD"][0]), "dlambda": float(grads["dlambda"][0]),
+                      "accuracy_gate": "1e-10 vs the CPU adjoint, 2e-4 vs central differences (tests)"}
+    return out
 
 
 def metric_name():
@@ -351,6 +460,10 @@ def run_ours(args):
            "steps": args.e2e_steps,
            "call": "bfvm_set_density(host) + bfvm_step(1) + bfvm_get_density(host)"}
 
+    forms = None
+    if not args.no_forms and world == 1:
+        forms = measure_forms(args, ups, dev, stream, flush)
+
     # continuous run for context: 1000 steps in one call (graphs, no flush)
     sim.set_option(bfvm.OPT_TIME_KERNELS, 0)
     sim.set_density(torch.as_tensor(p.rho0, dtype=sim.dtype, device=dev))
@@ -380,6 +493,8 @@ def run_ours(args):
                 "hbm_frac_step": ups / world * 6 * es / 1e9 / hbm,
                 "roofline": roof, "kernels": kernels, "gpu_launches": launches,
                 "wall_s_timed_region": t_wall, "e2e": e2e, "continuous": continuous}
+        if forms is not None:
+            line["forms"] = forms
         clocks = clk.summary()
         line["clocks"] = clocks
         if world == 1 and not args.no_cpu_baseline:
