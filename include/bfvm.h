@@ -192,6 +192,8 @@ bfvm_status bfvm_get_info(const bfvm_ctx* ctx, int64_t* info);
  *   key 5  per-kernel timing: 0 off (default), 1 each sweep and source
  *          launch is bracketed by CUDA events on the context's stream
  *          (bfvm_step then launches kernels one by one, without graphs)
+ *   key 6  cap on the CTAs of the persistent sweeps (0 = one per SM, the
+ *          default); small caps make every warp walk many line blocks
  */
 bfvm_status bfvm_set_option(bfvm_ctx* ctx, int32_t key, int64_t value);
 

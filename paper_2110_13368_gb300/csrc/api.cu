@@ -529,6 +529,11 @@ bfvm_status bfvm_set_option(bfvm_ctx* h, int32_t key, int64_t value)
             if (value != 0 && value != 1) return set_err(c, BFVM_EINVAL, "timing must be 0 or 1");
             c->time_kernels = (int)value;
             return BFVM_OK;
+        case 6:
+            if (value < 0 || value > 1000000) return set_err(c, BFVM_EINVAL, "grid limit must be >= 0");
+            c->grid_limit = (int)value;
+            drop_graphs(c);
+            return BFVM_OK;
         default:
             return set_err(c, BFVM_EINVAL, "unknown option key");
     }

@@ -86,6 +86,7 @@ struct Ctx {
     int period_override = 0;
     int fuse_sources = 0;
     int use_graphs = 1;
+    int grid_limit = 0;           // cap on persistent sweep CTAs (0 = one per SM)
     int scale_state = 0;          // rescale state p of the stored field
 
     cudaGraphExec_t period_graph = nullptr;

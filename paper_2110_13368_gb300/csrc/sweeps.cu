@@ -417,6 +417,7 @@ bfvm_status launch_axis(Ctx* c, const SweepArgs<T>& A)
         int64_t n_blocks = ceil_div(first[A.n_sub], 32);
         int64_t grid = ceil_div(n_blocks, warps);
         if (grid > c->sm_count) grid = c->sm_count;
+        if (c->grid_limit > 0 && grid > c->grid_limit) grid = c->grid_limit;
         kern<<<(unsigned)grid, 32 * warps, smem, c->stream>>>(A, S, n_blocks, ns);
     } else {
         size_t per_warp1 = (size_t)32 * A.n * sizeof(T);
