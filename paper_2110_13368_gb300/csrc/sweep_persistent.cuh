@@ -26,9 +26,10 @@
 // of a warp is eliminated on its own, and only its last one back-substituted
 // on its own.
 //
-// Shared-memory layout: element (slot, lane) sits at column
-// lane ^ ((slot mod G) * ROWS) of row `slot`, so that both a lane's own
-// column and the transposed copies of the x sweep hit every bank evenly.
+// Shared-memory layout: element (slot, lane) sits in row `slot`; for the x
+// sweep at column lane ^ ((slot mod G) * ROWS), so that both a lane's own
+// column and the transposed copies hit every bank evenly, for the y and z
+// sweeps at column lane.
 //
 // Global access: for the y and z sweeps adjacent lanes hold adjacent x, so
 // each per-element access of a warp is one coalesced row.  For the x sweep
@@ -145,10 +146,12 @@ struct Sweeper {
     __device__ __forceinline__ int slot(int k) const { return Q ? (ns - 1 - k) : k; }
     template <int Q>
     __device__ __forceinline__ static constexpr int res(int kmod) { return Q ? (G - 1 - kmod) : kmod; }
-    // element of lane/row l in slot s whose residue mod G is m
+    // element of lane/row l in slot s whose residue mod G is m; only the x
+    // sweep (transposed copies) swizzles, the y and z sweeps keep lane l in
+    // column l (every access path must agree on this)
     __device__ __forceinline__ T* at(int s, int l, int m) const
     {
-        return W + s * 32 + (l ^ (m * ROWS));
+        return W + s * 32 + (AXIS == 0 ? (l ^ (m * ROWS)) : l);
     }
     // this lane's element of the slot holding element k (k mod G == u)
     template <int Q>

@@ -28,8 +28,10 @@ def bf():
 
 
 def run_gpu(bf, p, steps=None, precision=None, variant=None, period=None, graphs=None,
-            cells_on_device=True):
+            cells_on_device=True, grid_limit=None):
     sim = bf.Sim.from_problem(p, precision=precision, cells_on_device=cells_on_device)
+    if grid_limit is not None:
+        sim.set_option(bf.OPT_GRID_LIMIT, grid_limit)
     if variant is not None:
         sim.set_option(bf.OPT_VARIANT, variant)
     if period is not None:
@@ -67,12 +69,15 @@ CASES = {
 }
 
 
+@pytest.mark.parametrize("grid_limit", [0, 1, 3])
 @pytest.mark.parametrize("variant", [0, 1])
 @pytest.mark.parametrize("case", sorted(CASES))
-def test_fp64_matches_oracle(bf, case, variant):
+def test_fp64_matches_oracle(bf, case, variant, grid_limit):
+    """grid_limit 1 or 3 caps the persistent sweeps at that many CTAs, so
+    every warp walks many 32-line blocks (the interleaved path)."""
     p = CASES[case]()
     ref = oracle.run(p)
-    got, info = run_gpu(bf, p, variant=variant)
+    got, info = run_gpu(bf, p, variant=variant, grid_limit=grid_limit)
     assert info["variant"] == variant
     err = rel_inf(got, ref)
     assert np.all(err <= TOL64), (case, variant, err)
@@ -171,12 +176,13 @@ def test_cells_on_faces_and_domain_max(bf):
     assert np.all(rel_inf(got, ref) <= TOL64)
 
 
+@pytest.mark.parametrize("grid_limit", [0, 1])
 @pytest.mark.parametrize("case", ["ragged_37x45x50", "cube_33", "thin_1x1x7", "long_x_300",
-                                  "plain_50_fullsteps"])
-def test_fp32_matches_fp64_oracle(bf, case):
+                                  "long_z_260", "plain_50_fullsteps"])
+def test_fp32_matches_fp64_oracle(bf, case, grid_limit):
     p = CASES[case]()
     ref = oracle.run(p)
-    got, info = run_gpu(bf, p, precision=32)
+    got, info = run_gpu(bf, p, precision=32, grid_limit=grid_limit)
     assert info["precision"] == 32
     err = rel_inf(got, ref)
     assert np.all(err <= TOL32), (case, err, rel_l2(got, ref))
