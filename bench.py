@@ -79,9 +79,11 @@ def peaks():
 def sweep_traffic(workload):
     """DRAM bytes per sweep launch from the committed ncu summary, if it was
     taken on the current sweep source; else None."""
-    src = os.path.join(ROOT, "paper_2110_13368_gb300", "csrc", "sweeps.cu")
-    digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    path = os.path.join(ROOT, "profiles", f"traffic_{workload}.txt")
+    h = hashlib.sha256()
+    for f in ("sweeps.cu", "sweep_persistent.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2110_13368_gb300", "csrc", f), "rb").read())
+    digest = h.hexdigest()[:16]
+    path = os.path.join(ROOT, "profiles", f"traffic_{workload}.txt")  # e.g. tumour_200_fp64
     if not os.path.exists(path):
         return None
     vals = {}
@@ -400,7 +402,7 @@ def run_ours(args):
                 kernels[name]["gbs"] = bytes_per_launch / (avg / 1e3) / 1e9
     dom = max(range(3), key=lambda k: kms[k])
     dom_avg = kms[dom] / max(kn[dom], 1)
-    traffic = sweep_traffic(p.name)
+    traffic = sweep_traffic(f"{args.workload.replace('_fp32', '')}_fp{prec}")
     info = sim.info()
     rescaled = prec == 64 and info["variant"] == 1
     if prec == 64:
