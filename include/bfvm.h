@@ -239,6 +239,39 @@ const char* bfvm_batch_last_error(const bfvm_batch* batch);
  * the three sweeps, source entries, launches issued, current rescale state. */
 bfvm_status bfvm_batch_info(const bfvm_batch* batch, int64_t* info);
 
+/*
+ * Allocation-free variant of the cell source/uptake update.  The paper has
+ * no counterpart: it exists for callers that must not allocate device
+ * memory, such as host loops driving many small simulations (cudaMalloc and
+ * cudaFree stall, and cudaFree synchronises the whole device) or programs
+ * whose memory manager owns all device memory.
+ *
+ * Applies, to the caller's dense FP64 device field rho[n_sub][nz][ny][nx]
+ * (in place), the same update as the source part of bfvm_step: every cell,
+ * in ascending index order within its voxel, does
+ *   rho_v <- (rho_v + dt (V_i/dx^3) S_i rho*_i) / (1 + dt (V_i/dx^3)(S_i+U_i)).
+ * pos, vol, S, U, rho_star are device arrays laid out as in bfvm_set_cells.
+ * It allocates nothing: its only scratch (the sort keys of at most 262,144
+ * cells plus a check flag, about 2 MB) is a fixed device array that every
+ * GPU loading this library holds until the process exits.
+ *  - n_cells > 262,144: BFVM_EINVAL with an explanatory text, nothing runs.
+ *  - Bad sizes or cells (positions outside [0, n_a*dx], non-positive
+ *    volumes, negative or non-finite rates): BFVM_EINVAL; the field is
+ *    untouched.  The cell check synchronises cuda_stream.
+ *  - Errors are reported by bfvm_last_error(NULL).
+ *  - The first call on a device looks up the scratch array's device address
+ *    (once per device); make that first call before any stream capture.
+ *  - All calls on one device share the scratch: calls whose GPU work can
+ *    overlap (different streams without ordering) race; order them on one
+ *    stream.  Each call rewrites every scratch word it reads.
+ */
+bfvm_status bfvm_apply_sources_noalloc(double* rho, int32_t nx, int32_t ny, int32_t nz,
+                                       int32_t n_sub, double dx_um, double dt_min,
+                                       int64_t n_cells, const double* pos,
+                                       const double* vol, const double* S,
+                                       const double* U, const double* rho_star,
+                                       void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -35,7 +35,7 @@ EXPORTED = ["bfvm_create", "bfvm_destroy", "bfvm_set_density", "bfvm_get_density
             "bfvm_last_error", "bfvm_status_string", "bfvm_get_info", "bfvm_set_option",
             "bfvm_kernel_times",
             "bfvm_batch_create", "bfvm_batch_step", "bfvm_batch_sync", "bfvm_batch_destroy",
-            "bfvm_batch_last_error", "bfvm_batch_info"]
+            "bfvm_batch_last_error", "bfvm_batch_info", "bfvm_apply_sources_noalloc"]
 
 
 class BfvmError(RuntimeError):
@@ -92,6 +92,9 @@ def load_library(path: Optional[str] = None):
         lib.bfvm_batch_last_error.restype = ctypes.c_char_p
         lib.bfvm_batch_info.argtypes = [_vp, ctypes.POINTER(_i64)]
         lib.bfvm_batch_info.restype = ctypes.c_int
+        lib.bfvm_apply_sources_noalloc.argtypes = ([_vp] + [_i32] * 4 + [ctypes.c_double] * 2
+                                                   + [_i64] + [_vp] * 5 + [_vp])
+        lib.bfvm_apply_sources_noalloc.restype = ctypes.c_int
         for name in ("bfvm_create", "bfvm_set_density", "bfvm_get_density", "bfvm_set_cells",
                      "bfvm_step", "bfvm_sync", "bfvm_record", "bfvm_backward", "bfvm_get_info",
                      "bfvm_set_option", "bfvm_kernel_times", "bfvm_batch_create", "bfvm_batch_step",
@@ -270,6 +273,23 @@ def bfvm_batch_info(b):
     keys = ["members", "precision", "rescaled", "period", "tasks_per_step", "source_entries",
             "launches", "state"]
     return {k: int(info[i]) for i, k in enumerate(keys)}
+
+
+def bfvm_apply_sources_noalloc(rho, nx, ny, nz, dx_um, dt_min, pos, vol, S, U, rho_star,
+                               stream=None):
+    """Cell source/uptake update on a dense FP64 device field, in place,
+    without any device allocation (for callers that must not allocate; see
+    include/bfvm.h).  All arrays are CUDA tensors."""
+    ptrs = [_ptr(a) for a in (rho, pos, vol, S, U, rho_star)]
+    if any(d != 1 for _, d, _ in ptrs):
+        raise ValueError("bfvm_apply_sources_noalloc takes device tensors only")
+    n_sub = int(rho.shape[0])
+    n_cells = int(pos.shape[0])
+    st = load_library().bfvm_apply_sources_noalloc(
+        ptrs[0][0], int(nx), int(ny), int(nz), n_sub, float(dx_um), float(dt_min), n_cells,
+        ptrs[1][0], ptrs[2][0], ptrs[3][0], ptrs[4][0], ptrs[5][0], _stream_handle(stream))
+    _check(st, None)
+    del ptrs
 
 
 class Batch:
