@@ -325,58 +325,34 @@ struct Sweeper {
             }
         }
         const int um = lane % G;
-        // operands of the current group, loaded one group ahead
-        T w[G], d[G], bb[G], aa[G], bl[G], al[G];
-        auto load_ops = [&](const T* rbw_, const T* rfd_, const T* cb_, const T* ca_,
-                            const T* cbl_, const T* cal_) {
-#pragma unroll
-            for (int u = 0; u < G; ++u) {
-                w[u] = rbw_[(Q ? -u : u) * RS + lx[res<Q>(u)]];
-                d[u] = rfd_[(P ? -u : u) * RS + lx[res<P>(u)]];
-                bb[u] = cb_[u];
-                aa[u] = ca_[u];
-                if (MODE == 0 && sizeof(T) == 4) {
-                    bl[u] = cbl_[u];
-                    al[u] = cal_[u];
-                }
-            }
-        };
-        cp_async_wait<LG - 1>();
-        __syncwarp();
-        load_ops(rbw, rfd, cb, ca, cbl, cal);
         for (int jg = j0; jg < j1; ++jg) {
-            T o[G], f[G];
-            T wc[G], dc[G], bc[G], ac[G], blc[G], alc[G];
+            cp_async_wait<LG - 1>();
+            __syncwarp();
+            T w[G], d[G], bb[G], aa[G], bl[G], al[G], o[G], f[G];
 #pragma unroll
             for (int u = 0; u < G; ++u) {
-                wc[u] = w[u];
-                dc[u] = d[u];
-                bc[u] = bb[u];
-                ac[u] = aa[u];
-                blc[u] = bl[u];
-                alc[u] = al[u];
-            }
-            // next group's operands: its forward copies (e-group g+1) are
-            // complete once at most LG - 2 newer commit groups are pending
-            if (jg + 1 < j1) {
-                cp_async_wait<LG - 2>();
-                __syncwarp();
-                load_ops(rbw + (Q ? G : -G) * RS, rfd + (P ? -G : G) * RS, cb - G, ca + G,
-                         cbl - G, cal + G);
+                w[u] = rbw[(Q ? -u : u) * RS + lx[res<Q>(u)]];
+                d[u] = rfd[(P ? -u : u) * RS + lx[res<P>(u)]];
+                bb[u] = cb[u];
+                aa[u] = ca[u];
+                if (MODE == 0 && sizeof(T) == 4) {
+                    bl[u] = cbl[u];
+                    al[u] = cal[u];
+                }
             }
 #pragma unroll
             for (int u = 0; u < G; ++u) {
                 const int ub = G - 1 - u;
                 if (MODE == 0 && sizeof(T) == 4) {
-                    x = (T)comp_axpy((float)bc[ub], (float)blc[ub], (float)x, (float)wc[ub]);
-                    float t = comp_axpy((float)CN.c, (float)CN.c_lo, (float)prev, (float)dc[u]);
-                    prev = (T)__fmaf_rn(t, (float)ac[u], __fmul_rn(t, (float)alc[u]));
+                    x = (T)comp_axpy((float)bb[ub], (float)bl[ub], (float)x, (float)w[ub]);
+                    float t = comp_axpy((float)CN.c, (float)CN.c_lo, (float)prev, (float)d[u]);
+                    prev = (T)__fmaf_rn(t, (float)aa[u], __fmul_rn(t, (float)al[u]));
                 } else if (MODE == 0) {
-                    x = fma(bc[ub], x, wc[ub]);
-                    prev = fma(CN.c, prev, dc[u]) * ac[u];
+                    x = fma(bb[ub], x, w[ub]);
+                    prev = fma(CN.c, prev, d[u]) * aa[u];
                 } else {
-                    x = fma(bc[ub], x, wc[ub]);
-                    prev = fma(ac[u], prev, dc[u]);
+                    x = fma(bb[ub], x, w[ub]);
+                    prev = fma(aa[u], prev, d[u]);
                 }
                 o[ub] = (MODE == 2) ? (T)(((double)x * co[ub]) * L.inv_other) : x;
                 f[u] = prev;
