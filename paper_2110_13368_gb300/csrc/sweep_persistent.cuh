@@ -325,9 +325,27 @@ struct Sweeper {
             }
         }
         const int um = lane % G;
+        // results of the previous group, stored one group late so that the
+        // stores never wait for a DFMA that has only just been issued
+        T po[G], pf[G];
+        T* ppout = nullptr;
+        T* prfd = nullptr;
+        bool pending = false;
         for (int jg = j0; jg < j1; ++jg) {
             cp_async_wait<LG - 1>();
             __syncwarp();
+            if (AXIS != 0 && pending) {
+#pragma unroll
+                for (int u = 0; u < G; ++u) prfd[(P ? -u : u) * RS + lx[res<P>(u)]] = pf[u];
+                if (L.valid) {
+                    T* p = ppout;
+#pragma unroll
+                    for (int u = 0; u < G; ++u) {
+                        *p = po[u];
+                        p += stride;
+                    }
+                }
+            }
             T w[G], d[G], bb[G], aa[G], bl[G], al[G], o[G], f[G];
 #pragma unroll
             for (int u = 0; u < G; ++u) {
@@ -357,19 +375,17 @@ struct Sweeper {
                 o[ub] = (MODE == 2) ? (T)(((double)x * co[ub]) * L.inv_other) : x;
                 f[u] = prev;
             }
-#pragma unroll
-            for (int u = 0; u < G; ++u) rfd[(P ? -u : u) * RS + lx[res<P>(u)]] = f[u];
             // element u of the copied group lands in row hG + (G-1-u) (Q = 0)
             // or ns-1-hG-(G-1-u) (Q = 1), i.e. rbw + (Q ? u-(G-1) : (G-1)-u) rows
             if (AXIS != 0) {
-                if (L.valid) {
-                    T* p = pout;
 #pragma unroll
-                    for (int u = 0; u < G; ++u) {
-                        *p = o[u];
-                        p += stride;
-                    }
+                for (int u = 0; u < G; ++u) {
+                    pf[u] = f[u];
+                    po[u] = o[u];
                 }
+                prfd = rfd;
+                ppout = pout;
+                pending = true;
                 const T* q = psrc;
 #pragma unroll
                 for (int u = 0; u < G; ++u) {
@@ -378,6 +394,8 @@ struct Sweeper {
                     q += stride;
                 }
             } else {
+#pragma unroll
+                for (int u = 0; u < G; ++u) rfd[(P ? -u : u) * RS + lx[res<P>(u)]] = f[u];
 #pragma unroll
                 for (int u = 0; u < G; ++u) rbw[(Q ? -u : u) * RS + lx[res<Q>(u)]] = o[u];
                 __syncwarp();
@@ -415,6 +433,18 @@ struct Sweeper {
             co -= G;
             pout -= sG;
             psrc += sG;
+        }
+        if (AXIS != 0 && pending) {
+#pragma unroll
+            for (int u = 0; u < G; ++u) prfd[(P ? -u : u) * RS + lx[res<P>(u)]] = pf[u];
+            if (L.valid) {
+                T* p = ppout;
+#pragma unroll
+                for (int u = 0; u < G; ++u) {
+                    *p = po[u];
+                    p += stride;
+                }
+            }
         }
     }
 
