@@ -35,17 +35,20 @@
 // each per-element access of a warp is one coalesced row.  For the x sweep
 // the lanes hold 32 rows; copies and stores are transposed so that each
 // instruction moves (32/G) rows x G consecutive elements = whole 32-byte
-// sectors (G = 32 bytes / element size).
+// sectors.
 #pragma once
 
 namespace bfvm {
 namespace persistent {
 
+// Group of G consecutive elements per loop iteration: 8 for both types (one
+// 32-byte sector of FP32, two of FP64), so that per-group costs (waits,
+// commits, pointer updates, boundary groups) are amortised over 8 elements.
 template <typename T>
 struct Groups {
-    static constexpr int G = 32 / (int)sizeof(T);   // elements per 32-byte sector
+    static constexpr int G = 8;
     static constexpr int ROWS = 32 / G;             // rows per transposed instruction
-    static constexpr int LAG_GROUPS = sizeof(T) == 8 ? 6 : 4;
+    static constexpr int LAG_GROUPS = sizeof(T) == 8 ? 3 : 4;
 };
 
 // Lines of one axis that need a solve, substrate by substrate: for a
