@@ -194,6 +194,8 @@ bfvm_status bfvm_get_info(const bfvm_ctx* ctx, int64_t* info);
  *          (bfvm_step then launches kernels one by one, without graphs)
  *   key 6  cap on the CTAs of the persistent sweeps (0 = one per SM, the
  *          default); small caps make every warp walk many line blocks
+ *   key 7  FP64 sweep kernel: 0 warp pairs sharing each line buffer (the
+ *          default), 1 one warp per line buffer
  */
 bfvm_status bfvm_set_option(bfvm_ctx* ctx, int32_t key, int64_t value);
 

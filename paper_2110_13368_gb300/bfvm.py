@@ -29,6 +29,7 @@ OPT_FUSE_SOURCES = 3
 OPT_GRAPHS = 4
 OPT_TIME_KERNELS = 5
 OPT_GRID_LIMIT = 6
+OPT_SWEEP_KERNEL = 7
 
 EXPORTED = ["bfvm_create", "bfvm_destroy", "bfvm_set_density", "bfvm_get_density",
             "bfvm_set_cells", "bfvm_step", "bfvm_sync", "bfvm_record", "bfvm_backward",

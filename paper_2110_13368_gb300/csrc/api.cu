@@ -534,6 +534,11 @@ bfvm_status bfvm_set_option(bfvm_ctx* h, int32_t key, int64_t value)
             c->grid_limit = (int)value;
             drop_graphs(c);
             return BFVM_OK;
+        case 7:
+            if (value != 0 && value != 1) return set_err(c, BFVM_EINVAL, "sweep kernel must be 0 or 1");
+            c->sweep_kernel = (int)value;
+            drop_graphs(c);
+            return BFVM_OK;
         default:
             return set_err(c, BFVM_EINVAL, "unknown option key");
     }

@@ -87,6 +87,7 @@ struct Ctx {
     int fuse_sources = 0;
     int use_graphs = 1;
     int grid_limit = 0;           // cap on persistent sweep CTAs (0 = one per SM)
+    int sweep_kernel = 0;         // FP64: 0 warp pairs, 1 one warp per buffer
     int scale_state = 0;          // rescale state p of the stored field
 
     cudaGraphExec_t period_graph = nullptr;

@@ -1,0 +1,302 @@
+// Warp-pair line sweep for FP64 (included by sweeps.cu after
+// sweep_persistent.cuh, whose LineSet / Line / make_line it reuses).
+//
+// The FP64 pipe of an SMSP only reaches its issue rate with two warps
+// feeding it, but one 32-line block of 200 doubles per lane fills 51 KB of
+// shared memory, so only four such blocks fit per SM.  Here each column
+// buffer is shared by a pair of warps:
+//   - warp F of the pair copies the elements of a block into the buffer and
+//     runs its forward elimination;
+//   - warp B of the pair runs the back substitution of the previous block
+//     on the same buffer and writes the results out.
+// The slot of element k alternates between k and n_slots-1-k from block to
+// block, so the slots that B frees (from the end of the line backwards)
+// are exactly those of the first elements of F's next block.  Both warps
+// walk the same iteration count per block; after each group of G elements
+// they meet at a named barrier (one per pair): B has finished reading and
+// writing its group, so F may refill those slots.  F's forward runs LAG
+// groups behind its copies.  A block's last intermediate passes from F to B
+// through shared memory at another barrier.
+//
+// Every barrier is reached the same number of times by both warps of a
+// pair: the block list, group count and lag are the same for both, and no
+// warp leaves the loop early.
+#pragma once
+
+namespace bfvm {
+namespace persistent {
+
+template <typename T, int AXIS, int MODE>
+struct PairSweeper {
+    static constexpr int G = Groups<T>::G;
+    static constexpr int ROWS = Groups<T>::ROWS;
+    static constexpr int LG = Groups<T>::LAG_GROUPS;
+
+    const SweepArgs<T>& A;
+    T* W;
+    const T* fin;
+    T* fout;
+    int64_t stride;
+    int n, ns, lane;
+    int bar_id;
+
+    __device__ __forceinline__ void pair_bar() const
+    {
+        asm volatile("bar.sync %0, 64;" ::"r"(bar_id) : "memory");
+    }
+    template <int Q>
+    __device__ __forceinline__ int slot(int k) const { return Q ? (ns - 1 - k) : k; }
+    template <int Q>
+    __device__ __forceinline__ static constexpr int res(int kmod) { return Q ? (G - 1 - kmod) : kmod; }
+    __device__ __forceinline__ T* at(int s, int l, int m) const
+    {
+        return W + s * 32 + (AXIS == 0 ? (l ^ (m * ROWS)) : l);
+    }
+    template <int Q>
+    __device__ __forceinline__ T* own(int k, int u) const
+    {
+        return at(slot<Q>(k), lane, res<Q>(u));
+    }
+
+    // F: copy elements [gG, gG+G) of a block into the slots of parity Q
+    template <int Q>
+    __device__ __forceinline__ void copy_group(const Line& ln, const int64_t* rb, int g) const
+    {
+        if (g * G >= n) return;
+        if (AXIS == 0) {
+            const int e = g * G + (lane % G);
+            if (e < n) {
+                const int s = slot<Q>(e);
+                const int m = res<Q>(lane % G);
+#pragma unroll
+                for (int t = 0; t < G; ++t) {
+                    const int r = t * ROWS + lane / G;
+                    cp_async_elem(at(s, r, m), fin + rb[r] + e);
+                }
+            }
+        } else {
+            const T* src = fin + ln.base + (int64_t)g * G * stride;
+#pragma unroll
+            for (int u = 0; u < G; ++u)
+                if (g * G + u < n) cp_async_elem(own<Q>(g * G + u, u), src + u * stride);
+        }
+    }
+
+    // F: forward elimination of group g (parity Q); prev carries the chain
+    template <int Q>
+    __device__ __forceinline__ void fwd_group(const Line& L, const CoefRow<T>& C, T& prev,
+                                              int g) const
+    {
+        T d[G];
+#pragma unroll
+        for (int u = 0; u < G; ++u)
+            if (g * G + u < n) d[u] = *own<Q>(g * G + u, u);
+#pragma unroll
+        for (int u = 0; u < G; ++u) {
+            const int k = g * G + u;
+            if (k < n) {
+                T dk = d[u];
+                if (L.dir && k == 0) dk = (T)L.end0;
+                if (L.dir && k == n - 1) dk = (T)L.end1;
+                if (MODE == 0) prev = fma(C.c, prev, dk) * C.a[k];
+                else prev = (k == 0) ? dk : fma(C.a[k], prev, dk);
+                if (k < n - 1) *own<Q>(k, u) = prev;
+            }
+        }
+    }
+
+    // B: back substitution of group h (parity Q) and its output
+    template <int Q>
+    __device__ __forceinline__ void bwd_group(const Line& L, const CoefRow<T>& C, T& x, int h,
+                                              const int64_t* rb) const
+    {
+        T w[G], o[G];
+#pragma unroll
+        for (int u = 0; u < G; ++u)
+            if (h * G + u < n - 1) w[u] = *own<Q>(h * G + u, u);
+#pragma unroll
+        for (int u = G - 1; u >= 0; --u) {
+            const int k = h * G + u;
+            if (k < n) {
+                if (k < n - 1) x = fma(C.b[k], x, w[u]);
+                o[u] = (MODE == 2) ? (T)(((double)x * C.o[k]) * L.inv_other) : x;
+            }
+        }
+        if (AXIS == 0) {
+#pragma unroll
+            for (int u = 0; u < G; ++u)
+                if (h * G + u < n) *own<Q>(h * G + u, u) = o[u];
+            __syncwarp();
+            const int k = h * G + (lane % G);
+            if (k < n) {
+                const int s = slot<Q>(k);
+                const int m = res<Q>(lane % G);
+#pragma unroll
+                for (int t = 0; t < G; ++t) {
+                    const int r = t * ROWS + lane / G;
+                    if (rb[r] >= 0) fout[rb[r] + k] = *at(s, r, m);
+                }
+            }
+            __syncwarp();
+        } else if (L.valid) {
+            T* dst = fout + L.base + (int64_t)h * G * stride;
+#pragma unroll
+            for (int u = 0; u < G; ++u)
+                if (h * G + u < n) dst[u * stride] = o[u];
+        }
+    }
+};
+
+// Dynamic shared memory: [coefficients of all substrates, this axis]
+// [MODE 2 output scales] [line-set prefix] [per pair: column buffer,
+// 2 x 32 row bases of each warp (4 x 32), 32 chain hand-over values].
+template <typename T, int AXIS, int MODE>
+__global__ void __launch_bounds__(256, 1) k_sweep_pair(SweepArgs<T> A, LineSet S,
+                                                       int64_t n_blocks, int n_slots)
+{
+    constexpr int G = Groups<T>::G;
+    constexpr int LG = Groups<T>::LAG_GROUPS;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int pairs = blockDim.x >> 6;
+    const int pair = warp >> 1;
+    const bool is_b = (warp & 1) != 0;   // B: back substitution; F: copies + forward
+    const int n = A.n;
+    const int ns = n_slots;
+    const int n_sub = A.n_sub;
+
+    const int ncoef = 2;
+    T* cbase = reinterpret_cast<T*>(smem_raw);
+    const int per_sub = ncoef * n;
+    const size_t coef_bytes = (size_t)n_sub * per_sub * sizeof(T);
+    double* obase = reinterpret_cast<double*>(smem_raw + ((coef_bytes + 15) & ~(size_t)15));
+    const size_t o_bytes = (MODE == 2) ? (size_t)n_sub * n * sizeof(double) : 0;
+    int64_t* first_s = reinterpret_cast<int64_t*>(
+        reinterpret_cast<unsigned char*>(obase) + ((o_bytes + 15) & ~(size_t)15));
+    unsigned char* pair_area = reinterpret_cast<unsigned char*>(first_s) +
+                               (((size_t)(n_sub + 1) * 8 + 15) & ~(size_t)15);
+    for (int i = threadIdx.x; i < n_sub * n; i += blockDim.x) {
+        const int s = i / n, k = i % n;
+        const int64_t src = (int64_t)s * A.L + A.axis_off + k;
+        T* dst = cbase + (size_t)s * per_sub;
+        if (MODE == 0) {
+            dst[k] = A.r[src];
+            dst[n + k] = A.cr[src];
+        } else {
+            dst[k] = (T)A.fa[src];
+            dst[n + k] = (T)A.fb[src];
+            if (MODE == 2) obase[(size_t)s * n + k] = A.isc_p1[src];
+        }
+    }
+    for (int i = threadIdx.x; i <= n_sub; i += blockDim.x) first_s[i] = S.first[i];
+    __syncthreads();
+
+    const size_t pair_bytes = (size_t)ns * 32 * sizeof(T) + 4 * 32 * sizeof(int64_t) +
+                              32 * sizeof(T);
+    unsigned char* my = pair_area + (size_t)pair * pair_bytes;
+    T* W = reinterpret_cast<T*>(my);
+    int64_t* rbF = reinterpret_cast<int64_t*>(my + (size_t)ns * 32 * sizeof(T));  // [32] copy rows
+    int64_t* rbB = rbF + 64;                                                       // [32] store rows
+    T* handover = reinterpret_cast<T*>(rbF + 128);
+
+    const int64_t tp = (int64_t)gridDim.x * pairs;
+    const int64_t b0 = (int64_t)blockIdx.x * pairs + pair;
+    if (b0 >= n_blocks) return;   // both warps of the pair leave together
+    const int64_t nb = (n_blocks - 1 - b0) / tp + 1;   // blocks of this pair
+
+    PairSweeper<T, AXIS, MODE> sw{A, W, A.in, A.field,
+                                  AXIS == 0 ? 1 : (AXIS == 1 ? A.pitch : (int64_t)A.ny * A.pitch),
+                                  n, ns, lane, 1 + pair};
+    auto coef_row = [&](int s) {
+        CoefRow<T> C;
+        const T* r = cbase + (size_t)s * per_sub;
+        C.a = r;
+        C.b = r + n;
+        C.a_lo = r;
+        C.b_lo = r;
+        C.o = obase + (size_t)s * n;
+        C.c = (MODE == 0) ? A.cvec[s * 3 + AXIS] : (T)0;
+        C.c_lo = (T)0;
+        return C;
+    };
+    const int gcount = (n + G - 1) / G;
+    const int h_top = gcount - 1;
+
+    if (!is_b) {
+        // ------------------------------------------------------- warp F
+        Line cur = make_line<T, AXIS, MODE>(A, S, first_s, b0 * 32 + lane);
+        rbF[lane] = cur.base;
+        __syncwarp();
+        for (int g = 0; g < gcount; ++g) sw.template copy_group<0>(cur, rbF, g);
+        cp_async_commit();
+        cp_async_wait<0>();
+        __syncwarp();
+        CoefRow<T> C = coef_row(cur.s);
+        T prev = (T)0;
+        for (int g = 0; g < gcount; ++g) sw.template fwd_group<0>(cur, C, prev, g);
+        handover[lane] = prev;
+        sw.pair_bar();                                  // hand-over of block 0
+        for (int64_t k = 1; k < nb; ++k) {
+            const int q = (int)(k & 1);                 // parity of this block
+            Line nxt = make_line<T, AXIS, MODE>(A, S, first_s, (b0 + k * tp) * 32 + lane);
+            CoefRow<T> CN = coef_row(nxt.s);
+            __syncwarp();
+            rbF[lane] = nxt.base;
+            __syncwarp();
+            prev = (T)0;
+            for (int jg = 0; jg < gcount + LG; ++jg) {
+                const int g = jg - LG;
+                if (g >= 0) {
+                    cp_async_wait<LG - 1>();
+                    __syncwarp();
+                    if (q) sw.template fwd_group<1>(nxt, CN, prev, g);
+                    else sw.template fwd_group<0>(nxt, CN, prev, g);
+                }
+                sw.pair_bar();                          // B is done with group h
+                if (jg <= h_top) {
+                    if (q) sw.template copy_group<1>(nxt, rbF, jg);
+                    else sw.template copy_group<0>(nxt, rbF, jg);
+                }
+                cp_async_commit();
+            }
+            cp_async_wait<0>();
+            handover[lane] = prev;
+            sw.pair_bar();                              // hand-over of block k
+        }
+    } else {
+        // ------------------------------------------------------- warp B
+        sw.pair_bar();                                  // hand-over of block 0
+        Line cur = make_line<T, AXIS, MODE>(A, S, first_s, b0 * 32 + lane);
+        CoefRow<T> C = coef_row(cur.s);
+        T x = handover[lane];
+        rbB[lane] = cur.valid ? cur.base : -1;
+        __syncwarp();
+        for (int64_t k = 1; k < nb; ++k) {
+            const int q = (int)((k - 1) & 1);           // parity of the block B finishes
+            for (int jg = 0; jg < gcount + LG; ++jg) {
+                const int h = h_top - jg;
+                if (h >= 0) {
+                    if (q) sw.template bwd_group<1>(cur, C, x, h, rbB);
+                    else sw.template bwd_group<0>(cur, C, x, h, rbB);
+                }
+                sw.pair_bar();                          // group h released to F
+            }
+            sw.pair_bar();                              // hand-over of block k
+            x = handover[lane];
+            cur = make_line<T, AXIS, MODE>(A, S, first_s, (b0 + k * tp) * 32 + lane);
+            C = coef_row(cur.s);
+            __syncwarp();
+            rbB[lane] = cur.valid ? cur.base : -1;
+            __syncwarp();
+        }
+        const int q = (int)((nb - 1) & 1);
+        for (int h = h_top; h >= 0; --h) {
+            if (q) sw.template bwd_group<1>(cur, C, x, h, rbB);
+            else sw.template bwd_group<0>(cur, C, x, h, rbB);
+        }
+    }
+}
+
+}  // namespace persistent
+}  // namespace bfvm

@@ -344,6 +344,7 @@ __global__ void k_sources(T* __restrict__ field, int64_t n_entries,
 }  // namespace bfvm
 
 #include "sweep_persistent.cuh"
+#include "sweep_pair.cuh"
 
 namespace bfvm {
 namespace {
@@ -410,6 +411,25 @@ bfvm_status launch_axis(Ctx* c, const SweepArgs<T>& A)
         S.lo_a = c->d_lo_a[AXIS];
         S.cnt_a = c->d_cnt_a[AXIS];
         S.lo_b = c->d_lo_b[AXIS];
+        // FP64: one column buffer per warp pair (see sweep_pair.cuh)
+        const size_t per_pair = (size_t)32 * ns * sizeof(T) + 4 * 32 * sizeof(int64_t) +
+                                32 * sizeof(T);
+        int pairs = (int)((c->smem_optin - fixed) / per_pair);
+        if (pairs > 4) pairs = 4;
+        if (sizeof(T) == 8 && c->sweep_kernel == 0 && pairs >= 1) {
+            size_t smem = fixed + per_pair * pairs;
+            auto kern = persistent::k_sweep_pair<T, AXIS, MODE>;
+            BFVM_CUDA(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)smem));
+            int64_t n_blocks = ceil_div(first[A.n_sub], 32);
+            int64_t grid = ceil_div(n_blocks, pairs);
+            if (grid > c->sm_count) grid = c->sm_count;
+            if (c->grid_limit > 0 && grid > c->grid_limit) grid = c->grid_limit;
+            kern<<<(unsigned)grid, 64 * pairs, smem, c->stream>>>(A, S, n_blocks, ns);
+            c->launches += 1;
+            BFVM_CUDA(c, cudaGetLastError());
+            return BFVM_OK;
+        }
         size_t smem = fixed + per_warp * warps;
         auto kern = persistent::k_sweep_persistent<T, AXIS, MODE>;
         BFVM_CUDA(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -28,10 +28,12 @@ def bf():
 
 
 def run_gpu(bf, p, steps=None, precision=None, variant=None, period=None, graphs=None,
-            cells_on_device=True, grid_limit=None):
+            cells_on_device=True, grid_limit=None, sweep_kernel=None):
     sim = bf.Sim.from_problem(p, precision=precision, cells_on_device=cells_on_device)
     if grid_limit is not None:
         sim.set_option(bf.OPT_GRID_LIMIT, grid_limit)
+    if sweep_kernel is not None:
+        sim.set_option(bf.OPT_SWEEP_KERNEL, sweep_kernel)
     if variant is not None:
         sim.set_option(bf.OPT_VARIANT, variant)
     if period is not None:
@@ -69,15 +71,17 @@ CASES = {
 }
 
 
+@pytest.mark.parametrize("sweep_kernel", [0, 1])
 @pytest.mark.parametrize("grid_limit", [0, 1, 3])
 @pytest.mark.parametrize("variant", [0, 1])
 @pytest.mark.parametrize("case", sorted(CASES))
-def test_fp64_matches_oracle(bf, case, variant, grid_limit):
+def test_fp64_matches_oracle(bf, case, variant, grid_limit, sweep_kernel):
     """grid_limit 1 or 3 caps the persistent sweeps at that many CTAs, so
-    every warp walks many 32-line blocks (the interleaved path)."""
+    every warp (pair) walks many 32-line blocks; sweep_kernel selects the
+    warp-pair (0) or one-warp (1) FP64 sweep."""
     p = CASES[case]()
     ref = oracle.run(p)
-    got, info = run_gpu(bf, p, variant=variant, grid_limit=grid_limit)
+    got, info = run_gpu(bf, p, variant=variant, grid_limit=grid_limit, sweep_kernel=sweep_kernel)
     assert info["variant"] == variant
     err = rel_inf(got, ref)
     assert np.all(err <= TOL64), (case, variant, err)
