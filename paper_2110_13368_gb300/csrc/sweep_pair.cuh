@@ -105,6 +105,155 @@ struct PairSweeper {
         }
     }
 
+    // Column of element k0+u relative to row slot<Q>(k0) (compile-time u)
+    template <int Q>
+    __device__ __forceinline__ int off(int u) const
+    {
+        return (Q ? -u : u) * 32 + (AXIS == 0 ? (lane ^ (res<Q>(u) * ROWS)) : lane);
+    }
+
+    // Interior groups: all G elements exist, none is the line's last and
+    // (forward) none its first, so no element needs a test and every
+    // offset is a constant from one row pointer.
+    template <int Q>
+    __device__ __forceinline__ void copy_fast(const Line& ln, const int64_t (&rv)[G], int g) const
+    {
+        if (AXIS == 0) {
+            const int e = g * G + (lane % G);
+            const int s = slot<Q>(e);
+            const int m = res<Q>(lane % G);
+#pragma unroll
+            for (int t = 0; t < G; ++t)
+                cp_async_elem(at(s, t * ROWS + lane / G, m), fin + rv[t] + e);
+        } else {
+            T* p = W + slot<Q>(g * G) * 32;
+            const T* src = fin + ln.base + (int64_t)g * G * stride;
+#pragma unroll
+            for (int u = 0; u < G; ++u) cp_async_elem(p + off<Q>(u), src + u * stride);
+        }
+    }
+
+    template <int Q>
+    __device__ __forceinline__ void fwd_fast(const CoefRow<T>& C, T& prev, int g) const
+    {
+        T* p = W + slot<Q>(g * G) * 32;
+        const T* a = C.a + g * G;
+        T d[G];
+#pragma unroll
+        for (int u = 0; u < G; ++u) d[u] = p[off<Q>(u)];
+#pragma unroll
+        for (int u = 0; u < G; ++u) {
+            if (MODE == 0) prev = fma(C.c, prev, d[u]) * a[u];
+            else prev = fma(a[u], prev, d[u]);
+            p[off<Q>(u)] = prev;
+        }
+    }
+
+    template <int Q>
+    __device__ __forceinline__ void bwd_fast(const Line& L, const CoefRow<T>& C, T& x, int h,
+                                             const int64_t (&rv)[G]) const
+    {
+        const int k0 = h * G;
+        T* p = W + slot<Q>(k0) * 32;
+        const T* b = C.b + k0;
+        T w[G], o[G];
+#pragma unroll
+        for (int u = 0; u < G; ++u) w[u] = p[off<Q>(u)];
+#pragma unroll
+        for (int u = G - 1; u >= 0; --u) {
+            x = fma(b[u], x, w[u]);
+            o[u] = (MODE == 2) ? (T)(((double)x * C.o[k0 + u]) * L.inv_other) : x;
+        }
+        if (AXIS == 0) {
+#pragma unroll
+            for (int u = 0; u < G; ++u) p[off<Q>(u)] = o[u];
+            __syncwarp();
+            const int k = k0 + (lane % G);
+            const int s = slot<Q>(k);
+            const int m = res<Q>(lane % G);
+#pragma unroll
+            for (int t = 0; t < G; ++t)
+                if (rv[t] >= 0) fout[rv[t] + k] = *at(s, t * ROWS + lane / G, m);
+            __syncwarp();
+        } else if (L.valid) {
+            T* dst = fout + L.base + (int64_t)k0 * stride;
+#pragma unroll
+            for (int u = 0; u < G; ++u) dst[u * stride] = o[u];
+        }
+    }
+
+    // Row bases of the transposed x-sweep accesses of this lane: rows
+    // t*ROWS + lane/G of the block (from the warp's row table)
+    __device__ __forceinline__ void load_rows(const int64_t* rb, int64_t (&rv)[G]) const
+    {
+#pragma unroll
+        for (int t = 0; t < G; ++t) rv[t] = (AXIS == 0) ? rb[t * ROWS + lane / G] : 0;
+    }
+
+    // F: forward elimination of a whole block on its own (the pair's first)
+    template <int Q>
+    __device__ __forceinline__ T f_solo(const Line& L, const CoefRow<T>& C) const
+    {
+        const int gcount = (n + G - 1) / G;
+        const int f_hi = (n - 1) / G;
+        T prev = (T)0;
+        for (int g = 0; g < gcount; ++g) {
+            if (g >= 1 && g < f_hi) fwd_fast<Q>(C, prev, g);
+            else fwd_group<Q>(L, C, prev, g);
+        }
+        return prev;
+    }
+
+    // F: copies and forward elimination of block L (parity Q) while B
+    // back-substitutes the previous block; one pair barrier per group.
+    template <int Q>
+    __device__ __forceinline__ T f_block(const Line& L, const CoefRow<T>& C, const int64_t* rb,
+                                         const int64_t (&rv)[G]) const
+    {
+        const int gcount = (n + G - 1) / G;
+        const int h_top = gcount - 1;
+        const int f_hi = (n - 1) / G;   // forward groups [1, f_hi) are interior
+        const int c_hi = n / G;         // copy groups [0, c_hi) are full
+        T prev = (T)0;
+        for (int jg = 0; jg < gcount + LG; ++jg) {
+            const int g = jg - LG;
+            if (g >= 0) {
+                cp_async_wait<LG - 1>();
+                __syncwarp();
+                if (g >= 1 && g < f_hi) fwd_fast<Q>(C, prev, g);
+                else fwd_group<Q>(L, C, prev, g);
+            }
+            pair_bar();                                  // B is done with group h_top - jg
+            if (jg <= h_top) {
+                if (jg < c_hi) copy_fast<Q>(L, rv, jg);
+                else copy_group<Q>(L, rb, jg);
+            }
+            cp_async_commit();
+        }
+        return prev;
+    }
+
+    // B: back substitution of block L (parity Q); with `paired`, the group
+    // loop meets F at the pair barrier gcount + LG times.
+    template <int Q>
+    __device__ __forceinline__ void b_block(const Line& L, const CoefRow<T>& C, T& x,
+                                            const int64_t* rb, const int64_t (&rv)[G],
+                                            bool paired) const
+    {
+        const int gcount = (n + G - 1) / G;
+        const int h_top = gcount - 1;
+        const int b_hi = (n - 1) / G;   // backward groups [0, b_hi) are interior
+        const int iters = gcount + (paired ? LG : 0);
+        for (int jg = 0; jg < iters; ++jg) {
+            const int h = h_top - jg;
+            if (h >= 0) {
+                if (h < b_hi) bwd_fast<Q>(L, C, x, h, rv);
+                else bwd_group<Q>(L, C, x, h, rb);
+            }
+            if (paired) pair_bar();                      // group h released to F
+        }
+    }
+
     // B: back substitution of group h (parity Q) and its output
     template <int Q>
     __device__ __forceinline__ void bwd_group(const Line& L, const CoefRow<T>& C, T& x, int h,
@@ -221,7 +370,6 @@ __global__ void __launch_bounds__(256, 1) k_sweep_pair(SweepArgs<T> A, LineSet S
         return C;
     };
     const int gcount = (n + G - 1) / G;
-    const int h_top = gcount - 1;
 
     if (!is_b) {
         // ------------------------------------------------------- warp F
@@ -232,34 +380,19 @@ __global__ void __launch_bounds__(256, 1) k_sweep_pair(SweepArgs<T> A, LineSet S
         cp_async_commit();
         cp_async_wait<0>();
         __syncwarp();
-        CoefRow<T> C = coef_row(cur.s);
-        T prev = (T)0;
-        for (int g = 0; g < gcount; ++g) sw.template fwd_group<0>(cur, C, prev, g);
+        T prev = sw.template f_solo<0>(cur, coef_row(cur.s));
         handover[lane] = prev;
         sw.pair_bar();                                  // hand-over of block 0
+        int64_t rv[G];
         for (int64_t k = 1; k < nb; ++k) {
-            const int q = (int)(k & 1);                 // parity of this block
             Line nxt = make_line<T, AXIS, MODE>(A, S, first_s, (b0 + k * tp) * 32 + lane);
             CoefRow<T> CN = coef_row(nxt.s);
             __syncwarp();
             rbF[lane] = nxt.base;
             __syncwarp();
-            prev = (T)0;
-            for (int jg = 0; jg < gcount + LG; ++jg) {
-                const int g = jg - LG;
-                if (g >= 0) {
-                    cp_async_wait<LG - 1>();
-                    __syncwarp();
-                    if (q) sw.template fwd_group<1>(nxt, CN, prev, g);
-                    else sw.template fwd_group<0>(nxt, CN, prev, g);
-                }
-                sw.pair_bar();                          // B is done with group h
-                if (jg <= h_top) {
-                    if (q) sw.template copy_group<1>(nxt, rbF, jg);
-                    else sw.template copy_group<0>(nxt, rbF, jg);
-                }
-                cp_async_commit();
-            }
+            sw.load_rows(rbF, rv);
+            if (k & 1) prev = sw.template f_block<1>(nxt, CN, rbF, rv);
+            else prev = sw.template f_block<0>(nxt, CN, rbF, rv);
             cp_async_wait<0>();
             handover[lane] = prev;
             sw.pair_bar();                              // hand-over of block k
@@ -272,16 +405,12 @@ __global__ void __launch_bounds__(256, 1) k_sweep_pair(SweepArgs<T> A, LineSet S
         T x = handover[lane];
         rbB[lane] = cur.valid ? cur.base : -1;
         __syncwarp();
+        int64_t rv[G];
+        sw.load_rows(rbB, rv);
         for (int64_t k = 1; k < nb; ++k) {
-            const int q = (int)((k - 1) & 1);           // parity of the block B finishes
-            for (int jg = 0; jg < gcount + LG; ++jg) {
-                const int h = h_top - jg;
-                if (h >= 0) {
-                    if (q) sw.template bwd_group<1>(cur, C, x, h, rbB);
-                    else sw.template bwd_group<0>(cur, C, x, h, rbB);
-                }
-                sw.pair_bar();                          // group h released to F
-            }
+            // parity of the block B finishes: that of block k-1
+            if ((k - 1) & 1) sw.template b_block<1>(cur, C, x, rbB, rv, true);
+            else sw.template b_block<0>(cur, C, x, rbB, rv, true);
             sw.pair_bar();                              // hand-over of block k
             x = handover[lane];
             cur = make_line<T, AXIS, MODE>(A, S, first_s, (b0 + k * tp) * 32 + lane);
@@ -289,12 +418,10 @@ __global__ void __launch_bounds__(256, 1) k_sweep_pair(SweepArgs<T> A, LineSet S
             __syncwarp();
             rbB[lane] = cur.valid ? cur.base : -1;
             __syncwarp();
+            sw.load_rows(rbB, rv);
         }
-        const int q = (int)((nb - 1) & 1);
-        for (int h = h_top; h >= 0; --h) {
-            if (q) sw.template bwd_group<1>(cur, C, x, h, rbB);
-            else sw.template bwd_group<0>(cur, C, x, h, rbB);
-        }
+        if ((nb - 1) & 1) sw.template b_block<1>(cur, C, x, rbB, rv, false);
+        else sw.template b_block<0>(cur, C, x, rbB, rv, false);
     }
 }
 
