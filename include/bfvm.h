@@ -196,13 +196,24 @@ bfvm_status bfvm_get_info(const bfvm_ctx* ctx, int64_t* info);
  *          default); small caps make every warp walk many line blocks
  *   key 7  FP64 sweep kernel: 0 warp pairs sharing each line buffer (the
  *          default), 1 one warp per line buffer
+ *   key 8  with the rescaled FP64 form and warp pairs: 1 (the default) runs
+ *          the x, y and z sweeps of a step as one persistent launch whose
+ *          warp pairs take (axis, substrate, 32-line block) tasks in order,
+ *          a task starting once the previous axis of its substrate is
+ *          complete; 0 launches one kernel per axis
+ *   key 9  test of the bounded device waits of key 8's launch: a value
+ *          v > 0 makes every dependency wait unreachable and give up after
+ *          v polls, so the next synchronising call reports BFVM_ETIMEOUT
+ *          (results of such steps are not valid); 0 (the default) is normal
+ *          operation
  */
 bfvm_status bfvm_set_option(bfvm_ctx* ctx, int32_t key, int64_t value);
 
 /*
  * Device time of the kernels timed under option 5, accumulated since the
- * last reset.  ms[4] (milliseconds) and counts[4] (launches) are host
- * arrays indexed by kind: 0 x sweep, 1 y sweep, 2 z sweep, 3 cell sources;
+ * last reset.  ms[5] (milliseconds) and counts[5] (launches) are host
+ * arrays indexed by kind: 0 x sweep, 1 y sweep, 2 z sweep, 3 cell sources
+ * and Dirichlet shell, 4 the x, y and z sweeps as one launch (option 8);
  * either may be NULL.  Synchronises the context's stream.  reset != 0 zeroes
  * the totals after reading them.
  */

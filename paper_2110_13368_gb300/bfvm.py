@@ -30,6 +30,8 @@ OPT_GRAPHS = 4
 OPT_TIME_KERNELS = 5
 OPT_GRID_LIMIT = 6
 OPT_SWEEP_KERNEL = 7
+OPT_FUSED_STEP = 8
+OPT_WAIT_TEST = 9
 
 EXPORTED = ["bfvm_create", "bfvm_destroy", "bfvm_set_density", "bfvm_get_density",
             "bfvm_set_cells", "bfvm_step", "bfvm_sync", "bfvm_record", "bfvm_backward",
@@ -230,9 +232,10 @@ def bfvm_set_option(h, key, value):
 
 
 def bfvm_kernel_times(h, reset=True):
-    """(ms[4], launches[4]) per kernel kind: x, y, z sweep, sources."""
-    ms = (ctypes.c_double * 4)()
-    n = (_i64 * 4)()
+    """(ms[5], launches[5]) per kernel kind: x, y, z sweep, sources and
+    shell, and the three sweeps as one launch."""
+    ms = (ctypes.c_double * 5)()
+    n = (_i64 * 5)()
     _check(load_library().bfvm_kernel_times(h, ms, n, int(bool(reset))), h)
     return list(ms), list(n)
 

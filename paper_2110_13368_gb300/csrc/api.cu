@@ -27,6 +27,18 @@ bfvm_status cuda_err(Ctx* c, cudaError_t e, const char* what)
     return set_err(c, e == cudaErrorMemoryAllocation ? BFVM_ENOMEM : BFVM_ECUDA, m);
 }
 
+// Flag 1 of d_err: a bounded device wait of the one-launch step gave up.
+// Read (and cleared) after the stream is idle.
+bfvm_status check_wait_flag(Ctx* c)
+{
+    if (!c->d_err) return BFVM_OK;
+    int flag = 0;
+    BFVM_CUDA(c, cudaMemcpy(&flag, c->d_err + 1, sizeof(int), cudaMemcpyDeviceToHost));
+    if (!flag) return BFVM_OK;
+    BFVM_CUDA(c, cudaMemset(c->d_err + 1, 0, sizeof(int)));
+    return set_err(c, BFVM_ETIMEOUT, "a device wait of the step kernel gave up (result not valid)");
+}
+
 namespace {
 
 size_t elem_size(const Ctx* c) { return c->precision == 64 ? 8 : 4; }
@@ -81,6 +93,7 @@ bfvm_status launch_graph_block(Ctx* c, int len)
         }
         c->stream = saved;
         cudaStreamDestroy(cs);
+        c->period_graph_launches = c->launches - launches_before;   // kernels in the graph
         c->launches = launches_before;
         if (st != BFVM_OK) {
             drop_graphs(c);
@@ -89,7 +102,7 @@ bfvm_status launch_graph_block(Ctx* c, int len)
         c->period_graph_len = len;
     }
     BFVM_CUDA(c, cudaGraphLaunch(c->period_graph, c->stream));
-    c->launches += (int64_t)len * sweep_kernel_count_per_step(c);
+    c->launches += c->period_graph_launches;
     return BFVM_OK;
 }
 
@@ -235,6 +248,8 @@ bfvm_status bfvm_create(bfvm_ctx** out, int32_t nx, int32_t ny, int32_t nz, doub
     if ((e = cudaMalloc(&c->d_bc_kind, sizeof(int32_t) * n_sub)) != cudaSuccess) return fail(cuda_err(c, e, "bc"));
     if ((e = cudaMalloc(&c->d_bc_value, sizeof(double) * n_sub)) != cudaSuccess) return fail(cuda_err(c, e, "bc"));
     if ((e = cudaMalloc(&c->d_err, sizeof(int) * 4)) != cudaSuccess) return fail(cuda_err(c, e, "flags"));
+    if ((e = cudaMemsetAsync(c->d_err, 0, sizeof(int) * 4, c->stream)) != cudaSuccess)
+        return fail(cuda_err(c, e, "flags memset"));
     cudaMemcpyAsync(c->d_bc_kind, bc_kind, sizeof(int32_t) * n_sub, cudaMemcpyHostToDevice, c->stream);
     cudaMemcpyAsync(c->d_bc_value, bc_value, sizeof(double) * n_sub, cudaMemcpyHostToDevice, c->stream);
     bfvm_status st = build_coefficients(c);
@@ -292,7 +307,9 @@ bfvm_status bfvm_get_density(bfvm_ctx* h, void* out, int32_t on_device)
     if (!h) return BFVM_EINVAL;
     Ctx* c = &h->impl;
     if (!out) return set_err(c, BFVM_EINVAL, "out is NULL");
-    return copy_out_dense(c, out, on_device != 0);
+    bfvm_status st = copy_out_dense(c, out, on_device != 0);
+    if (st != BFVM_OK || on_device) return st;
+    return check_wait_flag(c);
 }
 
 bfvm_status bfvm_set_cells(bfvm_ctx* h, int64_t n_cells, const double* pos, const double* vol,
@@ -391,7 +408,7 @@ bfvm_status bfvm_sync(bfvm_ctx* h)
     Ctx* c = &h->impl;
     BFVM_CUDA(c, cudaStreamSynchronize(c->stream));
     BFVM_CUDA(c, cudaGetLastError());
-    return BFVM_OK;
+    return check_wait_flag(c);
 }
 
 bfvm_status bfvm_record(bfvm_ctx* h, int32_t checkpoint_every)
@@ -467,7 +484,7 @@ bfvm_status bfvm_kernel_times(bfvm_ctx* h, double* ms, int64_t* counts, int32_t 
     c->ev_start.clear();
     c->ev_stop.clear();
     c->ev_kind.clear();
-    for (int k = 0; k < 4; ++k) {
+    for (int k = 0; k < 5; ++k) {
         if (ms) ms[k] = c->kt_ms[k];
         if (counts) counts[k] = c->kt_n[k];
         if (reset) {
@@ -537,6 +554,16 @@ bfvm_status bfvm_set_option(bfvm_ctx* h, int32_t key, int64_t value)
         case 7:
             if (value != 0 && value != 1) return set_err(c, BFVM_EINVAL, "sweep kernel must be 0 or 1");
             c->sweep_kernel = (int)value;
+            drop_graphs(c);
+            return BFVM_OK;
+        case 8:
+            if (value != 0 && value != 1) return set_err(c, BFVM_EINVAL, "fused step must be 0 or 1");
+            c->fused_step = (int)value;
+            drop_graphs(c);
+            return BFVM_OK;
+        case 9:
+            if (value < 0 || value > 1000000) return set_err(c, BFVM_EINVAL, "poll limit must be 0..1e6");
+            c->wait_test_polls = (int)value;
             drop_graphs(c);
             return BFVM_OK;
         default:

@@ -88,10 +88,14 @@ struct Ctx {
     int use_graphs = 1;
     int grid_limit = 0;           // cap on persistent sweep CTAs (0 = one per SM)
     int sweep_kernel = 0;         // FP64: 0 warp pairs, 1 one warp per buffer
+    int fused_step = 1;           // FP64 rescaled pairs: 1 one launch for x, y, z
+    int wait_test_polls = 0;      // > 0: the step's dependency waits cannot end and
+                                  // give up after this many polls (tests only)
     int scale_state = 0;          // rescale state p of the stored field
 
     cudaGraphExec_t period_graph = nullptr;
     int period_graph_len = 0;
+    int64_t period_graph_launches = 0;   // kernel launches captured in it
 
     // recording for the adjoint
     int record_every = 0;
@@ -131,8 +135,19 @@ struct Ctx {
         line_tables_ready[axis] = true;
         return cudaSuccess;
     }
+    // task list of the one-launch step (see sweep_step.cuh): first task of
+    // each (axis, substrate), and the scheduling counters [claim, exit,
+    // done[3][n_sub]] (zero between launches)
+    int* d_task_first = nullptr;
+    unsigned* d_sched = nullptr;
+    int n_tasks = 0;
     void free_line_tables()
     {
+        if (d_task_first) cudaFree(d_task_first);
+        if (d_sched) cudaFree(d_sched);
+        d_task_first = nullptr;
+        d_sched = nullptr;
+        n_tasks = 0;
         for (int a = 0; a < 3; ++a) {
             if (d_first[a]) cudaFree(d_first[a]);
             if (d_lo_a[a]) cudaFree(d_lo_a[a]);
@@ -144,12 +159,12 @@ struct Ctx {
     }
 
     // optional per-kernel CUDA-event timing (kinds: 0 x, 1 y, 2 z sweep,
-    // 3 sources)
+    // 3 sources and shell, 4 the x, y and z sweeps as one launch)
     int time_kernels = 0;
     std::vector<cudaEvent_t> ev_start, ev_stop;
     std::vector<int> ev_kind;
-    double kt_ms[4] = {0, 0, 0, 0};
-    int64_t kt_n[4] = {0, 0, 0, 0};
+    double kt_ms[5] = {0, 0, 0, 0, 0};
+    int64_t kt_n[5] = {0, 0, 0, 0, 0};
 };
 
 // Brackets one kernel launch with CUDA events when timing is enabled.
@@ -178,6 +193,7 @@ struct KernelTimer {
 // ------------------------------------------------------------ helpers
 bfvm_status set_err(Ctx* c, bfvm_status st, const std::string& msg);
 bfvm_status cuda_err(Ctx* c, cudaError_t e, const char* what);
+bfvm_status check_wait_flag(Ctx* c);
 
 #define BFVM_CUDA(ctx, call)                                  \
     do {                                                      \
@@ -194,7 +210,6 @@ bfvm_status launch_step(Ctx* c, int p, bool renorm);
 bfvm_status launch_shell_fill(Ctx* c, int p_scale);
 bfvm_status build_line_tables(Ctx* c);
 bfvm_status launch_unscale_copy(Ctx* c, void* out_dev, int p);
-int sweep_kernel_count_per_step(const Ctx* c);
 
 // sources (sources.cu)
 bfvm_status build_sources(Ctx* c, int64_t n_cells, const double* pos,

@@ -206,16 +206,21 @@ struct PairSweeper {
 
     // F: copies and forward elimination of block L (parity Q) while B
     // back-substitutes the previous block; one pair barrier per group.
+    // `iters` (default gcount + LG) is the number of barrier meetings: the
+    // step kernel pairs blocks of different line lengths and passes the
+    // larger count to both warps; iterations past this block's groups only
+    // meet the barrier.
     template <int Q>
     __device__ __forceinline__ T f_block(const Line& L, const CoefRow<T>& C, const int64_t* rb,
-                                         const int64_t (&rv)[G]) const
+                                         const int64_t (&rv)[G], int iters = -1) const
     {
         const int gcount = (n + G - 1) / G;
         const int h_top = gcount - 1;
         const int f_hi = (n - 1) / G;   // forward groups [1, f_hi) are interior
         const int c_hi = n / G;         // copy groups [0, c_hi) are full
+        if (iters < 0) iters = gcount + LG;
         T prev = (T)0;
-        for (int jg = 0; jg < gcount + LG; ++jg) {
+        for (int jg = 0; jg < iters; ++jg) {
             const int g = jg - LG;
             if (g >= 0) {
                 cp_async_wait<LG - 1>();
@@ -234,16 +239,17 @@ struct PairSweeper {
     }
 
     // B: back substitution of block L (parity Q); with `paired`, the group
-    // loop meets F at the pair barrier gcount + LG times.
+    // loop meets F at the pair barrier `iters` times (default gcount + LG).
     template <int Q>
     __device__ __forceinline__ void b_block(const Line& L, const CoefRow<T>& C, T& x,
                                             const int64_t* rb, const int64_t (&rv)[G],
-                                            bool paired) const
+                                            bool paired, int iters = -1) const
     {
         const int gcount = (n + G - 1) / G;
         const int h_top = gcount - 1;
         const int b_hi = (n - 1) / G;   // backward groups [0, b_hi) are interior
-        const int iters = gcount + (paired ? LG : 0);
+        if (!paired) iters = gcount;
+        else if (iters < 0) iters = gcount + LG;
         for (int jg = 0; jg < iters; ++jg) {
             const int h = h_top - jg;
             if (h >= 0) {
@@ -309,8 +315,11 @@ __global__ void __launch_bounds__(256, 1) k_sweep_pair(SweepArgs<T> A, LineSet S
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int pairs = blockDim.x >> 6;
-    const int pair = warp >> 1;
-    const bool is_b = (warp & 1) != 0;   // B: back substitution; F: copies + forward
+    // warps p and p + pairs form pair p: with four pairs the F warps sit on
+    // the four SMSPs (warp % 4), so the pipe is fed from all of them also
+    // while the partner warps wait (a pair's first and last block)
+    const int pair = warp % pairs;
+    const bool is_b = warp >= pairs;     // B: back substitution; F: copies + forward
     const int n = A.n;
     const int ns = n_slots;
     const int n_sub = A.n_sub;

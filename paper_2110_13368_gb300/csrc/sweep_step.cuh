@@ -1,0 +1,501 @@
+// The three sweeps of one step (FP64, rescaled form) as one persistent
+// launch (included by sweeps.cu after sweep_pair.cuh, whose PairSweeper it
+// drives).
+//
+// Why: one pair of warps sweeps a 32-line block in one phase (the forward
+// elimination of block k+1 next to the back substitution of block k).  A
+// separate launch per axis gives each pair only a few blocks, and every
+// launch pays a phase in which one warp of each pair has nothing to do (the
+// first block's forward and the last block's back substitution), plus the
+// tail where the pairs that drew one block more than the rest finish
+// alone.  Here the pairs keep their pipeline running across axes and
+// substrates, so that cost is paid once per step.
+//
+// Tasks: (axis a, substrate s, block j) with blocks of 32 lines of the line
+// set of (a, s) (lines entirely on a Dirichlet shell are not in the set;
+// blocks never straddle substrates), numbered axis-major: all x tasks of
+// substrate 0, of substrate 1, ..., then the y tasks, then the z tasks.
+// task_first[a * n_sub + s] is the first task of (a, s).
+//
+// Dependencies: a task of (a, s) with a > 0 reads lines that every task of
+// (a - 1, s) writes, so it starts only when done[a - 1][s] (tasks of
+// (a - 1, s) completed) reaches their count.  With several substrates the
+// order above leaves the tasks of the other substrates between a task and
+// its dependencies, so the wait is normally over before it starts.
+//
+// Scheduling: each pair's F warp claims the next task from a counter
+// (atomicAdd), so tasks are claimed in order by pairs that are running; a
+// claimed task only waits on tasks with smaller numbers.  A pair never
+// blocks while it holds a task that another task needs: when F claims a task
+// whose input is not complete yet, B back-substitutes its current task on
+// its own (no pair barriers), signals its completion, and only then does F
+// wait.  So the smallest unfinished task always progresses, and every wait
+// ends.  Waits are still bounded (kMaxPolls polls): on expiry the kernel sets
+// the error flag (reported as BFVM_ETIMEOUT by the next synchronising call)
+// and carries on.
+//
+// Memory ordering: B makes its stores visible (fence) before lane 0 adds to
+// done[a][s]; F reads done with ld.acquire and then every lane executes an
+// acquire fence, so the copies that follow (cp.async through L1) see the
+// other SMs' writes and no L1 line left from an earlier task of this SM.
+//
+// The counters (claim, exit, done) are zero at every launch: the last CTA to
+// finish resets them, and the next launch is ordered after this one on the
+// stream.
+#pragma once
+
+namespace bfvm {
+namespace persistent {
+
+struct StepSched {
+    unsigned* claim;        // [1] next task to hand out
+    unsigned* exit_count;   // [1] CTAs that have finished
+    unsigned* done;         // [3 * n_sub] completed tasks per (axis, substrate)
+    const int* task_first;  // [3 * n_sub + 1] first task of (axis, substrate)
+    int* err;               // set to 1 when a dependency wait gave up
+    int n_sub;
+    int n_tasks;
+    unsigned max_polls;     // polls before a wait gives up (kMaxPolls)
+    unsigned extra_need;    // 0; 1 only to test the give-up path (no wait can end)
+};
+
+// about 2^21 polls with a 128 ns back-off: well over a second
+constexpr unsigned kMaxPolls = 1u << 21;
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void fence_acq_rel_gpu()
+{
+    asm volatile("fence.acq_rel.gpu;" ::: "memory");
+}
+
+struct TaskRef {
+    int a, s, j;   // axis, substrate, block within (a, s)
+};
+
+__device__ __forceinline__ TaskRef decode_task(const int* tf, int n_sub, int t)
+{
+    int i = 0;
+    const int last = 3 * n_sub;
+    while (i + 1 < last && t >= tf[i + 1]) ++i;
+    TaskRef r;
+    r.a = i / n_sub;
+    r.s = i % n_sub;
+    r.j = t - tf[i];
+    return r;
+}
+
+// F warp: next task number (n_tasks when none is left)
+__device__ __forceinline__ int claim_task(const StepSched& Q, int lane)
+{
+    unsigned t = 0;
+    if (lane == 0) t = atomicAdd(Q.claim, 1u);
+    t = __shfl_sync(0xffffffffu, t, 0);
+    return t < (unsigned)Q.n_tasks ? (int)t : Q.n_tasks;
+}
+
+// F warp: is the input of task r complete?  (no waiting)
+__device__ __forceinline__ bool task_ready(const StepSched& Q, const int* tf, TaskRef r, int lane)
+{
+    if (r.a == 0) return true;
+    const int i = (r.a - 1) * Q.n_sub + r.s;
+    const unsigned need = (unsigned)(tf[i + 1] - tf[i]) + Q.extra_need;
+    int ok = 0;
+    if (lane == 0) ok = ld_acquire_u32(Q.done + i) >= need;
+    ok = __shfl_sync(0xffffffffu, ok, 0);
+    if (ok) fence_acq_rel_gpu();
+    return ok != 0;
+}
+
+// F warp: wait (bounded) until the input of task r is complete
+__device__ __forceinline__ void task_wait(const StepSched& Q, const int* tf, TaskRef r, int lane)
+{
+    if (r.a == 0) return;
+    const int i = (r.a - 1) * Q.n_sub + r.s;
+    const unsigned need = (unsigned)(tf[i + 1] - tf[i]) + Q.extra_need;
+    if (lane == 0) {
+        unsigned polls = 0;
+        while (ld_acquire_u32(Q.done + i) < need) {
+            if (++polls > Q.max_polls) {
+                atomicExch(Q.err, 1);
+                break;
+            }
+            __nanosleep(128);
+        }
+    }
+    __syncwarp();
+    fence_acq_rel_gpu();
+}
+
+// B warp: all of task r's outputs are stored; publish its completion
+__device__ __forceinline__ void task_done(const StepSched& Q, TaskRef r, int lane)
+{
+    __threadfence();
+    __syncwarp();
+    if (lane == 0) atomicAdd(Q.done + r.a * Q.n_sub + r.s, 1u);
+}
+
+// Line of this lane in task r (padding lanes past the set's end repeat its
+// last line and are not stored)
+template <int AXIS, int MODE>
+__device__ __forceinline__ Line task_line(const SweepArgs<double>& A, const LineSet& S,
+                                          const int64_t* fs, TaskRef r, int lane)
+{
+    const int64_t hi = fs[r.s + 1];
+    int64_t line = fs[r.s] + (int64_t)r.j * 32 + lane;
+    const bool valid = line < hi;
+    if (!valid) line = hi - 1;
+    Line L = make_line<double, AXIS, MODE>(A, S, fs, line);
+    L.valid = valid;
+    return L;
+}
+
+// Coefficient rows of substrate s on this axis: the forward and backward
+// coefficients from the kernel's shared copies cfa / cfb ([s][L]; every lane
+// of a task has the same s, so each read is a broadcast), the output scales
+// of a renormalising z sweep from global memory
+__device__ __forceinline__ CoefRow<double> step_coef_row(const SweepArgs<double>& A,
+                                                         const double* cfa, const double* cfb,
+                                                         int s)
+{
+    CoefRow<double> C;
+    const int64_t row = (int64_t)s * A.L + A.axis_off;
+    C.a = cfa + row;
+    C.b = cfb + row;
+    C.a_lo = C.a;
+    C.b_lo = C.b;
+    C.o = A.isc_p1 + row;
+    C.c = 0.0;
+    C.c_lo = 0.0;
+    return C;
+}
+
+__device__ __forceinline__ int64_t axis_stride(const SweepArgs<double>& A, int axis)
+{
+    return axis == 0 ? 1 : (axis == 1 ? A.pitch : (int64_t)A.ny * A.pitch);
+}
+
+// F: copies and forward elimination of task r with slot parity q; solo:
+// the whole task on its own, else next to B's back substitution with
+// `iters` pair-barrier meetings.  Returns the chain value of the last
+// element (handed to B).
+template <int AXIS, int MODE>
+__device__ __forceinline__ double f_task(const SweepArgs<double>& A, const LineSet& S,
+                                         const int64_t* fs, double* field, const double* cfa,
+                                         const double* cfb, double* W, int ns, int lane,
+                                         int bar_id, TaskRef r, int64_t* rbF, int q, bool solo,
+                                         int iters)
+{
+    constexpr int G = Groups<double>::G;
+    PairSweeper<double, AXIS, MODE> sw{A, W, field, field, axis_stride(A, AXIS), A.n, ns, lane,
+                                       bar_id};
+    const Line L = task_line<AXIS, MODE>(A, S, fs, r, lane);
+    const CoefRow<double> C = step_coef_row(A, cfa, cfb, L.s);
+    __syncwarp();
+    rbF[lane] = L.base;
+    __syncwarp();
+    int64_t rv[G];
+    sw.load_rows(rbF, rv);
+    double prev;
+    if (solo) {
+        const int gcount = (A.n + G - 1) / G;
+        for (int g = 0; g < gcount; ++g) {
+            if (q) sw.template copy_group<1>(L, rbF, g);
+            else sw.template copy_group<0>(L, rbF, g);
+        }
+        cp_async_commit();
+        cp_async_wait<0>();
+        __syncwarp();
+        prev = q ? sw.template f_solo<1>(L, C) : sw.template f_solo<0>(L, C);
+    } else {
+        prev = q ? sw.template f_block<1>(L, C, rbF, rv, iters)
+                 : sw.template f_block<0>(L, C, rbF, rv, iters);
+        cp_async_wait<0>();
+    }
+    return prev;
+}
+
+// B: back substitution of task r (parity q) from chain value x, with or
+// without F next to it
+template <int AXIS, int MODE>
+__device__ __forceinline__ void b_task(const SweepArgs<double>& A, const LineSet& S,
+                                       const int64_t* fs, double* field, const double* cfa,
+                                       const double* cfb, double* W, int ns, int lane,
+                                       int bar_id, TaskRef r, int64_t* rbB, int q, double x,
+                                       bool paired, int iters)
+{
+    constexpr int G = Groups<double>::G;
+    PairSweeper<double, AXIS, MODE> sw{A, W, field, field, axis_stride(A, AXIS), A.n, ns, lane,
+                                       bar_id};
+    const Line L = task_line<AXIS, MODE>(A, S, fs, r, lane);
+    const CoefRow<double> C = step_coef_row(A, cfa, cfb, L.s);
+    __syncwarp();
+    rbB[lane] = L.valid ? L.base : -1;
+    __syncwarp();
+    int64_t rv[G];
+    sw.load_rows(rbB, rv);
+    if (q) sw.template b_block<1>(L, C, x, rbB, rv, paired, iters);
+    else sw.template b_block<0>(L, C, x, rbB, rv, paired, iters);
+}
+
+__device__ __forceinline__ void pair_sync(int bar_id)
+{
+    asm volatile("bar.sync %0, 64;" ::"r"(bar_id) : "memory");
+}
+
+// What a pair's two warps share besides the column buffer.
+struct PairShared {
+    double* field;         // the field (read and written in place)
+    const double* cfa;     // shared forward coefficients [s][L]
+    const double* cfb;     // shared backward coefficients [s][L]
+    int64_t* rbF;          // [32] row bases of F's task (x tasks)
+    int64_t* rbB;          // [32] row bases of B's task
+    double* handover;      // [32] chain values of the task handed to B
+    volatile int* ho;      // task handed over, next task, paired (0/1)
+    double* W;             // column buffer
+    int ns, lane, bar_id;
+};
+
+// Group count of an axis' lines
+__device__ __forceinline__ int axis_groups(const SweepArgs<double>* sA, int a)
+{
+    constexpr int G = Groups<double>::G;
+    return (sA[a].n + G - 1) / G;
+}
+
+// State of a pair's F warp between tasks
+struct FState {
+    int t;        // task whose forward elimination is due (n_tasks: none)
+    int k;        // its index among this pair's tasks (slot parity k & 1)
+    bool solo;    // on its own (first task, or B finished its task alone)
+    int iters;    // pair-barrier meetings when not solo
+};
+
+// F warp: the forward eliminations of consecutive tasks on axis AXIS, each
+// followed by the claim of the next task and the hand-over to B.  Tasks are
+// claimed in increasing order, so a warp's axis never goes back and the
+// three axes run as three loops with their own specialised code.
+template <int AXIS, int MODE>
+__device__ __forceinline__ void f_axis(FState& f, const SweepArgs<double>& A, const LineSet& S,
+                                       const int64_t* fs, const SweepArgs<double>* sA,
+                                       const StepSched& Q, const int* tf, const PairShared& P)
+{
+    constexpr int LG = Groups<double>::LAG_GROUPS;
+    const int T = Q.n_tasks;
+    while (f.t < T) {
+        const TaskRef r = decode_task(tf, Q.n_sub, f.t);
+        if (r.a != AXIS) return;
+        const double prev = f_task<AXIS, MODE>(A, S, fs, P.field, P.cfa, P.cfb, P.W, P.ns, P.lane,
+                                                P.bar_id, r, P.rbF, f.k & 1, f.solo, f.iters);
+        const int t_next = claim_task(Q, P.lane);
+        bool paired = false;
+        TaskRef rn{0, 0, 0};
+        if (t_next < T) {
+            rn = decode_task(tf, Q.n_sub, t_next);
+            paired = task_ready(Q, tf, rn, P.lane);
+        }
+        P.handover[P.lane] = prev;
+        if (P.lane == 0) {
+            P.ho[0] = f.t;
+            P.ho[1] = t_next;
+            P.ho[2] = paired ? 1 : 0;
+        }
+        pair_sync(P.bar_id);                            // hand-over of task f.t
+        if (t_next >= T) {
+            f.t = T;
+            return;
+        }
+        if (paired) {
+            f.solo = false;
+            f.iters = max(axis_groups(sA, AXIS), axis_groups(sA, rn.a)) + LG;
+        } else {
+            task_wait(Q, tf, rn, P.lane);
+            pair_sync(P.bar_id);                        // B has finished f.t on its own
+            f.solo = true;
+            f.iters = 0;
+        }
+        f.t = t_next;
+        ++f.k;
+    }
+}
+
+// State of a pair's B warp: the task handed over last
+struct BState {
+    int t, t_next;
+    bool paired;
+    int k;
+    double x;
+};
+
+// B warp: back substitutions of consecutive tasks on axis AXIS
+template <int AXIS, int MODE>
+__device__ __forceinline__ void b_axis(BState& b, const SweepArgs<double>& A, const LineSet& S,
+                                       const int64_t* fs, const SweepArgs<double>* sA,
+                                       const StepSched& Q, const int* tf, const PairShared& P)
+{
+    constexpr int LG = Groups<double>::LAG_GROUPS;
+    const int T = Q.n_tasks;
+    while (b.t < T) {
+        const TaskRef r = decode_task(tf, Q.n_sub, b.t);
+        if (r.a != AXIS) return;
+        const bool more = b.t_next < T;
+        const bool paired = more && b.paired;
+        int iters = 0;
+        if (paired) {
+            const TaskRef rn = decode_task(tf, Q.n_sub, b.t_next);
+            iters = max(axis_groups(sA, AXIS), axis_groups(sA, rn.a)) + LG;
+        }
+        b_task<AXIS, MODE>(A, S, fs, P.field, P.cfa, P.cfb, P.W, P.ns, P.lane, P.bar_id, r, P.rbB,
+                           b.k & 1, b.x, paired, iters);
+        task_done(Q, r, P.lane);
+        if (!more) {
+            b.t = T;
+            return;
+        }
+        if (!b.paired) pair_sync(P.bar_id);             // buffer free for F
+        pair_sync(P.bar_id);                            // next hand-over
+        b.t = P.ho[0];
+        b.t_next = P.ho[1];
+        b.paired = P.ho[2] != 0;
+        b.x = P.handover[P.lane];
+        ++b.k;
+    }
+}
+
+// Dynamic shared memory: [copies of the 3 axes' SweepArgs and LineSets]
+// [task_first] [line-set prefixes of the 3 axes] [forward and backward
+// coefficients of state p, all substrates and axes: 2 x n_sub x L]
+// [per pair: column buffer (n_slots x 32), 4 x 32 row bases, 32 chain
+// values, 4 hand-over words].  n_slots = G * max over axes of ceil(n/G), so
+// the slot schedule of PairSweeper holds for any two axes.
+template <bool RENORM>
+__global__ void __launch_bounds__(256, 1)
+    k_step_pair(SweepArgs<double> A0, SweepArgs<double> A1, SweepArgs<double> A2, LineSet S0,
+                LineSet S1, LineSet S2, StepSched Q, int n_slots)
+{
+    constexpr int MZ = RENORM ? 2 : 1;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int pairs = blockDim.x >> 6;
+    const int pair = warp % pairs;
+    const bool is_b = warp >= pairs;
+    const int n_sub = Q.n_sub;
+    const int ns = n_slots;
+    const int T = Q.n_tasks;
+
+    // the launch arguments of the three axes are read from shared copies:
+    // the loop body stores to shared memory, so the compiler reloads them
+    // per task instead of keeping all three axes' values live in registers
+    SweepArgs<double>* sA = reinterpret_cast<SweepArgs<double>*>(smem_raw);
+    LineSet* sS = reinterpret_cast<LineSet*>(smem_raw + 3 * sizeof(SweepArgs<double>));
+    const size_t args_bytes =
+        (3 * sizeof(SweepArgs<double>) + 3 * sizeof(LineSet) + 15) & ~(size_t)15;
+    int* tf = reinterpret_cast<int*>(smem_raw + args_bytes);
+    const size_t tf_bytes = (((size_t)3 * n_sub + 1) * sizeof(int) + 15) & ~(size_t)15;
+    int64_t* fs = reinterpret_cast<int64_t*>(smem_raw + args_bytes + tf_bytes);  // [3][n_sub+1]
+    const size_t fs_bytes = ((size_t)3 * (n_sub + 1) * sizeof(int64_t) + 15) & ~(size_t)15;
+    const int64_t n_coef = (int64_t)n_sub * A0.L;
+    double* cfa = reinterpret_cast<double*>(smem_raw + args_bytes + tf_bytes + fs_bytes);
+    double* cfb = cfa + n_coef;
+    unsigned char* pair_area =
+        smem_raw + args_bytes + tf_bytes + fs_bytes + 2 * n_coef * sizeof(double);
+    if (threadIdx.x == 0) {
+        sA[0] = A0;
+        sA[1] = A1;
+        sA[2] = A2;
+        sS[0] = S0;
+        sS[1] = S1;
+        sS[2] = S2;
+    }
+    for (int i = threadIdx.x; i <= 3 * n_sub; i += blockDim.x) tf[i] = Q.task_first[i];
+    for (int64_t i = threadIdx.x; i < n_coef; i += blockDim.x) {
+        cfa[i] = A0.fa[i];   // the three axes share one table per state
+        cfb[i] = A0.fb[i];
+    }
+    for (int i = threadIdx.x; i <= n_sub; i += blockDim.x) {
+        fs[i] = S0.first[i];
+        fs[(n_sub + 1) + i] = S1.first[i];
+        fs[2 * (n_sub + 1) + i] = S2.first[i];
+    }
+    __syncthreads();
+    const int64_t* fs0 = fs;
+    const int64_t* fs1 = fs + (n_sub + 1);
+    const int64_t* fs2 = fs + 2 * (n_sub + 1);
+
+    const size_t pair_bytes = (size_t)ns * 32 * sizeof(double) + 4 * 32 * sizeof(int64_t) +
+                              32 * sizeof(double) + 4 * sizeof(int);
+    unsigned char* my = pair_area + (size_t)pair * pair_bytes;
+    double* W = reinterpret_cast<double*>(my);
+    int64_t* rbF = reinterpret_cast<int64_t*>(my + (size_t)ns * 32 * sizeof(double));
+    int64_t* rbB = rbF + 64;
+    double* handover = reinterpret_cast<double*>(rbF + 128);
+    volatile int* ho = reinterpret_cast<volatile int*>(handover + 32);  // t_cur, t_next, paired
+    const int bar_id = 1 + pair;
+
+    PairShared P;
+    P.field = A0.field;
+    P.cfa = cfa;
+    P.cfb = cfb;
+    P.rbF = rbF;
+    P.rbB = rbB;
+    P.handover = handover;
+    P.ho = ho;
+    P.W = W;
+    P.ns = ns;
+    P.lane = lane;
+    P.bar_id = bar_id;
+
+    if (!is_b) {
+        FState f;
+        f.t = claim_task(Q, lane);
+        f.k = 0;
+        f.solo = true;
+        f.iters = 0;
+        if (f.t < T) {
+            task_wait(Q, tf, decode_task(tf, n_sub, f.t), lane);
+        } else {
+            if (lane == 0) {
+                ho[0] = T;
+                ho[1] = T;
+                ho[2] = 0;
+            }
+            pair_sync(bar_id);                          // nothing for B
+        }
+        f_axis<0, 1>(f, sA[0], sS[0], fs0, sA, Q, tf, P);
+        f_axis<1, 1>(f, sA[1], sS[1], fs1, sA, Q, tf, P);
+        f_axis<2, MZ>(f, sA[2], sS[2], fs2, sA, Q, tf, P);
+    } else {
+        BState b;
+        pair_sync(bar_id);                              // first hand-over
+        b.t = ho[0];
+        b.t_next = ho[1];
+        b.paired = ho[2] != 0;
+        b.x = handover[lane];
+        b.k = 0;
+        b_axis<0, 1>(b, sA[0], sS[0], fs0, sA, Q, tf, P);
+        b_axis<1, 1>(b, sA[1], sS[1], fs1, sA, Q, tf, P);
+        b_axis<2, MZ>(b, sA[2], sS[2], fs2, sA, Q, tf, P);
+    }
+
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned before = atomicAdd(Q.exit_count, 1u);
+        if (before == gridDim.x - 1) {
+            // every CTA is past its last claim, wait and completion count
+            *Q.claim = 0u;
+            for (int i = 0; i < 3 * n_sub; ++i) Q.done[i] = 0u;
+            *Q.exit_count = 0u;
+            __threadfence();
+        }
+    }
+}
+
+}  // namespace persistent
+}  // namespace bfvm

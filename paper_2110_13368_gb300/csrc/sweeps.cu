@@ -16,6 +16,9 @@
 // intermediates in the field itself (the field is overwritten in place).
 #include <math.h>
 
+#include <algorithm>
+#include <vector>
+
 #include "internal.cuh"
 
 namespace bfvm {
@@ -345,6 +348,7 @@ __global__ void k_sources(T* __restrict__ field, int64_t n_entries,
 
 #include "sweep_persistent.cuh"
 #include "sweep_pair.cuh"
+#include "sweep_step.cuh"
 
 namespace bfvm {
 namespace {
@@ -462,6 +466,71 @@ bfvm_status launch_axis(Ctx* c, const SweepArgs<T>& A)
     return BFVM_OK;
 }
 
+// The x, y and z sweeps of a rescaled FP64 step as one persistent launch
+// (sweep_step.cuh).  Returns BFVM_ESTATE without launching when the context
+// does not qualify (the caller then launches the axes one by one).
+bfvm_status launch_step_fused(Ctx* c, int p, bool renorm)
+{
+    constexpr int G = persistent::Groups<double>::G;
+    if (!c->fused_step || c->sweep_kernel != 0 || !c->d_task_first || !c->d_sched ||
+        c->n_sub > 64)
+        return BFVM_ESTATE;
+    for (int a = 0; a < 3; ++a)
+        if (!c->line_tables_ready[a]) return BFVM_ESTATE;
+    const int ext[3] = {c->nx, c->ny, c->nz};
+    int ns = 0;
+    for (int a = 0; a < 3; ++a) ns = std::max(ns, (int)ceil_div(ext[a], G) * G);
+    const size_t fixed =
+        ((3 * sizeof(SweepArgs<double>) + 3 * sizeof(persistent::LineSet) + 15) & ~(size_t)15) +
+        ((((size_t)3 * c->n_sub + 1) * sizeof(int) + 15) & ~(size_t)15) +
+                         (((size_t)3 * (c->n_sub + 1) * sizeof(int64_t) + 15) & ~(size_t)15) +
+        2 * (size_t)c->n_sub * c->coef.L * sizeof(double);
+    const size_t pair_bytes = (size_t)ns * 32 * sizeof(double) + 4 * 32 * sizeof(int64_t) +
+                              32 * sizeof(double) + 4 * sizeof(int);
+    if (c->smem_optin < fixed + pair_bytes) return BFVM_ESTATE;
+    int pairs = (int)((c->smem_optin - fixed) / pair_bytes);
+    if (pairs > 4) pairs = 4;
+    // the per-axis launches stage one axis' coefficients only; where that
+    // leaves room for more pairs, they are the faster choice
+    const size_t fixed_axis = (size_t)c->n_sub * 2 * ns * sizeof(double) + 1024;
+    const int pairs_axis = (int)std::min<size_t>(4, (c->smem_optin - fixed_axis) / pair_bytes);
+    if (pairs < pairs_axis) return BFVM_ESTATE;
+    KernelTimer timer(c, 4);
+    if (c->n_tasks == 0) return BFVM_OK;
+    SweepArgs<double> A[3];
+    persistent::LineSet S[3];
+    for (int a = 0; a < 3; ++a) {
+        A[a] = make_args<double>(c, a, p, c->coef.r, c->coef.cr, c->coef.c);
+        S[a].n_sub = c->n_sub;
+        S[a].first = c->d_first[a];
+        S[a].lo_a = c->d_lo_a[a];
+        S[a].cnt_a = c->d_cnt_a[a];
+        S[a].lo_b = c->d_lo_b[a];
+    }
+    persistent::StepSched Q;
+    Q.claim = c->d_sched;
+    Q.exit_count = c->d_sched + 1;
+    Q.done = c->d_sched + 2;
+    Q.task_first = c->d_task_first;
+    Q.err = c->d_err + 1;
+    Q.n_sub = c->n_sub;
+    Q.n_tasks = c->n_tasks;
+    Q.max_polls = c->wait_test_polls > 0 ? (unsigned)c->wait_test_polls : persistent::kMaxPolls;
+    Q.extra_need = c->wait_test_polls > 0 ? 1u : 0u;
+    const size_t smem = fixed + pair_bytes * pairs;
+    int64_t grid = ceil_div(c->n_tasks, pairs);
+    if (grid > c->sm_count) grid = c->sm_count;
+    if (c->grid_limit > 0 && grid > c->grid_limit) grid = c->grid_limit;
+    auto kern = renorm ? persistent::k_step_pair<true> : persistent::k_step_pair<false>;
+    BFVM_CUDA(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem));
+    kern<<<(unsigned)grid, 64 * pairs, smem, c->stream>>>(A[0], A[1], A[2], S[0], S[1], S[2], Q,
+                                                          ns);
+    c->launches += 1;
+    BFVM_CUDA(c, cudaGetLastError());
+    return BFVM_OK;
+}
+
 template <typename T, int MODE_Z>
 bfvm_status launch_xyz(Ctx* c, int p, const T* r, const T* cr, const T* cv)
 {
@@ -521,6 +590,24 @@ bfvm_status build_line_tables(Ctx* c)
         }
         BFVM_CUDA(c, c->ensure_line_tables(axis, first));
     }
+    // task list of the one-launch step: blocks of 32 lines per (axis,
+    // substrate), numbered axis-major
+    std::vector<int> tf(3 * c->n_sub + 1, 0);
+    int64_t t = 0;
+    for (int axis = 0; axis < 3; ++axis)
+        for (int s = 0; s < c->n_sub; ++s) {
+            tf[axis * c->n_sub + s] = (int)t;
+            t += ceil_div(c->lines_first[axis][s + 1] - c->lines_first[axis][s], 32);
+        }
+    if (t > (int64_t)1 << 30) return BFVM_OK;   // the per-axis launches handle these
+    tf[3 * c->n_sub] = (int)t;
+    c->n_tasks = (int)t;
+    BFVM_CUDA(c, cudaMalloc(&c->d_task_first, sizeof(int) * tf.size()));
+    BFVM_CUDA(c, cudaMemcpy(c->d_task_first, tf.data(), sizeof(int) * tf.size(),
+                            cudaMemcpyHostToDevice));
+    const size_t nsched = 2 + 3 * (size_t)c->n_sub;
+    BFVM_CUDA(c, cudaMalloc(&c->d_sched, sizeof(unsigned) * nsched));
+    BFVM_CUDA(c, cudaMemset(c->d_sched, 0, sizeof(unsigned) * nsched));
     return BFVM_OK;
 }
 
@@ -599,18 +686,14 @@ bfvm_status launch_step(Ctx* c, int p, bool renorm)
         if ((st = launch_shell_fill(c, -1)) != BFVM_OK) return st;
         return launch_sources(c, 0, true);
     }
-    if (renorm) st = launch_xyz<double, 2>(c, p, c->coef.r, c->coef.cr, c->coef.c);
-    else st = launch_xyz<double, 1>(c, p, c->coef.r, c->coef.cr, c->coef.c);
+    st = launch_step_fused(c, p, renorm);
+    if (st == BFVM_ESTATE) {
+        if (renorm) st = launch_xyz<double, 2>(c, p, c->coef.r, c->coef.cr, c->coef.c);
+        else st = launch_xyz<double, 1>(c, p, c->coef.r, c->coef.cr, c->coef.c);
+    }
     if (st != BFVM_OK) return st;
     if ((st = launch_shell_fill(c, renorm ? -1 : p + 1)) != BFVM_OK) return st;
     return launch_sources(c, p + 1, renorm);
-}
-
-int sweep_kernel_count_per_step(const Ctx* c)
-{
-    bool any = false;
-    for (int s = 0; s < c->n_sub; ++s) any = any || c->bc_kind[s] == BFVM_BC_DIRICHLET;
-    return 3 + (any ? 1 : 0) + (c->src.n_entries > 0 ? 1 : 0);
 }
 
 // ---------------------------------------------------------------- layout

@@ -87,6 +87,63 @@ def test_fp64_matches_oracle(bf, case, variant, grid_limit, sweep_kernel):
     assert np.all(err <= TOL64), (case, variant, err)
 
 
+FUSED_CASES = ["ragged_37x45x50", "cube_33", "thin_1x1x7", "thin_2x3x1", "flat_64x2x40",
+               "long_z_260", "no_cells_3sub", "plain_50_fullsteps"]
+
+
+@pytest.mark.parametrize("grid_limit", [0, 1, 2])
+@pytest.mark.parametrize("case", FUSED_CASES)
+def test_one_launch_step_matches_per_axis_launches(bf, case, grid_limit):
+    """The step's three sweeps as one persistent launch (option 8) compute
+    each line exactly as the per-axis launches do, so the fields agree bit
+    for bit, and both agree with the oracle.  One or two CTAs make every
+    pair take many tasks of all three axes, with dependency waits at the
+    axis boundaries (single-substrate cases) and pairs of tasks of different
+    line lengths (non-cubic grids)."""
+    p = CASES[case]()
+    ref = oracle.run(p)
+    outs = []
+    for fused in (1, 0):
+        sim = bf.Sim.from_problem(p)
+        sim.set_option(bf.OPT_VARIANT, 1)
+        sim.set_option(bf.OPT_SWEEP_KERNEL, 0)
+        sim.set_option(bf.OPT_FUSED_STEP, fused)
+        if grid_limit:
+            sim.set_option(bf.OPT_GRID_LIMIT, grid_limit)
+        n0 = sim.info()["launches"]
+        sim.step(p.steps)
+        sim.sync()
+        launches = sim.info()["launches"] - n0
+        outs.append(sim.get_density().cpu().numpy())
+        sim.close()
+        assert launches > 0
+    np.testing.assert_array_equal(outs[0], outs[1])
+    assert np.all(rel_inf(outs[0], ref) <= TOL64), rel_inf(outs[0], ref)
+
+
+def test_one_launch_step_wait_gives_up_with_status(bf):
+    """The dependency waits of the one-launch step are bounded: with option 9
+    no wait can be satisfied, each gives up after a few polls, the kernel
+    still finishes, and the next synchronising call reports BFVM_ETIMEOUT.
+    Normal operation afterwards is unaffected."""
+    p = inputs.make_problem(12, 10, 8, n_sub=1, D=[2e4], lam=[0.1], bc_kind=[0],
+                            bc_value=[0.0], n_cells=20, U=[1.0], S=[0.5], rho_star=[2.0],
+                            steps=2, seed=5)
+    sim = bf.Sim.from_problem(p)
+    sim.set_option(bf.OPT_WAIT_TEST, 200)
+    sim.step(1)
+    with pytest.raises(bf.BfvmError) as ei:
+        sim.sync()
+    assert ei.value.status == 5
+    sim.sync()                                   # the flag was cleared
+    sim.set_option(bf.OPT_WAIT_TEST, 0)
+    sim.set_density(__import__("torch").as_tensor(p.rho0, device=sim.device))
+    sim.step(p.steps)
+    got = sim.get_density().cpu().numpy()
+    sim.close()
+    assert np.all(rel_inf(got, oracle.run(p)) <= TOL64)
+
+
 def test_rescaled_across_periods_and_mid_period_reads(bf):
     """Short rescale period: the renormalising z sweep runs several times and
     the field is read while it still carries a scale."""
