@@ -253,6 +253,28 @@ const char* bfvm_batch_last_error(const bfvm_batch* batch);
 bfvm_status bfvm_batch_info(const bfvm_batch* batch, int64_t* info);
 
 /*
+ * Line-block shape of the batched sweeps.  At bfvm_batch_create a built-in
+ * autotuner times every candidate shape of each axis on scratch copies of
+ * the members' fields (the fields themselves are not touched) and keeps the
+ * fastest:
+ *   algo 0  Thomas elimination, one thread per line, one warp per 32-line
+ *           block, `warps` warps (2, 4 or 8, as far as the 32 x n line
+ *           buffers fit in shared memory) per CTA;
+ *   algo 1  parallel cyclic reduction (PCR) of the x lines, one warp per
+ *           line holding it in registers, neighbours exchanged by warp
+ *           shuffles, 4 or 8 warps per CTA; offered when no member's x line
+ *           is longer than 128 voxels.  Its per-stage multipliers depend on
+ *           the line matrix only and are built once, on the GPU, in FP64.
+ * bfvm_batch_shape reads the chosen shape of an axis (0 x, 1 y, 2 z) and
+ * ms[2] = the best measured time (ms per launch) of Thomas and of PCR
+ * (-1 where not measured).  bfvm_batch_set_shape forces a shape (EINVAL
+ * for an unsupported one).  Both give the same results up to rounding.
+ */
+bfvm_status bfvm_batch_shape(const bfvm_batch* batch, int32_t axis, int32_t* algo,
+                             int32_t* warps, double* ms);
+bfvm_status bfvm_batch_set_shape(bfvm_batch* batch, int32_t axis, int32_t algo, int32_t warps);
+
+/*
  * Allocation-free variant of the cell source/uptake update.  The paper has
  * no counterpart: it exists for callers that must not allocate device
  * memory, such as host loops driving many small simulations (cudaMalloc and

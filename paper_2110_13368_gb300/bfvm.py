@@ -38,7 +38,8 @@ EXPORTED = ["bfvm_create", "bfvm_destroy", "bfvm_set_density", "bfvm_get_density
             "bfvm_last_error", "bfvm_status_string", "bfvm_get_info", "bfvm_set_option",
             "bfvm_kernel_times",
             "bfvm_batch_create", "bfvm_batch_step", "bfvm_batch_sync", "bfvm_batch_destroy",
-            "bfvm_batch_last_error", "bfvm_batch_info", "bfvm_apply_sources_noalloc"]
+            "bfvm_batch_last_error", "bfvm_batch_info", "bfvm_batch_shape",
+            "bfvm_batch_set_shape", "bfvm_apply_sources_noalloc"]
 
 
 class BfvmError(RuntimeError):
@@ -95,6 +96,10 @@ def load_library(path: Optional[str] = None):
         lib.bfvm_batch_last_error.restype = ctypes.c_char_p
         lib.bfvm_batch_info.argtypes = [_vp, ctypes.POINTER(_i64)]
         lib.bfvm_batch_info.restype = ctypes.c_int
+        lib.bfvm_batch_shape.argtypes = [_vp, _i32, ctypes.POINTER(_i32), ctypes.POINTER(_i32), _dp]
+        lib.bfvm_batch_shape.restype = ctypes.c_int
+        lib.bfvm_batch_set_shape.argtypes = [_vp, _i32, _i32, _i32]
+        lib.bfvm_batch_set_shape.restype = ctypes.c_int
         lib.bfvm_apply_sources_noalloc.argtypes = ([_vp] + [_i32] * 4 + [ctypes.c_double] * 2
                                                    + [_i64] + [_vp] * 5 + [_vp])
         lib.bfvm_apply_sources_noalloc.restype = ctypes.c_int
@@ -279,6 +284,20 @@ def bfvm_batch_info(b):
     return {k: int(info[i]) for i, k in enumerate(keys)}
 
 
+def bfvm_batch_shape(b, axis):
+    """(algo, warps per CTA, [best Thomas ms, best PCR ms]) of an axis; algo
+    0 Thomas, 1 PCR; times -1 where not measured."""
+    algo, warps = _i32(), _i32()
+    ms = (ctypes.c_double * 2)()
+    _check(load_library().bfvm_batch_shape(b, int(axis), ctypes.byref(algo), ctypes.byref(warps),
+                                           ms), b, batch=True)
+    return int(algo.value), int(warps.value), [ms[0], ms[1]]
+
+
+def bfvm_batch_set_shape(b, axis, algo, warps):
+    _check(load_library().bfvm_batch_set_shape(b, int(axis), int(algo), int(warps)), b, batch=True)
+
+
 def bfvm_apply_sources_noalloc(rho, nx, ny, nz, dx_um, dt_min, pos, vol, S, U, rho_star,
                                stream=None):
     """Cell source/uptake update on a dense FP64 device field, in place,
@@ -313,6 +332,12 @@ class Batch:
 
     def info(self):
         return bfvm_batch_info(self.handle)
+
+    def shape(self, axis):
+        return bfvm_batch_shape(self.handle, axis)
+
+    def set_shape(self, axis, algo, warps):
+        bfvm_batch_set_shape(self.handle, axis, algo, warps)
 
     def close(self):
         if getattr(self, "handle", None) is not None:
@@ -414,3 +439,75 @@ class Sim:
             self.close()
         except Exception:
             pass
+
+
+# ------------------------------------------------------------- autograd
+_LOD_FN = None
+
+
+def _lod_function():
+    """torch.autograd.Function around a recorded forward run (bfvm_record +
+    bfvm_step) and its hand-written adjoint (bfvm_backward)."""
+    global _LOD_FN
+    if _LOD_FN is not None:
+        return _LOD_FN
+    import torch
+
+    class LODRun(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, rho0, D, lam, S, U, spec):
+            nx, ny, nz = spec["grid"]
+            sim = Sim(nx, ny, nz, spec["dx"], spec["dt"], D.detach().cpu().tolist(),
+                      lam.detach().cpu().tolist(), spec["bc_kind"], spec["bc_value"], 64,
+                      stream=spec.get("stream"), device=rho0.device)
+            try:
+                sim.set_density(rho0.detach().contiguous())
+                if spec["pos"] is not None and spec["pos"].shape[0] > 0:
+                    sim.set_cells(spec["pos"], spec["vol"], S.detach().contiguous(),
+                                  U.detach().contiguous(), spec["rho_star"])
+                sim.record(spec["checkpoint_every"])
+                sim.step(spec["steps"])
+                out = sim.get_density()
+            except Exception:
+                sim.close()
+                raise
+            ctx.sim = sim
+            ctx.shapes = (D.shape, lam.shape, S.shape, U.shape)
+            return out
+
+        @staticmethod
+        def backward(ctx, g):
+            sim = ctx.sim
+            try:
+                grads = sim.backward(g.contiguous().to(torch.float64), want_g0=True)
+            finally:
+                sim.close()
+                ctx.sim = None
+            sD, sl, sS, sU = ctx.shapes
+            dS = grads["dS"] if sim.n_cells else torch.zeros(sS, dtype=torch.float64, device=g.device)
+            dU = grads["dU"] if sim.n_cells else torch.zeros(sU, dtype=torch.float64, device=g.device)
+            return (grads["g0"], grads["dD"].reshape(sD), grads["dlambda"].reshape(sl),
+                    dS.reshape(sS), dU.reshape(sU), None)
+
+    _LOD_FN = LODRun
+    return LODRun
+
+
+def lod_run(rho0, D, lam, S, U, *, grid, dx, dt, bc_kind, bc_value, pos=None, vol=None,
+            rho_star=None, steps=1, checkpoint_every=20, stream=None):
+    """Differentiable FP64 run of `steps` LOD steps (Eq. 1) on the GPU.
+
+    rho0 [n_sub, nz, ny, nx], D and lam [n_sub], S and U [n_cells, n_sub]:
+    FP64 tensors (rho0, S, U on the GPU) that may require gradients; pos
+    [n_cells, 3], vol [n_cells] and rho_star [n_cells, n_sub] are constants.
+    Returns the field after the run.  The forward records a checkpoint every
+    `checkpoint_every` steps; the backward replays each segment from its
+    checkpoint and runs the library's adjoint kernels (bfvm_backward), giving
+    d(loss)/d(rho0, D, lambda, S, U).  A context is created per call and
+    released by the backward.
+    """
+    spec = {"grid": tuple(int(v) for v in grid), "dx": float(dx), "dt": float(dt),
+            "bc_kind": list(bc_kind), "bc_value": list(bc_value), "pos": pos, "vol": vol,
+            "rho_star": rho_star, "steps": int(steps), "checkpoint_every": int(checkpoint_every),
+            "stream": stream}
+    return _lod_function().apply(rho0, D, lam, S, U, spec)

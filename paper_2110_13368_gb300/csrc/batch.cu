@@ -157,6 +157,31 @@ void bfvm_batch_destroy(bfvm_batch* h)
 
 const char* bfvm_batch_last_error(const bfvm_batch* h) { return h ? h->impl.err.c_str() : ""; }
 
+bfvm_status bfvm_batch_shape(const bfvm_batch* h, int32_t axis, int32_t* algo, int32_t* warps,
+                             double* ms)
+{
+    if (!h || axis < 0 || axis > 2) return BFVM_EINVAL;
+    const BatchImpl* b = &h->impl;
+    if (algo) *algo = b->algo[axis];
+    if (warps) *warps = b->warps[axis];
+    if (ms) {
+        ms[0] = b->tune_ms[axis][0];
+        ms[1] = b->tune_ms[axis][1];
+    }
+    return BFVM_OK;
+}
+
+bfvm_status bfvm_batch_set_shape(bfvm_batch* h, int32_t axis, int32_t algo, int32_t warps)
+{
+    if (!h) return BFVM_EINVAL;
+    BatchImpl* b = &h->impl;
+    bfvm_status st = batch_set_shape(b, axis, algo, warps);
+    if (st != BFVM_OK)
+        return berr(b, st, "unsupported line-block shape (PCR: x lines of at most 128 voxels; "
+                           "Thomas: as many warps as the line buffers fit)");
+    return BFVM_OK;
+}
+
 bfvm_status bfvm_batch_info(const bfvm_batch* h, int64_t* info)
 {
     if (!h || !info) return BFVM_EINVAL;

@@ -257,9 +257,21 @@ struct BatchImpl {
     int graph_len = 0;
     int64_t launches = 0;
     std::string err;
+    // Line-block shape of each axis' launch, chosen by measurement when the
+    // batch is created (batch_tune): algo 0 = Thomas, one thread per line,
+    // one warp per 32-line block; algo 1 = parallel cyclic reduction, one
+    // warp per line (x lines of at most 128 voxels only); warps per CTA.
+    int algo[3] = {0, 0, 0};
+    int warps[3] = {8, 8, 8};
+    double tune_ms[3][2] = {{-1, -1}, {-1, -1}, {-1, -1}};   // best Thomas, best PCR
+    bool pcr_ok = false;          // every member's x lines are <= 128 voxels
+    int pcr_e = 1;                // elements per lane of the PCR kernel (ceil(max nx / 32))
+    double* d_pcr = nullptr;      // PCR stage tables of all members (FP64)
+    float* d_pcr32 = nullptr;     // their FP32 hi/lo splits
 };
 
 bfvm_status batch_build(BatchImpl* b);
+bfvm_status batch_set_shape(BatchImpl* b, int axis, int algo, int warps);
 bfvm_status batch_launch_step(BatchImpl* b, int p, bool renorm);
 void batch_free(BatchImpl* b);
 

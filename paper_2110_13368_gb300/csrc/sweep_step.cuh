@@ -23,14 +23,16 @@
 // order above leaves the tasks of the other substrates between a task and
 // its dependencies, so the wait is normally over before it starts.
 //
-// Scheduling: each pair's F warp claims the next task from a counter
-// (atomicAdd), so tasks are claimed in order by pairs that are running; a
-// claimed task only waits on tasks with smaller numbers.  A pair never
-// blocks while it holds a task that another task needs: when F claims a task
-// whose input is not complete yet, B back-substitutes its current task on
-// its own (no pair barriers), signals its completion, and only then does F
-// wait.  So the smallest unfinished task always progresses, and every wait
-// ends.  Waits are still bounded (kMaxPolls polls): on expiry the kernel sets
+// Scheduling: each pair's F warp claims tasks from a counter (atomicAdd),
+// one task ahead of the one it eliminates, so tasks are claimed in order by
+// pairs that are running, and a claimed task only waits on tasks with
+// smaller numbers.  A pair never blocks while it holds a started task that
+// another task needs: when the task F is to start next has incomplete input,
+// B back-substitutes its current task on its own (no pair barriers), signals
+// its completion, and only then does F wait.  The smallest unfinished task
+// is therefore never stuck (if it is started, its pair runs; if it is only
+// claimed, its pair's F is waiting on smaller, finished tasks), and every
+// wait ends.  Waits are still bounded (kMaxPolls polls): on expiry the kernel sets
 // the error flag (reported as BFVM_ETIMEOUT by the next synchronising call)
 // and carries on.
 //
@@ -132,10 +134,18 @@ __device__ __forceinline__ void task_wait(const StepSched& Q, const int* tf, Tas
     fence_acq_rel_gpu();
 }
 
-// B warp: all of task r's outputs are stored; publish its completion
+__device__ __forceinline__ unsigned ld_relaxed_u32(const unsigned* p)
+{
+    unsigned v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
+}
+
+// B warp: all of task r's outputs are stored; publish its completion (each
+// lane's release fence orders its stores before lane 0's count)
 __device__ __forceinline__ void task_done(const StepSched& Q, TaskRef r, int lane)
 {
-    __threadfence();
+    fence_acq_rel_gpu();
     __syncwarp();
     if (lane == 0) atomicAdd(Q.done + r.a * Q.n_sub + r.s, 1u);
 }
@@ -268,18 +278,34 @@ __device__ __forceinline__ int axis_groups(const SweepArgs<double>* sA, int a)
     return (sA[a].n + G - 1) / G;
 }
 
+// Pair-barrier meetings of a phase in which F eliminates a task of axis
+// a_f while B back-substitutes one of axis a_b: B meets once per group of
+// its task; F copies group j after meeting j and eliminates it LG meetings
+// later.
+__device__ __forceinline__ int phase_iters(const SweepArgs<double>* sA, int a_f, int a_b)
+{
+    constexpr int LG = Groups<double>::LAG_GROUPS;
+    return max(axis_groups(sA, a_f) + LG, axis_groups(sA, a_b));
+}
+
 // State of a pair's F warp between tasks
 struct FState {
     int t;        // task whose forward elimination is due (n_tasks: none)
-    int k;        // its index among this pair's tasks (slot parity k & 1)
+    int tn;       // the task claimed after it (n_tasks: none)
+    int k;        // index of t among this pair's tasks (slot parity k & 1)
     bool solo;    // on its own (first task, or B finished its task alone)
     int iters;    // pair-barrier meetings when not solo
 };
 
 // F warp: the forward eliminations of consecutive tasks on axis AXIS, each
-// followed by the claim of the next task and the hand-over to B.  Tasks are
-// claimed in increasing order, so a warp's axis never goes back and the
-// three axes run as three loops with their own specialised code.
+// followed by the hand-over to B.  Tasks are claimed in increasing order, so
+// a warp's axis never goes back and the three axes run as three loops with
+// their own specialised code.  F works one task ahead in its claims: while
+// it eliminates task t it already holds the next task tn, and at the start
+// it issues the claim of the task after tn and a relaxed read of tn's
+// dependency count, so neither round trip is on the pair's path at the
+// hand-over (an acquire fence there completes the acquire pattern; only when
+// the early read was short does F read the count again).
 template <int AXIS, int MODE>
 __device__ __forceinline__ void f_axis(FState& f, const SweepArgs<double>& A, const LineSet& S,
                                        const int64_t* fs, const SweepArgs<double>* sA,
@@ -290,36 +316,54 @@ __device__ __forceinline__ void f_axis(FState& f, const SweepArgs<double>& A, co
     while (f.t < T) {
         const TaskRef r = decode_task(tf, Q.n_sub, f.t);
         if (r.a != AXIS) return;
+        const bool has_next = f.tn < T;
+        TaskRef rn{0, 0, 0};
+        unsigned need = 0, seen = 0, raw2 = 0;
+        if (has_next) {
+            rn = decode_task(tf, Q.n_sub, f.tn);
+            if (rn.a > 0) {
+                const int i = (rn.a - 1) * Q.n_sub + rn.s;
+                need = (unsigned)(tf[i + 1] - tf[i]) + Q.extra_need;
+                if (P.lane == 0) seen = ld_relaxed_u32(Q.done + i);
+            }
+            if (P.lane == 0) raw2 = atomicAdd(Q.claim, 1u);
+        }
         const double prev = f_task<AXIS, MODE>(A, S, fs, P.field, P.cfa, P.cfb, P.W, P.ns, P.lane,
                                                 P.bar_id, r, P.rbF, f.k & 1, f.solo, f.iters);
-        const int t_next = claim_task(Q, P.lane);
         bool paired = false;
-        TaskRef rn{0, 0, 0};
-        if (t_next < T) {
-            rn = decode_task(tf, Q.n_sub, t_next);
-            paired = task_ready(Q, tf, rn, P.lane);
+        if (has_next) {
+            const int early = __shfl_sync(0xffffffffu, (int)(seen >= need), 0);
+            if (rn.a == 0) paired = true;
+            else if (early) {
+                fence_acq_rel_gpu();
+                paired = true;
+            } else {
+                paired = task_ready(Q, tf, rn, P.lane);
+            }
         }
         P.handover[P.lane] = prev;
         if (P.lane == 0) {
             P.ho[0] = f.t;
-            P.ho[1] = t_next;
+            P.ho[1] = f.tn;
             P.ho[2] = paired ? 1 : 0;
         }
         pair_sync(P.bar_id);                            // hand-over of task f.t
-        if (t_next >= T) {
+        if (!has_next) {
             f.t = T;
             return;
         }
         if (paired) {
             f.solo = false;
-            f.iters = max(axis_groups(sA, AXIS), axis_groups(sA, rn.a)) + LG;
+            f.iters = phase_iters(sA, rn.a, AXIS);
         } else {
             task_wait(Q, tf, rn, P.lane);
             pair_sync(P.bar_id);                        // B has finished f.t on its own
             f.solo = true;
             f.iters = 0;
         }
-        f.t = t_next;
+        const unsigned t2 = __shfl_sync(0xffffffffu, raw2, 0);
+        f.t = f.tn;
+        f.tn = t2 < (unsigned)T ? (int)t2 : T;
         ++f.k;
     }
 }
@@ -348,7 +392,7 @@ __device__ __forceinline__ void b_axis(BState& b, const SweepArgs<double>& A, co
         int iters = 0;
         if (paired) {
             const TaskRef rn = decode_task(tf, Q.n_sub, b.t_next);
-            iters = max(axis_groups(sA, AXIS), axis_groups(sA, rn.a)) + LG;
+            iters = phase_iters(sA, rn.a, AXIS);
         }
         b_task<AXIS, MODE>(A, S, fs, P.field, P.cfa, P.cfb, P.W, P.ns, P.lane, P.bar_id, r, P.rbB,
                            b.k & 1, b.x, paired, iters);
@@ -454,6 +498,7 @@ __global__ void __launch_bounds__(256, 1)
     if (!is_b) {
         FState f;
         f.t = claim_task(Q, lane);
+        f.tn = f.t < T ? claim_task(Q, lane) : T;
         f.k = 0;
         f.solo = true;
         f.iters = 0;

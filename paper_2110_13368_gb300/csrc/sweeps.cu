@@ -767,6 +767,13 @@ struct BatchDesc {
     int nx, ny;
     int64_t L;
     const double* sc;        // scale tables (state 0)
+    // parallel cyclic reduction of the x lines (when the batch has it):
+    // per substrate (2 S + 1) x nx coefficients, stage st rows 2 st and
+    // 2 st + 1 = minus the multipliers of the neighbours at -h and +h
+    // (h = 2^st), row 2 S = the reciprocal of the final diagonal
+    const double* pcr;       // FP64 [n_sub][2S+1][nx]
+    const float* pcr32;      // FP32 [n_sub][hi, lo][2S+1][nx]
+    int pcr_S;
 };
 
 template <typename T, int AXIS, int MODE>
@@ -823,6 +830,191 @@ __global__ void k_batch_sources(const BatchDesc<T>* __restrict__ D,
     *f = (T)fma(d.alpha[i], (double)*f, b);
 }
 
+// ---- parallel cyclic reduction of short x lines (batched form) ------------
+// The line matrix is the same for every line of a (member, substrate), so
+// the reduction's multipliers are computed once (k_pcr_coefs) and a line's
+// solve is, per stage st (h = 2^st), d_k <- d_k - k1_k d_{k-h} - k2_k d_{k+h}
+// (two FMAs per element), and x_k = d_k / b_k after the last stage.
+struct PcrSys {
+    double c, ell;   // off-diagonal magnitude and lambda dt / 3
+    int n, S;        // line length and stage count (2^S >= n)
+    int64_t off;     // first double of this system in the FP64 table
+};
+
+// One CTA per system, one thread per position (n <= 128): stage by stage
+// reduction of the tridiagonal matrix (diagonal 1 + ell + c at the ends,
+// 1 + ell + 2c inside, off-diagonals -c) in FP64.
+__global__ void k_pcr_coefs(const PcrSys* __restrict__ sys, double* __restrict__ tab,
+                            float* __restrict__ tab32)
+{
+    __shared__ double a[128], b[128], cc[128];
+    const PcrSys q = sys[blockIdx.x];
+    const int n = q.n, k = threadIdx.x;
+    if (k < n) {
+        const int nb = (k > 0) + (k < n - 1);
+        a[k] = k > 0 ? -q.c : 0.0;
+        cc[k] = k < n - 1 ? -q.c : 0.0;
+        b[k] = 1.0 + q.ell + q.c * (double)nb;
+    }
+    __syncthreads();
+    double* T = tab + q.off;
+    for (int st = 0; st < q.S; ++st) {
+        const int h = 1 << st;
+        double na = 0.0, nc = 0.0, nbv = 0.0;
+        if (k < n) {
+            double k1 = 0.0, k2 = 0.0;
+            if (k - h >= 0) k1 = a[k] / b[k - h];
+            if (k + h < n) k2 = cc[k] / b[k + h];
+            na = (k - h >= 0) ? -a[k - h] * k1 : 0.0;
+            nc = (k + h < n) ? -cc[k + h] * k2 : 0.0;
+            nbv = b[k] - ((k - h >= 0) ? cc[k - h] * k1 : 0.0) - ((k + h < n) ? a[k + h] * k2 : 0.0);
+            T[(2 * st) * n + k] = -k1;
+            T[(2 * st + 1) * n + k] = -k2;
+        }
+        __syncthreads();
+        if (k < n) {
+            a[k] = na;
+            cc[k] = nc;
+            b[k] = nbv;
+        }
+        __syncthreads();
+    }
+    if (k < n) T[2 * q.S * n + k] = 1.0 / b[k];
+    __syncthreads();
+    const int rows = 2 * q.S + 1;
+    float* H = tab32 + 2 * q.off;
+    for (int j = k; j < rows * n; j += blockDim.x) {
+        const double v = T[j];
+        const float hi = (float)v;
+        H[j] = hi;
+        H[rows * n + j] = (float)(v - (double)hi);
+    }
+}
+
+template <typename T, int E, int MODE>
+__device__ __forceinline__ void pcr_stage(T (&dv)[E], const double* tb, const float* tb32,
+                                          int rows_n, int n, int lane, int st)
+{
+    const int h = 1 << st;
+    T nd[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        T dm, dp;
+        if (h < 32) {
+            const int sm = (lane - h) & 31, sp = (lane + h) & 31;
+            const T a0 = __shfl_sync(0xffffffffu, dv[e], sm);
+            const T a1 = e > 0 ? __shfl_sync(0xffffffffu, dv[e > 0 ? e - 1 : 0], sm) : (T)0;
+            dm = lane >= h ? a0 : a1;
+            const T b0 = __shfl_sync(0xffffffffu, dv[e], sp);
+            const T b1 = e + 1 < E ? __shfl_sync(0xffffffffu, dv[e + 1 < E ? e + 1 : e], sp) : (T)0;
+            dp = lane + h < 32 ? b0 : b1;
+        } else {
+            const int qh = h >> 5;
+            dm = e >= qh ? dv[e >= qh ? e - qh : 0] : (T)0;
+            dp = e + qh < E ? dv[e + qh < E ? e + qh : 0] : (T)0;
+        }
+        const int k = e * 32 + lane;
+        nd[e] = dv[e];
+        if (k < n) {
+            const int j1 = (2 * st) * n + k, j2 = (2 * st + 1) * n + k;
+            if (sizeof(T) == 8) {
+                nd[e] = (T)fma(tb[j1], (double)dm, fma(tb[j2], (double)dp, (double)dv[e]));
+            } else {
+                const float t = comp_axpy(tb32[j2], tb32[rows_n + j2], (float)dp, (float)dv[e]);
+                nd[e] = (T)comp_axpy(tb32[j1], tb32[rows_n + j1], (float)dm, t);
+            }
+        }
+    }
+#pragma unroll
+    for (int e = 0; e < E; ++e) dv[e] = nd[e];
+}
+
+// x sweep of a batch by parallel cyclic reduction: one warp per 32-line
+// block task, its lines one after another, each line held as E elements
+// per lane (element k in lane k mod 32, slot k / 32), so loads and stores
+// are contiguous rows.  MODE 0 plain values; MODE 1 the rescaled FP64 form:
+// the input is divided by this axis' scale of state p (a factor constant
+// along the line passes through the solve), the output multiplied by that
+// of state p + 1.  Dirichlet handling as in sweep_one_line (DIR 0).
+template <typename T, int E, int MODE>
+__global__ void __launch_bounds__(256) k_batch_pcr_x(const BatchDesc<T>* __restrict__ D,
+                                                     const int2* __restrict__ tasks,
+                                                     int64_t n_tasks, int p)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t task = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (task >= n_tasks) return;
+    const int2 t = tasks[task];
+    const BatchDesc<T>& d = D[t.x];
+    const SweepArgs<T>& A = d.ax[0];
+    const int n = A.n, S = d.pcr_S, ny = A.ny, nz = A.nz;
+    const int rows_n = (2 * S + 1) * n;
+    const int64_t off_p = (int64_t)p * d.per_state;
+    for (int li = 0; li < 32; ++li) {
+        const int64_t line = (int64_t)t.y * 32 + li;
+        if (line >= A.n_lines) break;
+        const int oy = (int)(line % ny);
+        const int64_t tt = line / ny;
+        const int oz = (int)(tt % nz);
+        const int s = (int)(tt / nz);
+        T* f = A.field + (((int64_t)s * nz + oz) * ny + oy) * A.pitch;
+        const bool dir = A.bc_kind[s] == BFVM_BC_DIRICHLET;
+        const double v = A.bc_value[s];
+        const bool shell = dir && (oy == 0 || oy == ny - 1 || oz == 0 || oz == nz - 1);
+        const int64_t row = (int64_t)s * A.L;
+        double kline = v;
+        const double* scp1 = nullptr;
+        const double* iscp = nullptr;
+        if (MODE == 1) {
+            const double* scp = A.sc_p + off_p + row;
+            scp1 = A.sc_p1 + off_p + row;
+            iscp = A.isc_p1 + off_p - d.per_state + row;   // inverse scales of state p
+            kline = v * scp[A.off_y + oy] * scp[A.off_z + oz];
+        }
+        if (shell) {
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                const int k = e * 32 + lane;
+                if (k < n) f[k] = MODE == 1 ? (T)(kline * scp1[k]) : (T)v;
+            }
+            continue;
+        }
+        T dv[E];
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const int k = e * 32 + lane;
+            T x = (T)0;
+            if (k < n) {
+                x = f[k];
+                if (MODE == 1) x = (T)((double)x * iscp[k]);
+                if (dir && (k == 0 || k == n - 1)) x = (T)kline;
+            }
+            dv[e] = x;
+        }
+        const double* tb = d.pcr ? d.pcr + (int64_t)s * rows_n : nullptr;
+        const float* tb32 = d.pcr32 ? d.pcr32 + (int64_t)s * 2 * rows_n : nullptr;
+#pragma unroll
+        for (int st = 0; st < 7; ++st)
+            if (st < S) pcr_stage<T, E, MODE>(dv, tb, tb32, rows_n, n, lane, st);
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const int k = e * 32 + lane;
+            if (k < n) {
+                const int j = 2 * S * n + k;
+                T x;
+                if (sizeof(T) == 8) x = (T)((double)dv[e] * tb[j]);
+                else x = (T)__fmaf_rn((float)dv[e], tb32[j], __fmul_rn((float)dv[e], tb32[rows_n + j]));
+                if (dir && (k == 0 || k == n - 1)) x = MODE == 1 ? (T)(kline * scp1[k]) : (T)v;
+                else if (MODE == 1) x = (T)((double)x * scp1[k]);
+                f[k] = x;
+            }
+        }
+    }
+}
+
+template <typename T>
+bfvm_status batch_tune_t(BatchImpl* b, const std::vector<BatchDesc<T>>& desc);
+
 template <typename T>
 bfvm_status batch_build_t(BatchImpl* b)
 {
@@ -869,6 +1061,47 @@ bfvm_status batch_build_t(BatchImpl* b)
     b->max_n = max_n;
     b->n_entries = prefix[M];
     cudaError_t e;
+    // PCR stage tables of the x lines (offered when no x line is longer than
+    // 128 voxels, so that a warp holds a line in at most 4 elements per lane)
+    int max_nx = 0;
+    for (int m = 0; m < M; ++m) max_nx = std::max(max_nx, b->members[m]->nx);
+    b->pcr_ok = M > 0 && max_nx <= 128;
+    if (b->pcr_ok) {
+        b->pcr_e = (max_nx + 31) / 32;
+        std::vector<PcrSys> sys;
+        std::vector<int64_t> first(M);
+        int64_t total = 0;
+        for (int m = 0; m < M; ++m) {
+            Ctx* c = b->members[m];
+            int S = 0;
+            while ((1 << S) < c->nx) ++S;
+            desc[m].pcr_S = S;
+            first[m] = total;
+            for (int sb = 0; sb < c->n_sub; ++sb) {
+                PcrSys q;
+                q.c = c->D[sb] * c->dt / (c->dx * c->dx);
+                q.ell = c->lambda[sb] * c->dt / 3.0;
+                q.n = c->nx;
+                q.S = S;
+                q.off = total;
+                sys.push_back(q);
+                total += (int64_t)(2 * S + 1) * c->nx;
+            }
+        }
+        PcrSys* d_sys = nullptr;
+        if ((e = cudaMalloc(&b->d_pcr, sizeof(double) * total)) != cudaSuccess) return BFVM_ENOMEM;
+        if ((e = cudaMalloc(&b->d_pcr32, sizeof(float) * 2 * total)) != cudaSuccess) return BFVM_ENOMEM;
+        if ((e = cudaMalloc(&d_sys, sizeof(PcrSys) * sys.size())) != cudaSuccess) return BFVM_ENOMEM;
+        cudaMemcpy(d_sys, sys.data(), sizeof(PcrSys) * sys.size(), cudaMemcpyHostToDevice);
+        k_pcr_coefs<<<(unsigned)sys.size(), 128, 0, b->stream>>>(d_sys, b->d_pcr, b->d_pcr32);
+        e = cudaStreamSynchronize(b->stream);
+        cudaFree(d_sys);
+        if (e != cudaSuccess) return BFVM_ECUDA;
+        for (int m = 0; m < M; ++m) {
+            desc[m].pcr = b->d_pcr + first[m];
+            desc[m].pcr32 = b->d_pcr32 + 2 * first[m];
+        }
+    }
     if ((e = cudaMalloc(&b->d_desc, sizeof(BatchDesc<T>) * M)) != cudaSuccess) return BFVM_ENOMEM;
     cudaMemcpy(b->d_desc, desc.data(), sizeof(BatchDesc<T>) * M, cudaMemcpyHostToDevice);
     for (int a = 0; a < 3; ++a) {
@@ -883,28 +1116,154 @@ bfvm_status batch_build_t(BatchImpl* b)
     if ((e = cudaMemcpy(b->d_entry_prefix, prefix.data(), sizeof(int64_t) * (M + 1),
                         cudaMemcpyHostToDevice)) != cudaSuccess)
         return BFVM_ECUDA;
-    return BFVM_OK;
+    return batch_tune_t<T>(b, desc);
+}
+
+// Largest Thomas CTA (warps of one 32-line block each) whose line buffers
+// fit in shared memory.
+template <typename T>
+int batch_thomas_max_warps(const BatchImpl* b)
+{
+    const size_t per_warp = (size_t)32 * b->max_n * sizeof(T);
+    int w = (int)(b->members[0]->smem_optin / per_warp);
+    return w > 8 ? 8 : w;
+}
+
+// One launch of an axis' sweep over all members with line-block shape
+// (algo, warps) on the descriptors `desc` (the batch's own, or the tuner's
+// copies that point at scratch fields).
+template <typename T, int AXIS, int MODE>
+bfvm_status batch_axis_run(BatchImpl* b, const void* desc, int p, int algo, int warps)
+{
+    if (b->n_tasks[AXIS] == 0) return BFVM_OK;
+    const auto* D = reinterpret_cast<const BatchDesc<T>*>(desc);
+    const unsigned grid = (unsigned)ceil_div(b->n_tasks[AXIS], warps);
+    if (algo == 1) {
+        if constexpr (AXIS == 0 && MODE <= 1) {
+            if (!b->pcr_ok) return BFVM_EINVAL;
+            const int2* tk = b->d_tasks[AXIS];
+            const int64_t nt = b->n_tasks[AXIS];
+            switch (b->pcr_e) {
+                case 1: k_batch_pcr_x<T, 1, MODE><<<grid, 32 * warps, 0, b->stream>>>(D, tk, nt, p); break;
+                case 2: k_batch_pcr_x<T, 2, MODE><<<grid, 32 * warps, 0, b->stream>>>(D, tk, nt, p); break;
+                case 3: k_batch_pcr_x<T, 3, MODE><<<grid, 32 * warps, 0, b->stream>>>(D, tk, nt, p); break;
+                default: k_batch_pcr_x<T, 4, MODE><<<grid, 32 * warps, 0, b->stream>>>(D, tk, nt, p); break;
+            }
+        } else {
+            return BFVM_EINVAL;
+        }
+    } else {
+        if (warps > batch_thomas_max_warps<T>(b)) return BFVM_EINVAL;
+        const size_t smem = (size_t)32 * b->max_n * sizeof(T) * warps;
+        auto kern = k_batch_sweep<T, AXIS, MODE>;
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess)
+            return BFVM_ECUDA;
+        kern<<<grid, 32 * warps, smem, b->stream>>>(D, b->d_tasks[AXIS], b->n_tasks[AXIS], p,
+                                                     b->max_n);
+    }
+    return cudaGetLastError() == cudaSuccess ? BFVM_OK : BFVM_ECUDA;
 }
 
 template <typename T, int AXIS, int MODE>
 bfvm_status batch_axis(BatchImpl* b, int p)
 {
     if (b->n_tasks[AXIS] == 0) return BFVM_OK;
-    Ctx* c0 = b->members[0];
-    size_t per_warp = (size_t)32 * b->max_n * sizeof(T);
-    int warps = (int)(c0->smem_optin / per_warp);
-    if (warps > 8) warps = 8;
-    if (warps < 1) return BFVM_EINVAL;
-    size_t smem = per_warp * warps;
-    auto kern = k_batch_sweep<T, AXIS, MODE>;
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-        cudaSuccess)
-        return BFVM_ECUDA;
-    unsigned grid = (unsigned)ceil_div(b->n_tasks[AXIS], warps);
-    kern<<<grid, 32 * warps, smem, b->stream>>>(
-        reinterpret_cast<const BatchDesc<T>*>(b->d_desc), b->d_tasks[AXIS], b->n_tasks[AXIS], p,
-        b->max_n);
-    b->launches += 1;
+    bfvm_status st = batch_axis_run<T, AXIS, MODE>(b, b->d_desc, p, b->algo[AXIS], b->warps[AXIS]);
+    if (st == BFVM_OK) b->launches += 1;
+    return st;
+}
+
+// Autotuner of the line-block shapes: every candidate (Thomas with 2, 4 or
+// 8 warps per CTA as far as shared memory allows; for x lines of at most
+// 128 voxels also PCR with 4 or 8 warps per CTA) is launched once to warm
+// up and then three times under CUDA events, on copies of the members'
+// fields, in rescale state 0; the fastest shape of each axis is kept.  The
+// members' own fields are not touched.  If the scratch copies cannot be
+// allocated the defaults (Thomas, largest CTA) stay.
+template <typename T>
+bfvm_status batch_tune_t(BatchImpl* b, const std::vector<BatchDesc<T>>& desc)
+{
+    const int M = (int)b->members.size();
+    const int wmax = batch_thomas_max_warps<T>(b);
+    if (wmax < 1) return BFVM_EINVAL;
+    for (int a = 0; a < 3; ++a) {
+        b->algo[a] = 0;
+        b->warps[a] = wmax;
+        b->tune_ms[a][0] = b->tune_ms[a][1] = -1.0;
+    }
+    std::vector<int64_t> off(M + 1, 0);
+    for (int m = 0; m < M; ++m) off[m + 1] = off[m] + b->members[m]->n_field * (int64_t)sizeof(T);
+    unsigned char* scratch = nullptr;
+    void* d_tune = nullptr;
+    if (cudaMalloc(&scratch, off[M]) != cudaSuccess) {
+        cudaGetLastError();
+        return BFVM_OK;
+    }
+    if (cudaMalloc(&d_tune, sizeof(BatchDesc<T>) * M) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(scratch);
+        return BFVM_OK;
+    }
+    std::vector<BatchDesc<T>> dt = desc;
+    for (int m = 0; m < M; ++m) {
+        T* fs = reinterpret_cast<T*>(scratch + off[m]);
+        cudaMemcpyAsync(fs, b->members[m]->field, off[m + 1] - off[m], cudaMemcpyDeviceToDevice,
+                        b->stream);
+        for (int a = 0; a < 3; ++a) {
+            dt[m].ax[a].in = fs;
+            dt[m].ax[a].field = fs;
+        }
+        dt[m].field = fs;
+    }
+    cudaMemcpyAsync(d_tune, dt.data(), sizeof(BatchDesc<T>) * M, cudaMemcpyHostToDevice, b->stream);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    auto run = [&](int axis, int algo, int warps) -> bfvm_status {
+        if (b->rescaled) {
+            if constexpr (sizeof(T) == 8) {
+                if (axis == 0) return batch_axis_run<T, 0, 1>(b, d_tune, 0, algo, warps);
+                if (axis == 1) return batch_axis_run<T, 1, 1>(b, d_tune, 0, algo, warps);
+                return batch_axis_run<T, 2, 1>(b, d_tune, 0, algo, warps);
+            }
+            return BFVM_EINVAL;
+        }
+        if (axis == 0) return batch_axis_run<T, 0, 0>(b, d_tune, 0, algo, warps);
+        if (axis == 1) return batch_axis_run<T, 1, 0>(b, d_tune, 0, algo, warps);
+        return batch_axis_run<T, 2, 0>(b, d_tune, 0, algo, warps);
+    };
+    for (int axis = 0; axis < 3; ++axis) {
+        if (b->n_tasks[axis] == 0) continue;
+        double best = 1e30;
+        const int cand[5][2] = {{0, 2}, {0, 4}, {0, 8}, {1, 4}, {1, 8}};
+        for (const auto& cw : cand) {
+            const int algo = cw[0], warps = cw[1];
+            if (algo == 0 && warps > wmax) continue;
+            if (algo == 1 && (axis != 0 || !b->pcr_ok)) continue;
+            if (run(axis, algo, warps) != BFVM_OK) continue;
+            cudaEventRecord(e0, b->stream);
+            bool ok = true;
+            for (int r = 0; r < 3 && ok; ++r) ok = run(axis, algo, warps) == BFVM_OK;
+            cudaEventRecord(e1, b->stream);
+            if (!ok || cudaEventSynchronize(e1) != cudaSuccess) continue;
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            const double t = ms / 3.0;
+            double& slot = b->tune_ms[axis][algo];
+            if (slot < 0 || t < slot) slot = t;
+            if (t < best) {
+                best = t;
+                b->algo[axis] = algo;
+                b->warps[axis] = warps;
+            }
+        }
+    }
+    cudaStreamSynchronize(b->stream);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(d_tune);
+    cudaFree(scratch);
     return cudaGetLastError() == cudaSuccess ? BFVM_OK : BFVM_ECUDA;
 }
 
@@ -947,8 +1306,27 @@ bfvm_status batch_launch_step(BatchImpl* b, int p, bool renorm)
     return batch_step_t<double, 1>(b, p);
 }
 
+bfvm_status batch_set_shape(BatchImpl* b, int axis, int algo, int warps)
+{
+    if (axis < 0 || axis > 2 || algo < 0 || algo > 1 || warps < 1 || warps > 8) return BFVM_EINVAL;
+    if (algo == 1 && (axis != 0 || !b->pcr_ok)) return BFVM_EINVAL;
+    const int wmax = b->precision == 64 ? batch_thomas_max_warps<double>(b)
+                                        : batch_thomas_max_warps<float>(b);
+    if (algo == 0 && warps > wmax) return BFVM_EINVAL;
+    b->algo[axis] = algo;
+    b->warps[axis] = warps;
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+    b->graph_len = 0;
+    return BFVM_OK;
+}
+
 void batch_free(BatchImpl* b)
 {
+    if (b->d_pcr) cudaFree(b->d_pcr);
+    if (b->d_pcr32) cudaFree(b->d_pcr32);
+    b->d_pcr = nullptr;
+    b->d_pcr32 = nullptr;
     if (b->d_desc) cudaFree(b->d_desc);
     for (int a = 0; a < 3; ++a)
         if (b->d_tasks[a]) cudaFree(b->d_tasks[a]);

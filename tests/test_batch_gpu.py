@@ -95,3 +95,79 @@ def test_batch_rejects_mixed_precision(bf):
         bf.Batch([a, b])
     a.close()
     b.close()
+
+
+def pcr_batch(steps=5):
+    """Members whose x lines span every PCR register layout (1 to 4 elements
+    per lane, lines of 1 and 2 voxels, 128 voxels), Dirichlet and zero-flux
+    substrates side by side."""
+    edges = [(1, 3, 4), (2, 5, 3), (7, 6, 5), (33, 4, 3), (64, 3, 5), (100, 4, 4), (128, 3, 3)]
+    probs = []
+    for i, (nx, ny, nz) in enumerate(edges):
+        probs.append(inputs.make_problem(nx, ny, nz, n_sub=2, D=[2e4 * (i + 1), 3e2],
+                                         lam=[0.1, 0.01 * (i + 1)], bc_kind=[i % 2, 0],
+                                         bc_value=[38.0, 0.0], n_cells=10 + 5 * i,
+                                         U=[10.0, 1.0], S=[0.5, 5.0], rho_star=[1.0, 2.0],
+                                         steps=steps, seed=20 + i))
+    return probs
+
+
+@pytest.mark.parametrize("precision,variant,tol", [(64, 1, 1e-12), (64, 0, 1e-12), (32, None, 1e-5)])
+@pytest.mark.parametrize("x_algo,x_warps,yz_warps", [(1, 4, 2), (1, 8, 4), (0, 2, 4)])
+def test_batch_line_block_shapes_match_oracle(bf, precision, variant, tol, x_algo, x_warps,
+                                              yz_warps):
+    """Every line-block shape the autotuner may pick (PCR or Thomas for the
+    x lines, CTA sizes) gives each member's oracle result, in the rescaled
+    and plain FP64 forms and in FP32."""
+    probs = pcr_batch()
+    sims = [bf.Sim.from_problem(p, precision=precision) for p in probs]
+    if variant is not None:
+        for s in sims:
+            s.set_option(bf.OPT_VARIANT, variant)
+    batch = bf.Batch(sims)
+    batch.set_shape(0, x_algo, x_warps)
+    batch.set_shape(1, 0, yz_warps)
+    batch.set_shape(2, 0, yz_warps)
+    assert batch.shape(0)[:2] == (x_algo, x_warps)
+    batch.step(probs[0].steps)
+    batch.sync()
+    for p, s in zip(probs, sims):
+        got = s.get_density().double().cpu().numpy()
+        err = rel_inf(got, oracle.run(p))
+        assert np.all(err <= tol), (p.name, x_algo, err)
+    batch.close()
+    for s in sims:
+        s.close()
+
+
+def test_batch_autotuner_measures_and_leaves_fields(bf):
+    """The tuner times Thomas on every axis and PCR on the x lines, keeps a
+    valid shape, and runs its trials on copies: the members' fields are
+    unchanged by bfvm_batch_create.  Unsupported shapes are rejected."""
+    import torch
+    probs = pcr_batch()
+    sims = [bf.Sim.from_problem(p) for p in probs]
+    before = [s.get_density().clone() for s in sims]
+    batch = bf.Batch(sims)
+    for s, b0 in zip(sims, before):
+        assert torch.equal(s.get_density(), b0)
+    algo, warps, ms = batch.shape(0)
+    assert algo in (0, 1) and warps in (2, 4, 8)
+    assert ms[0] > 0 and ms[1] > 0
+    for axis in (1, 2):
+        algo, warps, ms = batch.shape(axis)
+        assert algo == 0 and ms[0] > 0 and ms[1] == -1
+    with pytest.raises(bf.BfvmError):
+        batch.set_shape(1, 1, 4)            # PCR only for x lines
+    with pytest.raises(bf.BfvmError):
+        batch.set_shape(0, 0, 9)
+    batch.close()
+    big = [bf.Sim.from_problem(inputs.make_problem(130, 3, 3, n_sub=1, D=[1e4], lam=[0.1],
+                                                   bc_kind=[0], bc_value=[0.0], steps=1))]
+    b2 = bf.Batch(big)
+    assert b2.shape(0)[2][1] == -1          # x lines over 128 voxels: no PCR candidate
+    with pytest.raises(bf.BfvmError):
+        b2.set_shape(0, 1, 4)
+    b2.close()
+    for s in sims + big:
+        s.close()
