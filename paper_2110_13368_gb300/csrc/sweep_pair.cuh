@@ -238,26 +238,39 @@ struct PairSweeper {
         return prev;
     }
 
+    struct NoRelease {
+        __device__ void operator()() const {}
+    };
+
     // B: back substitution of block L (parity Q); with `paired`, the group
     // loop meets F at the pair barrier `iters` times (default gcount + LG).
-    template <int Q>
+    // `rel` runs once after the last group's stores have been issued: in the
+    // first iteration that has no group left (F is still eliminating its
+    // last groups then), else after the loop.
+    template <int Q, typename Rel = NoRelease>
     __device__ __forceinline__ void b_block(const Line& L, const CoefRow<T>& C, T& x,
                                             const int64_t* rb, const int64_t (&rv)[G],
-                                            bool paired, int iters = -1) const
+                                            bool paired, int iters = -1,
+                                            const Rel& rel = Rel()) const
     {
         const int gcount = (n + G - 1) / G;
         const int h_top = gcount - 1;
         const int b_hi = (n - 1) / G;   // backward groups [0, b_hi) are interior
         if (!paired) iters = gcount;
         else if (iters < 0) iters = gcount + LG;
+        bool released = false;
         for (int jg = 0; jg < iters; ++jg) {
             const int h = h_top - jg;
             if (h >= 0) {
                 if (h < b_hi) bwd_fast<Q>(L, C, x, h, rv);
                 else bwd_group<Q>(L, C, x, h, rb);
+            } else if (!released) {
+                rel();
+                released = true;
             }
             if (paired) pair_bar();                      // group h released to F
         }
+        if (!released) rel();
     }
 
     // B: back substitution of group h (parity Q) and its output

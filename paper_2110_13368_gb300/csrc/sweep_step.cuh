@@ -165,6 +165,90 @@ __device__ __forceinline__ Line task_line(const SweepArgs<double>& A, const Line
     return L;
 }
 
+// A task's lines in two halves: issue_line() computes the integer part and
+// issues the few global reads a line needs (the Dirichlet value's scales of
+// the other axes and of this axis' two ends, the renormalising inverse
+// scales), finish_line() does the arithmetic on them.  F issues the reads
+// of its next task before it eliminates the current one and finishes them
+// after, so their latency overlaps the elimination.
+struct LinePre {
+    int64_t base;
+    int s;
+    bool valid, dir;
+    double v, sa, sb, se0, se1, ia, ib;
+};
+
+template <int AXIS, int MODE>
+__device__ __forceinline__ LinePre issue_line(const SweepArgs<double>& A, const LineSet& S,
+                                              const int64_t* fs, const int* bck,
+                                              const double* bcv, TaskRef r, int lane)
+{
+    LinePre P;
+    const int64_t hi = fs[r.s + 1];
+    int64_t t = (int64_t)r.j * 32 + lane;
+    P.valid = fs[r.s] + t < hi;
+    if (!P.valid) t = hi - 1 - fs[r.s];
+    const int s = r.s;
+    P.s = s;
+    const int ca = S.cnt_a[s];
+    const int a = S.lo_a[s] + (int)(t % ca);
+    const int b = S.lo_b[s] + (int)(t / ca);
+    int ox = 0, oy = 0, oz = 0;
+    if (AXIS == 0) {
+        oy = a; oz = b;
+        P.base = (((int64_t)s * A.nz + oz) * A.ny + oy) * A.pitch;
+    } else if (AXIS == 1) {
+        ox = a; oz = b;
+        P.base = (((int64_t)s * A.nz + oz) * A.ny) * A.pitch + ox;
+    } else {
+        ox = a; oy = b;
+        P.base = ((int64_t)s * A.nz * A.ny + oy) * A.pitch + ox;
+    }
+    P.dir = bck[s] == BFVM_BC_DIRICHLET;
+    P.v = bcv[s];
+    P.sa = P.sb = P.se0 = P.se1 = P.ia = P.ib = 1.0;
+    if (MODE >= 1 && P.dir) {
+        const int64_t row = (int64_t)s * A.L;
+        if (AXIS == 0) {
+            P.sa = A.sc_p[row + A.off_y + oy];
+            P.sb = A.sc_p[row + A.off_z + oz];
+        } else if (AXIS == 1) {
+            P.sa = A.sc_p1[row + A.off_x + ox];
+            P.sb = A.sc_p[row + A.off_z + oz];
+        } else {
+            P.sa = A.sc_p1[row + A.off_x + ox];
+            P.sb = A.sc_p1[row + A.off_y + oy];
+        }
+        P.se0 = A.sc_p[row + A.axis_off];
+        P.se1 = A.sc_p[row + A.axis_off + A.n - 1];
+    }
+    if (MODE == 2 && AXIS == 2) {
+        const int64_t row = (int64_t)s * A.L;
+        P.ia = A.isc_p1[row + A.off_x + ox];
+        P.ib = A.isc_p1[row + A.off_y + oy];
+    }
+    return P;
+}
+
+template <int MODE>
+__device__ __forceinline__ Line finish_line(const LinePre& P)
+{
+    Line L;
+    L.base = P.base;
+    L.s = P.s;
+    L.valid = P.valid;
+    L.dir = P.dir;
+    if (MODE >= 1) {
+        const double kline = P.v * P.sa * P.sb;
+        L.end0 = kline * P.se0;
+        L.end1 = kline * P.se1;
+    } else {
+        L.end0 = L.end1 = P.v;
+    }
+    L.inv_other = P.ia * P.ib;
+    return L;
+}
+
 // Coefficient rows of substrate s on this axis: the forward and backward
 // coefficients from the kernel's shared copies cfa / cfb ([s][L]; every lane
 // of a task has the same s, so each read is a broadcast), the output scales
@@ -195,16 +279,14 @@ __device__ __forceinline__ int64_t axis_stride(const SweepArgs<double>& A, int a
 // `iters` pair-barrier meetings.  Returns the chain value of the last
 // element (handed to B).
 template <int AXIS, int MODE>
-__device__ __forceinline__ double f_task(const SweepArgs<double>& A, const LineSet& S,
-                                         const int64_t* fs, double* field, const double* cfa,
-                                         const double* cfb, double* W, int ns, int lane,
-                                         int bar_id, TaskRef r, int64_t* rbF, int q, bool solo,
+__device__ __forceinline__ double f_task(const SweepArgs<double>& A, const Line& L, double* field,
+                                         const double* cfa, const double* cfb, double* W, int ns,
+                                         int lane, int bar_id, int64_t* rbF, int q, bool solo,
                                          int iters)
 {
     constexpr int G = Groups<double>::G;
     PairSweeper<double, AXIS, MODE> sw{A, W, field, field, axis_stride(A, AXIS), A.n, ns, lane,
                                        bar_id};
-    const Line L = task_line<AXIS, MODE>(A, S, fs, r, lane);
     const CoefRow<double> C = step_coef_row(A, cfa, cfb, L.s);
     __syncwarp();
     rbF[lane] = L.base;
@@ -231,26 +313,34 @@ __device__ __forceinline__ double f_task(const SweepArgs<double>& A, const LineS
 }
 
 // B: back substitution of task r (parity q) from chain value x, with or
-// without F next to it
-template <int AXIS, int MODE>
+// without F next to it.  The line bases (-1 for padding lanes) and the
+// substrate come from F through shared memory (rbB, hs): F built them when
+// it eliminated the task.  `rel` publishes the task's completion.
+template <int AXIS, int MODE, typename Rel>
 __device__ __forceinline__ void b_task(const SweepArgs<double>& A, const LineSet& S,
-                                       const int64_t* fs, double* field, const double* cfa,
+                                       const int64_t* fs, const int* bck, const double* bcv,
+                                       double* field, const double* cfa,
                                        const double* cfb, double* W, int ns, int lane,
-                                       int bar_id, TaskRef r, int64_t* rbB, int q, double x,
-                                       bool paired, int iters)
+                                       int bar_id, TaskRef r, const int64_t* rbB, const int* hs,
+                                       int q, double x, bool paired, int iters, const Rel& rel)
 {
     constexpr int G = Groups<double>::G;
     PairSweeper<double, AXIS, MODE> sw{A, W, field, field, axis_stride(A, AXIS), A.n, ns, lane,
                                        bar_id};
-    const Line L = task_line<AXIS, MODE>(A, S, fs, r, lane);
+    Line L;
+    const int64_t hb = rbB[lane];
+    L.valid = hb >= 0;
+    L.base = L.valid ? hb : 0;
+    L.s = hs[lane];
+    L.dir = false;
+    L.end0 = L.end1 = 0.0;
+    L.inv_other = 1.0;
+    if (MODE == 2) L.inv_other = finish_line<MODE>(issue_line<AXIS, MODE>(A, S, fs, bck, bcv, r, lane)).inv_other;
     const CoefRow<double> C = step_coef_row(A, cfa, cfb, L.s);
-    __syncwarp();
-    rbB[lane] = L.valid ? L.base : -1;
-    __syncwarp();
     int64_t rv[G];
     sw.load_rows(rbB, rv);
-    if (q) sw.template b_block<1>(L, C, x, rbB, rv, paired, iters);
-    else sw.template b_block<0>(L, C, x, rbB, rv, paired, iters);
+    if (q) sw.template b_block<1>(L, C, x, rbB, rv, paired, iters, rel);
+    else sw.template b_block<0>(L, C, x, rbB, rv, paired, iters, rel);
 }
 
 __device__ __forceinline__ void pair_sync(int bar_id)
@@ -260,11 +350,14 @@ __device__ __forceinline__ void pair_sync(int bar_id)
 
 // What a pair's two warps share besides the column buffer.
 struct PairShared {
+    const int* bck;        // shared copy of the substrates' boundary kinds
+    const double* bcv;     // and Dirichlet values
     double* field;         // the field (read and written in place)
     const double* cfa;     // shared forward coefficients [s][L]
     const double* cfb;     // shared backward coefficients [s][L]
     int64_t* rbF;          // [32] row bases of F's task (x tasks)
-    int64_t* rbB;          // [32] row bases of B's task
+    int64_t* rbB;          // [32] line bases of B's task (-1: padding), written by F
+    int* hs;               // [32] substrate of each lane's line in B's task, written by F
     double* handover;      // [32] chain values of the task handed to B
     volatile int* ho;      // task handed over, next task, paired (0/1)
     double* W;             // column buffer
@@ -295,7 +388,15 @@ struct FState {
     int k;        // index of t among this pair's tasks (slot parity k & 1)
     bool solo;    // on its own (first task, or B finished its task alone)
     int iters;    // pair-barrier meetings when not solo
+    bool have_line;   // `pre` holds the lines of task t (issued during the previous task)
+    LinePre pre;
+    unsigned long long acq;  // bit (a - 1) n_sub + s: this warp has acquired the completion of (a - 1, s)
 };
+
+__device__ __forceinline__ void mark_acquired(FState& f, int i)
+{
+    if (i < 64) f.acq |= 1ull << i;
+}
 
 // F warp: the forward eliminations of consecutive tasks on axis AXIS, each
 // followed by the hand-over to B.  Tasks are claimed in increasing order, so
@@ -311,37 +412,53 @@ __device__ __forceinline__ void f_axis(FState& f, const SweepArgs<double>& A, co
                                        const int64_t* fs, const SweepArgs<double>* sA,
                                        const StepSched& Q, const int* tf, const PairShared& P)
 {
-    constexpr int LG = Groups<double>::LAG_GROUPS;
     const int T = Q.n_tasks;
     while (f.t < T) {
         const TaskRef r = decode_task(tf, Q.n_sub, f.t);
         if (r.a != AXIS) return;
+        const Line L = finish_line<MODE>(
+            f.have_line ? f.pre : issue_line<AXIS, MODE>(A, S, fs, P.bck, P.bcv, r, P.lane));
+        f.have_line = false;
         const bool has_next = f.tn < T;
         TaskRef rn{0, 0, 0};
         unsigned need = 0, seen = 0, raw2 = 0;
+        int dep = -1;              // completion counter tn waits on (-1: none or acquired)
         if (has_next) {
             rn = decode_task(tf, Q.n_sub, f.tn);
             if (rn.a > 0) {
-                const int i = (rn.a - 1) * Q.n_sub + rn.s;
-                need = (unsigned)(tf[i + 1] - tf[i]) + Q.extra_need;
-                if (P.lane == 0) seen = ld_relaxed_u32(Q.done + i);
+                dep = (rn.a - 1) * Q.n_sub + rn.s;
+                if (dep < 64 && ((f.acq >> dep) & 1ull)) dep = -1;
+            }
+            if (dep >= 0) {
+                need = (unsigned)(tf[dep + 1] - tf[dep]) + Q.extra_need;
+                if (P.lane == 0) seen = ld_relaxed_u32(Q.done + dep);
             }
             if (P.lane == 0) raw2 = atomicAdd(Q.claim, 1u);
-        }
-        const double prev = f_task<AXIS, MODE>(A, S, fs, P.field, P.cfa, P.cfb, P.W, P.ns, P.lane,
-                                                P.bar_id, r, P.rbF, f.k & 1, f.solo, f.iters);
-        bool paired = false;
-        if (has_next) {
-            const int early = __shfl_sync(0xffffffffu, (int)(seen >= need), 0);
-            if (rn.a == 0) paired = true;
-            else if (early) {
-                fence_acq_rel_gpu();
-                paired = true;
-            } else {
-                paired = task_ready(Q, tf, rn, P.lane);
+            if (rn.a == AXIS) {
+                // the next task's lines: their global reads overlap this task
+                f.pre = issue_line<AXIS, MODE>(A, S, fs, P.bck, P.bcv, rn, P.lane);
+                f.have_line = true;
             }
         }
+        const double prev = f_task<AXIS, MODE>(A, L, P.field, P.cfa, P.cfb, P.W, P.ns, P.lane,
+                                                P.bar_id, P.rbF, f.k & 1, f.solo, f.iters);
+        bool paired = false;
+        if (has_next) {
+            if (dep < 0) {
+                paired = true;
+            } else if (__shfl_sync(0xffffffffu, (int)(seen >= need), 0)) {
+                fence_acq_rel_gpu();
+                mark_acquired(f, dep);
+                paired = true;
+            } else if (task_ready(Q, tf, rn, P.lane)) {
+                mark_acquired(f, dep);
+                paired = true;
+            }
+        }
+        // hand task f.t to B: chain values, line bases, substrates, next task
         P.handover[P.lane] = prev;
+        P.rbB[P.lane] = L.valid ? L.base : -1;
+        P.hs[P.lane] = L.s;
         if (P.lane == 0) {
             P.ho[0] = f.t;
             P.ho[1] = f.tn;
@@ -357,6 +474,7 @@ __device__ __forceinline__ void f_axis(FState& f, const SweepArgs<double>& A, co
             f.iters = phase_iters(sA, rn.a, AXIS);
         } else {
             task_wait(Q, tf, rn, P.lane);
+            mark_acquired(f, dep);
             pair_sync(P.bar_id);                        // B has finished f.t on its own
             f.solo = true;
             f.iters = 0;
@@ -394,9 +512,10 @@ __device__ __forceinline__ void b_axis(BState& b, const SweepArgs<double>& A, co
             const TaskRef rn = decode_task(tf, Q.n_sub, b.t_next);
             iters = phase_iters(sA, rn.a, AXIS);
         }
-        b_task<AXIS, MODE>(A, S, fs, P.field, P.cfa, P.cfb, P.W, P.ns, P.lane, P.bar_id, r, P.rbB,
-                           b.k & 1, b.x, paired, iters);
-        task_done(Q, r, P.lane);
+        const int lane = P.lane;
+        auto rel = [&]() { task_done(Q, r, lane); };
+        b_task<AXIS, MODE>(A, S, fs, P.bck, P.bcv, P.field, P.cfa, P.cfb, P.W, P.ns, P.lane,
+                           P.bar_id, r, P.rbB, P.hs, b.k & 1, b.x, paired, iters, rel);
         if (!more) {
             b.t = T;
             return;
@@ -414,6 +533,8 @@ __device__ __forceinline__ void b_axis(BState& b, const SweepArgs<double>& A, co
 // Dynamic shared memory: [copies of the 3 axes' SweepArgs and LineSets]
 // [task_first] [line-set prefixes of the 3 axes] [forward and backward
 // coefficients of state p, all substrates and axes: 2 x n_sub x L]
+// [boundary values and kinds: n_sub doubles, n_sub ints] [per pair: column buffer, 4 x 32 row/line bases, 32 chain values,
+// 4 hand-over words, 32 substrates]
 // [per pair: column buffer (n_slots x 32), 4 x 32 row bases, 32 chain
 // values, 4 hand-over words].  n_slots = G * max over axes of ceil(n/G), so
 // the slot schedule of PairSweeper holds for any two axes.
@@ -447,8 +568,11 @@ __global__ void __launch_bounds__(256, 1)
     const int64_t n_coef = (int64_t)n_sub * A0.L;
     double* cfa = reinterpret_cast<double*>(smem_raw + args_bytes + tf_bytes + fs_bytes);
     double* cfb = cfa + n_coef;
+    double* bcv = cfb + n_coef;                                   // [n_sub]
+    int* bck = reinterpret_cast<int*>(bcv + n_sub);               // [n_sub]
+    const size_t bc_bytes = (n_sub * (sizeof(double) + sizeof(int)) + 15) & ~(size_t)15;
     unsigned char* pair_area =
-        smem_raw + args_bytes + tf_bytes + fs_bytes + 2 * n_coef * sizeof(double);
+        smem_raw + args_bytes + tf_bytes + fs_bytes + 2 * n_coef * sizeof(double) + bc_bytes;
     if (threadIdx.x == 0) {
         sA[0] = A0;
         sA[1] = A1;
@@ -462,6 +586,10 @@ __global__ void __launch_bounds__(256, 1)
         cfa[i] = A0.fa[i];   // the three axes share one table per state
         cfb[i] = A0.fb[i];
     }
+    for (int i = threadIdx.x; i < n_sub; i += blockDim.x) {
+        bcv[i] = A0.bc_value[i];
+        bck[i] = A0.bc_kind[i];
+    }
     for (int i = threadIdx.x; i <= n_sub; i += blockDim.x) {
         fs[i] = S0.first[i];
         fs[(n_sub + 1) + i] = S1.first[i];
@@ -473,21 +601,25 @@ __global__ void __launch_bounds__(256, 1)
     const int64_t* fs2 = fs + 2 * (n_sub + 1);
 
     const size_t pair_bytes = (size_t)ns * 32 * sizeof(double) + 4 * 32 * sizeof(int64_t) +
-                              32 * sizeof(double) + 4 * sizeof(int);
+                              32 * sizeof(double) + 4 * sizeof(int) + 32 * sizeof(int);
     unsigned char* my = pair_area + (size_t)pair * pair_bytes;
     double* W = reinterpret_cast<double*>(my);
     int64_t* rbF = reinterpret_cast<int64_t*>(my + (size_t)ns * 32 * sizeof(double));
     int64_t* rbB = rbF + 64;
     double* handover = reinterpret_cast<double*>(rbF + 128);
     volatile int* ho = reinterpret_cast<volatile int*>(handover + 32);  // t_cur, t_next, paired
+    int* hs = const_cast<int*>(ho) + 4;                                  // [32] substrates
     const int bar_id = 1 + pair;
 
     PairShared P;
+    P.bck = bck;
+    P.bcv = bcv;
     P.field = A0.field;
     P.cfa = cfa;
     P.cfb = cfb;
     P.rbF = rbF;
     P.rbB = rbB;
+    P.hs = hs;
     P.handover = handover;
     P.ho = ho;
     P.W = W;
@@ -502,8 +634,12 @@ __global__ void __launch_bounds__(256, 1)
         f.k = 0;
         f.solo = true;
         f.iters = 0;
+        f.have_line = false;
+        f.acq = 0ull;
         if (f.t < T) {
-            task_wait(Q, tf, decode_task(tf, n_sub, f.t), lane);
+            const TaskRef r0 = decode_task(tf, n_sub, f.t);
+            task_wait(Q, tf, r0, lane);
+            if (r0.a > 0) mark_acquired(f, (r0.a - 1) * n_sub + r0.s);
         } else {
             if (lane == 0) {
                 ho[0] = T;

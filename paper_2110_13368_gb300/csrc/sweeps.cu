@@ -484,9 +484,10 @@ bfvm_status launch_step_fused(Ctx* c, int p, bool renorm)
         ((3 * sizeof(SweepArgs<double>) + 3 * sizeof(persistent::LineSet) + 15) & ~(size_t)15) +
         ((((size_t)3 * c->n_sub + 1) * sizeof(int) + 15) & ~(size_t)15) +
                          (((size_t)3 * (c->n_sub + 1) * sizeof(int64_t) + 15) & ~(size_t)15) +
-        2 * (size_t)c->n_sub * c->coef.L * sizeof(double);
+        2 * (size_t)c->n_sub * c->coef.L * sizeof(double) +
+        (((size_t)c->n_sub * (sizeof(double) + sizeof(int)) + 15) & ~(size_t)15);
     const size_t pair_bytes = (size_t)ns * 32 * sizeof(double) + 4 * 32 * sizeof(int64_t) +
-                              32 * sizeof(double) + 4 * sizeof(int);
+                              32 * sizeof(double) + 4 * sizeof(int) + 32 * sizeof(int);
     if (c->smem_optin < fixed + pair_bytes) return BFVM_ESTATE;
     int pairs = (int)((c->smem_optin - fixed) / pair_bytes);
     if (pairs > 4) pairs = 4;
