@@ -19,7 +19,8 @@
 //
 // Dependencies: a task of (a, s) with a > 0 reads lines that every task of
 // (a - 1, s) writes, so it starts only when done[a - 1][s] (tasks of
-// (a - 1, s) completed) reaches their count.  With several substrates the
+// (a - 1, s) completed) reaches their count (an axis without tasks is
+// skipped: the nearest earlier axis of s that has tasks counts).  With several substrates the
 // order above leaves the tasks of the other substrates between a task and
 // its dependencies, so the wait is normally over before it starts.
 //
@@ -41,9 +42,13 @@
 // acquire fence, so the copies that follow (cp.async through L1) see the
 // other SMs' writes and no L1 line left from an earlier task of this SM.
 //
-// The counters (claim, exit, done) are zero at every launch: the last CTA to
-// finish resets them, and the next launch is ordered after this one on the
-// stream.
+// Epilogue: every warp that runs out of sweep tasks takes chunks of the
+// Dirichlet shell fill and of the cell sources (step_epilogue), so both run
+// in the same launch, next to the last sweep tasks.
+//
+// The counters (claim, exit, done, epilogue) are zero at every launch: the
+// last CTA to finish resets them, and the next launch is ordered after this
+// one on the stream.
 #pragma once
 
 namespace bfvm {
@@ -59,7 +64,42 @@ struct StepSched {
     int n_tasks;
     unsigned max_polls;     // polls before a wait gives up (kMaxPolls)
     unsigned extra_need;    // 0; 1 only to test the give-up path (no wait can end)
+    // epilogue of the step (after every z task of a substrate): the
+    // Dirichlet shell, then the cell sources, in chunks of kEpiChunk
+    unsigned* eclaim;       // [1] next epilogue chunk
+    unsigned* shell_done;   // [n_sub] completed shell chunks of each substrate
+    int n_epi_chunks;       // over all substrates
 };
+
+// Everything the epilogue reads: grid, the scales of state p + 1 (null when
+// the step renormalises: plain values) and the composed cell maps.
+struct EpiArgs {
+    double* field;
+    int nx, ny, nz;
+    int64_t pitch, L;
+    const double* sc;       // [s][L] scales of state p + 1, or null
+    int64_t n_seg;          // occupied voxels; entry g * n_sub + s is voxel g, substrate s
+    const int64_t* off;     // field offset of each (voxel, substrate) entry
+    const double* alpha;
+    const double* beta;
+    const int32_t* vox;     // voxel x + nx (y + ny z)
+    const int32_t* sub;
+};
+
+constexpr int kEpiUnroll = 8;                  // independent elements per lane
+constexpr int kEpiChunk = 32 * kEpiUnroll * 2;  // elements per claimed chunk (2 rounds)
+
+// Epilogue chunks, substrate by substrate: the shell chunks of s (Dirichlet
+// substrates only), then its source chunks (kEpiChunk occupied voxels each).
+__host__ __device__ inline int64_t epi_shell_chunks(int nx, int ny, int nz)
+{
+    const int64_t per = 2 * ((int64_t)nx * ny + (int64_t)nx * nz + (int64_t)ny * nz);
+    return (per + kEpiChunk - 1) / kEpiChunk;
+}
+__host__ __device__ inline int64_t epi_src_chunks(int64_t n_seg)
+{
+    return (n_seg + kEpiChunk - 1) / kEpiChunk;
+}
 
 // about 2^21 polls with a 128 ns back-off: well over a second
 constexpr unsigned kMaxPolls = 1u << 21;
@@ -92,6 +132,19 @@ __device__ __forceinline__ TaskRef decode_task(const int* tf, int n_sub, int t)
     return r;
 }
 
+// Completion counter that a task of axis a (0..2; 3 = the epilogue) of
+// substrate s waits on: that of the nearest earlier axis of s that has
+// tasks (on a Dirichlet substrate an axis can have none, e.g. when another
+// extent is at most 2), or -1 when no earlier axis has any.
+__device__ __forceinline__ int dep_index(const int* tf, int n_sub, int a, int s)
+{
+    for (int b = a - 1; b >= 0; --b) {
+        const int i = b * n_sub + s;
+        if (tf[i + 1] > tf[i]) return i;
+    }
+    return -1;
+}
+
 // F warp: next task number (n_tasks when none is left)
 __device__ __forceinline__ int claim_task(const StepSched& Q, int lane)
 {
@@ -104,8 +157,8 @@ __device__ __forceinline__ int claim_task(const StepSched& Q, int lane)
 // F warp: is the input of task r complete?  (no waiting)
 __device__ __forceinline__ bool task_ready(const StepSched& Q, const int* tf, TaskRef r, int lane)
 {
-    if (r.a == 0) return true;
-    const int i = (r.a - 1) * Q.n_sub + r.s;
+    const int i = dep_index(tf, Q.n_sub, r.a, r.s);
+    if (i < 0) return true;
     const unsigned need = (unsigned)(tf[i + 1] - tf[i]) + Q.extra_need;
     int ok = 0;
     if (lane == 0) ok = ld_acquire_u32(Q.done + i) >= need;
@@ -117,8 +170,8 @@ __device__ __forceinline__ bool task_ready(const StepSched& Q, const int* tf, Ta
 // F warp: wait (bounded) until the input of task r is complete
 __device__ __forceinline__ void task_wait(const StepSched& Q, const int* tf, TaskRef r, int lane)
 {
-    if (r.a == 0) return;
-    const int i = (r.a - 1) * Q.n_sub + r.s;
+    const int i = dep_index(tf, Q.n_sub, r.a, r.s);
+    if (i < 0) return;
     const unsigned need = (unsigned)(tf[i + 1] - tf[i]) + Q.extra_need;
     if (lane == 0) {
         unsigned polls = 0;
@@ -343,6 +396,143 @@ __device__ __forceinline__ void b_task(const SweepArgs<double>& A, const LineSet
     else sw.template b_block<0>(L, C, x, rbB, rv, paired, iters, rel);
 }
 
+// Shell voxels of one Dirichlet substrate, enumerated as z planes (2 nx ny),
+// y rows of the other planes (2 nx nz), x columns (2 ny nz); overlaps are
+// written twice with the same value.
+__device__ __forceinline__ int64_t shell_count(const EpiArgs& E)
+{
+    return 2 * ((int64_t)E.nx * E.ny + (int64_t)E.nx * E.nz + (int64_t)E.ny * E.nz);
+}
+
+__device__ __forceinline__ void shell_voxel(const EpiArgs& E, int s, double v, int64_t t)
+{
+    const int64_t fz = 2 * (int64_t)E.nx * E.ny, fy = 2 * (int64_t)E.nx * E.nz;
+    int x, y, z;
+    if (t < fz) {
+        x = (int)(t % E.nx); y = (int)((t / E.nx) % E.ny); z = (t / ((int64_t)E.nx * E.ny)) ? E.nz - 1 : 0;
+    } else if ((t -= fz) < fy) {
+        x = (int)(t % E.nx); z = (int)((t / E.nx) % E.nz); y = (t / ((int64_t)E.nx * E.nz)) ? E.ny - 1 : 0;
+    } else {
+        t -= fy;
+        y = (int)(t % E.ny); z = (int)((t / E.ny) % E.nz); x = (t / ((int64_t)E.ny * E.nz)) ? E.nx - 1 : 0;
+    }
+    if (E.sc) {
+        const double* q = E.sc + (int64_t)s * E.L;
+        v = v * (__ldg(q + x) * __ldg(q + E.nx + y) * __ldg(q + E.nx + E.ny + z));
+    }
+    E.field[(((int64_t)s * E.nz + z) * E.ny + y) * E.pitch + x] = v;
+}
+
+// Wait (bounded) until counter p reaches need; lane 0 polls, then every
+// lane executes an acquire fence.
+__device__ __forceinline__ void wait_count(const StepSched& Q, const unsigned* p, unsigned need,
+                                           int lane)
+{
+    if (lane == 0) {
+        unsigned polls = 0;
+        while (ld_acquire_u32(p) < need) {
+            if (++polls > Q.max_polls) {
+                atomicExch(Q.err, 1);
+                break;
+            }
+            __nanosleep(128);
+        }
+    }
+    __syncwarp();
+    fence_acq_rel_gpu();
+}
+
+// A warp with no sweep task left takes epilogue chunks, claimed in order:
+// for each substrate s, the shell chunks of s once every task of the last
+// swept axis of s is complete, then the source chunks of s once the shell
+// of s is complete too (a cell may sit in a shell voxel).  A chunk waits
+// only on sweep tasks and on earlier chunks that never wait on it, and a
+// warp acquires each completion at most once.
+__device__ __forceinline__ void step_epilogue(const StepSched& Q, const EpiArgs& E,
+                                              const int* tf, const int* bck, const double* bcv,
+                                              int lane)
+{
+    const int n_sub = Q.n_sub;
+    const int64_t per = shell_count(E);
+    const int sh_chunks = (int)epi_shell_chunks(E.nx, E.ny, E.nz);
+    const int src_chunks = (int)epi_src_chunks(E.n_seg);
+    unsigned long long got = 0ull;   // bit s: sweeps of s acquired; bit 32 + s: shell of s
+    for (;;) {
+        unsigned c = 0;
+        if (lane == 0) c = atomicAdd(Q.eclaim, 1u);
+        c = __shfl_sync(0xffffffffu, c, 0);
+        if (c >= (unsigned)Q.n_epi_chunks) return;
+        int s = 0, k = (int)c;
+        for (; s < n_sub; ++s) {
+            const int here = (bck[s] == BFVM_BC_DIRICHLET ? sh_chunks : 0) + src_chunks;
+            if (k < here) break;
+            k -= here;
+        }
+        const bool dir = bck[s] == BFVM_BC_DIRICHLET;
+        const bool mask_ok = s < 32;
+        if (!(mask_ok && ((got >> s) & 1ull))) {
+            const int i = dep_index(tf, n_sub, 3, s);   // last swept axis of substrate s
+            if (i >= 0) wait_count(Q, Q.done + i, (unsigned)(tf[i + 1] - tf[i]) + Q.extra_need, lane);
+            if (mask_ok) got |= 1ull << s;
+        }
+        if (dir && k < sh_chunks) {
+            const int64_t lo = (int64_t)k * kEpiChunk;
+            const int64_t hi = min(per, lo + kEpiChunk);
+            for (int64_t t0 = lo + lane; t0 < hi; t0 += 32 * kEpiUnroll) {
+#pragma unroll
+                for (int u = 0; u < kEpiUnroll; ++u) {
+                    const int64_t t = t0 + 32 * u;
+                    if (t < hi) shell_voxel(E, s, bcv[s], t);
+                }
+            }
+            fence_acq_rel_gpu();
+            __syncwarp();
+            if (lane == 0) atomicAdd(Q.shell_done + s, 1u);
+            continue;
+        }
+        if (dir) {
+            k -= sh_chunks;
+            if (!(mask_ok && ((got >> (32 + s)) & 1ull))) {
+                wait_count(Q, Q.shell_done + s, (unsigned)sh_chunks + Q.extra_need, lane);
+                if (mask_ok) got |= 1ull << (32 + s);
+            }
+        }
+        const int64_t lo = (int64_t)k * kEpiChunk;
+        const int64_t hi = min(E.n_seg, lo + kEpiChunk);
+        for (int64_t g0 = lo + lane; g0 < hi; g0 += 32 * kEpiUnroll) {
+            // all reads of kEpiUnroll entries first (entries are distinct
+            // voxel-substrate pairs, so no two touch one field element)
+            int64_t o[kEpiUnroll];
+            double a[kEpiUnroll], b[kEpiUnroll], f[kEpiUnroll];
+#pragma unroll
+            for (int u = 0; u < kEpiUnroll; ++u) {
+                const int64_t g = g0 + 32 * u;
+                o[u] = -1;
+                if (g < hi) {
+                    const int64_t e = g * n_sub + s;
+                    o[u] = __ldg(E.off + e);
+                    a[u] = __ldg(E.alpha + e);
+                    b[u] = __ldg(E.beta + e);
+                    if (E.sc) {
+                        const int32_t vv = __ldg(E.vox + e);
+                        const int x = vv % E.nx;
+                        const int y = (vv / E.nx) % E.ny;
+                        const int z = vv / (E.nx * E.ny);
+                        const double* q = E.sc + (int64_t)s * E.L;
+                        b[u] *= __ldg(q + x) * __ldg(q + E.nx + y) * __ldg(q + E.nx + E.ny + z);
+                    }
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kEpiUnroll; ++u)
+                if (o[u] >= 0) f[u] = E.field[o[u]];
+#pragma unroll
+            for (int u = 0; u < kEpiUnroll; ++u)
+                if (o[u] >= 0) E.field[o[u]] = fma(a[u], f[u], b[u]);
+        }
+    }
+}
+
 __device__ __forceinline__ void pair_sync(int bar_id)
 {
     asm volatile("bar.sync %0, 64;" ::"r"(bar_id) : "memory");
@@ -425,10 +615,8 @@ __device__ __forceinline__ void f_axis(FState& f, const SweepArgs<double>& A, co
         int dep = -1;              // completion counter tn waits on (-1: none or acquired)
         if (has_next) {
             rn = decode_task(tf, Q.n_sub, f.tn);
-            if (rn.a > 0) {
-                dep = (rn.a - 1) * Q.n_sub + rn.s;
-                if (dep < 64 && ((f.acq >> dep) & 1ull)) dep = -1;
-            }
+            dep = dep_index(tf, Q.n_sub, rn.a, rn.s);
+            if (dep >= 0 && dep < 64 && ((f.acq >> dep) & 1ull)) dep = -1;
             if (dep >= 0) {
                 need = (unsigned)(tf[dep + 1] - tf[dep]) + Q.extra_need;
                 if (P.lane == 0) seen = ld_relaxed_u32(Q.done + dep);
@@ -474,7 +662,7 @@ __device__ __forceinline__ void f_axis(FState& f, const SweepArgs<double>& A, co
             f.iters = phase_iters(sA, rn.a, AXIS);
         } else {
             task_wait(Q, tf, rn, P.lane);
-            mark_acquired(f, dep);
+            if (dep >= 0) mark_acquired(f, dep);
             pair_sync(P.bar_id);                        // B has finished f.t on its own
             f.solo = true;
             f.iters = 0;
@@ -541,7 +729,7 @@ __device__ __forceinline__ void b_axis(BState& b, const SweepArgs<double>& A, co
 template <bool RENORM>
 __global__ void __launch_bounds__(256, 1)
     k_step_pair(SweepArgs<double> A0, SweepArgs<double> A1, SweepArgs<double> A2, LineSet S0,
-                LineSet S1, LineSet S2, StepSched Q, int n_slots)
+                LineSet S1, LineSet S2, StepSched Q, EpiArgs E, int n_slots)
 {
     constexpr int MZ = RENORM ? 2 : 1;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -639,7 +827,8 @@ __global__ void __launch_bounds__(256, 1)
         if (f.t < T) {
             const TaskRef r0 = decode_task(tf, n_sub, f.t);
             task_wait(Q, tf, r0, lane);
-            if (r0.a > 0) mark_acquired(f, (r0.a - 1) * n_sub + r0.s);
+            const int d0 = dep_index(tf, n_sub, r0.a, r0.s);
+            if (d0 >= 0) mark_acquired(f, d0);
         } else {
             if (lane == 0) {
                 ho[0] = T;
@@ -664,6 +853,9 @@ __global__ void __launch_bounds__(256, 1)
         b_axis<2, MZ>(b, sA[2], sS[2], fs2, sA, Q, tf, P);
     }
 
+    // sweep tasks exhausted for this warp: the step's epilogue
+    step_epilogue(Q, E, tf, bck, bcv, lane);
+
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
@@ -672,6 +864,8 @@ __global__ void __launch_bounds__(256, 1)
             // every CTA is past its last claim, wait and completion count
             *Q.claim = 0u;
             for (int i = 0; i < 3 * n_sub; ++i) Q.done[i] = 0u;
+            *Q.eclaim = 0u;
+            for (int i = 0; i < n_sub; ++i) Q.shell_done[i] = 0u;
             *Q.exit_count = 0u;
             __threadfence();
         }

@@ -471,6 +471,7 @@ bfvm_status launch_axis(Ctx* c, const SweepArgs<T>& A)
 // does not qualify (the caller then launches the axes one by one).
 bfvm_status launch_step_fused(Ctx* c, int p, bool renorm)
 {
+    // also runs the step's Dirichlet shell and cell sources (its epilogue)
     constexpr int G = persistent::Groups<double>::G;
     if (!c->fused_step || c->sweep_kernel != 0 || !c->d_task_first || !c->d_sched ||
         c->n_sub > 64)
@@ -497,7 +498,6 @@ bfvm_status launch_step_fused(Ctx* c, int p, bool renorm)
     const int pairs_axis = (int)std::min<size_t>(4, (c->smem_optin - fixed_axis) / pair_bytes);
     if (pairs < pairs_axis) return BFVM_ESTATE;
     KernelTimer timer(c, 4);
-    if (c->n_tasks == 0) return BFVM_OK;
     SweepArgs<double> A[3];
     persistent::LineSet S[3];
     for (int a = 0; a < 3; ++a) {
@@ -518,15 +518,38 @@ bfvm_status launch_step_fused(Ctx* c, int p, bool renorm)
     Q.n_tasks = c->n_tasks;
     Q.max_polls = c->wait_test_polls > 0 ? (unsigned)c->wait_test_polls : persistent::kMaxPolls;
     Q.extra_need = c->wait_test_polls > 0 ? 1u : 0u;
+    Q.eclaim = c->d_sched + 2 + 3 * c->n_sub;
+    Q.shell_done = Q.eclaim + 1;
+    const int64_t n_seg = c->n_sub > 0 ? c->src.n_entries / c->n_sub : 0;
+    int64_t n_epi = 0;
+    for (int s = 0; s < c->n_sub; ++s)
+        n_epi += (c->bc_kind[s] == BFVM_BC_DIRICHLET ? persistent::epi_shell_chunks(c->nx, c->ny, c->nz) : 0) +
+                 persistent::epi_src_chunks(n_seg);
+    Q.n_epi_chunks = (int)n_epi;
+    persistent::EpiArgs E;
+    E.field = reinterpret_cast<double*>(c->field);
+    E.nx = c->nx;
+    E.ny = c->ny;
+    E.nz = c->nz;
+    E.pitch = c->pitch;
+    E.L = c->coef.L;
+    E.sc = renorm ? nullptr : A[0].sc_p1;
+    E.n_seg = n_seg;
+    E.off = c->src.off;
+    E.alpha = c->src.alpha;
+    E.beta = c->src.beta;
+    E.vox = c->src.vox;
+    E.sub = c->src.sub;
     const size_t smem = fixed + pair_bytes * pairs;
-    int64_t grid = ceil_div(c->n_tasks, pairs);
+    int64_t grid = ceil_div(std::max<int64_t>(c->n_tasks, 1), pairs);
+    grid = std::max<int64_t>(grid, ceil_div(Q.n_epi_chunks, 8 * pairs));
     if (grid > c->sm_count) grid = c->sm_count;
     if (c->grid_limit > 0 && grid > c->grid_limit) grid = c->grid_limit;
     auto kern = renorm ? persistent::k_step_pair<true> : persistent::k_step_pair<false>;
     BFVM_CUDA(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)smem));
     kern<<<(unsigned)grid, 64 * pairs, smem, c->stream>>>(A[0], A[1], A[2], S[0], S[1], S[2], Q,
-                                                          ns);
+                                                          E, ns);
     c->launches += 1;
     BFVM_CUDA(c, cudaGetLastError());
     return BFVM_OK;
@@ -606,7 +629,7 @@ bfvm_status build_line_tables(Ctx* c)
     BFVM_CUDA(c, cudaMalloc(&c->d_task_first, sizeof(int) * tf.size()));
     BFVM_CUDA(c, cudaMemcpy(c->d_task_first, tf.data(), sizeof(int) * tf.size(),
                             cudaMemcpyHostToDevice));
-    const size_t nsched = 2 + 3 * (size_t)c->n_sub;
+    const size_t nsched = 2 + 3 * (size_t)c->n_sub + 1 + (size_t)c->n_sub;
     BFVM_CUDA(c, cudaMalloc(&c->d_sched, sizeof(unsigned) * nsched));
     BFVM_CUDA(c, cudaMemset(c->d_sched, 0, sizeof(unsigned) * nsched));
     return BFVM_OK;
@@ -688,6 +711,7 @@ bfvm_status launch_step(Ctx* c, int p, bool renorm)
         return launch_sources(c, 0, true);
     }
     st = launch_step_fused(c, p, renorm);
+    if (st == BFVM_OK) return BFVM_OK;   // sweeps, shell and sources in one launch
     if (st == BFVM_ESTATE) {
         if (renorm) st = launch_xyz<double, 2>(c, p, c->coef.r, c->coef.cr, c->coef.c);
         else st = launch_xyz<double, 1>(c, p, c->coef.r, c->coef.cr, c->coef.c);
