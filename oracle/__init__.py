@@ -88,6 +88,13 @@ def _load():
                       + [_dp, _dp, _ip, _dp, ctypes.c_int64, _dp, _dp, _dp, _dp, _dp])
             lib.oracle_run.argtypes = common + [ctypes.c_int, ctypes.c_int, _dp]
             lib.oracle_run.restype = ctypes.c_int
+            lib.oracle_run_2d.argtypes = common + [ctypes.c_int, ctypes.c_int, _dp]
+            lib.oracle_run_2d.restype = ctypes.c_int
+            lib.oracle_apply_dirichlet_2d.argtypes = [ctypes.c_int] * 3 + [_ip, _dp, _dp]
+            lib.oracle_apply_dirichlet_2d.restype = None
+            lib.oracle_axis_solve_2d.argtypes = ([ctypes.c_int] * 4 + [ctypes.c_double] * 2
+                                                 + [_dp, _dp, _dp])
+            lib.oracle_axis_solve_2d.restype = None
             lib.oracle_adjoint.argtypes = common + [ctypes.c_int] * 3 + [_dp] * 8
             lib.oracle_adjoint.restype = ctypes.c_int
             lib.oracle_max_threads.argtypes = []
@@ -163,12 +170,14 @@ def _common(p):
 
 
 def run(p, rho0=None, n_steps=None, n_threads: int = 0):
-    """Field after n_steps (default p.steps) full steps from rho0 (default p.rho0)."""
+    """Field after n_steps (default p.steps) full steps from rho0 (default p.rho0);
+    the 2-D variant (oracle_run_2d) when the problem's `dims` is 2."""
     lib = _load()
     rho = _f64(p.rho0 if rho0 is None else rho0).copy()
     steps = int(p.steps if n_steps is None else n_steps)
     args, keep = _common(p)
-    rc = lib.oracle_run(*args, steps, int(n_threads or max_threads()), _d(rho))
+    fn = lib.oracle_run_2d if getattr(p, "dims", 3) == 2 else lib.oracle_run
+    rc = fn(*args, steps, int(n_threads or max_threads()), _d(rho))
     if rc != 0:
         raise ValueError(f"oracle_run failed ({rc})")
     del keep
@@ -236,4 +245,26 @@ def apply_sources(p, rho):
                              float(p.dt), ctypes.c_int64(cells.n), _d(cells.pos),
                              _d(cells.vol), _d(cells.S), _d(cells.U),
                              _d(cells.rho_star), _d(rho))
+    return rho
+
+
+def apply_dirichlet_2d(p, rho):
+    """The 2-D Dirichlet shell (the four edges of an nx x ny x 1 grid)."""
+    lib = _load()
+    rho = _f64(rho).copy()
+    kind = np.ascontiguousarray(p.bc_kind, dtype=np.int32)
+    val = _f64(p.bc_value)
+    lib.oracle_apply_dirichlet_2d(int(p.nx), int(p.ny), len(p.D), kind.ctypes.data_as(_ip),
+                                  _d(val), _d(rho))
+    return rho
+
+
+def axis_solve_2d(p, rho, axis: int):
+    """One 2-D line solve (decay share lambda dt / 2) along x (0) or y (1)."""
+    lib = _load()
+    rho = _f64(rho).copy()
+    D = _f64(p.D)
+    lam = _f64(p.lam)
+    lib.oracle_axis_solve_2d(int(axis), int(p.nx), int(p.ny), len(p.D), float(p.dx),
+                             float(p.dt), _d(D), _d(lam), _d(rho))
     return rho

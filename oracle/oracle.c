@@ -246,6 +246,78 @@ int oracle_run(int nx, int ny, int nz, double dx, double dt, int n_sub,
 }
 
 /* ------------------------------------------------------------------ */
+/* 2-D variant (the paper also ports BioFVM's 2-D diffusion: x- and    */
+/* y-diffusion only, "Using OpenACC programming model for PhysiCell"). */
+/* The grid is nx x ny x 1.  Each of the two axes takes half of the    */
+/* decay, ell = lambda dt / 2; the Dirichlet shell is the outer layer  */
+/* of the four edges x = 0, nx-1 and y = 0, ny-1 (the single z layer   */
+/* is not a boundary).  Step: Dirichlet, x-solve, Dirichlet, y-solve,  */
+/* Dirichlet, sources (V_vox = dx^3 as in 3-D).                        */
+/* ------------------------------------------------------------------ */
+void oracle_apply_dirichlet_2d(int nx, int ny, int n_sub, const int* bc_kind,
+                               const double* bc_value, double* rho)
+{
+    for (int s = 0; s < n_sub; ++s) {
+        if (bc_kind[s] != 1) continue;
+        for (int y = 0; y < ny; ++y)
+            for (int x = 0; x < nx; ++x)
+                if (x == 0 || x == nx - 1 || y == 0 || y == ny - 1)
+                    rho[vox_index(nx, ny, 1, s, 0, y, x)] = bc_value[s];
+    }
+}
+
+/* One implicit solve along axis 0 (x) or 1 (y) of a 2-D grid with the
+ * 2-D decay share lambda dt / 2. */
+void oracle_axis_solve_2d(int axis, int nx, int ny, int n_sub, double dx, double dt,
+                          const double* D, const double* lambda, double* rho)
+{
+    const int n_axis = axis == 0 ? nx : ny;
+    const int n_other = axis == 0 ? ny : nx;
+    const int64_t stride = axis == 0 ? 1 : (int64_t)nx;
+    double* buf = (double*)malloc(sizeof(double) * 6 * (size_t)n_axis);
+    double* lower = buf;
+    double* diag = buf + n_axis;
+    double* upper = buf + 2 * n_axis;
+    double* rhs = buf + 3 * n_axis;
+    double* x = buf + 4 * n_axis;
+    double* work = buf + 5 * n_axis;
+    for (int s = 0; s < n_sub; ++s) {
+        double c = D[s] * dt / (dx * dx);
+        double ell = lambda[s] * dt / 2.0;
+        oracle_line_matrix(n_axis, c, ell, lower, diag, upper);
+        for (int o = 0; o < n_other; ++o) {
+            int64_t base = axis == 0 ? vox_index(nx, ny, 1, s, 0, o, 0)
+                                     : vox_index(nx, ny, 1, s, 0, 0, o);
+            for (int i = 0; i < n_axis; ++i) rhs[i] = rho[base + i * stride];
+            oracle_tridiag_solve(n_axis, lower, diag, upper, rhs, x, work);
+            for (int i = 0; i < n_axis; ++i) rho[base + i * stride] = x[i];
+        }
+    }
+    free(buf);
+}
+
+/* n_steps 2-D steps in place on rho (nz must be 1). */
+int oracle_run_2d(int nx, int ny, int nz, double dx, double dt, int n_sub,
+                  const double* D, const double* lambda, const int* bc_kind,
+                  const double* bc_value, int64_t n_cells, const double* pos,
+                  const double* vol, const double* S, const double* U,
+                  const double* rho_star, int n_steps, int n_threads, double* rho)
+{
+    (void)n_threads;
+    if (nx < 1 || ny < 1 || nz != 1 || n_sub < 1 || n_steps < 0) return 1;
+    for (int t = 0; t < n_steps; ++t) {
+        oracle_apply_dirichlet_2d(nx, ny, n_sub, bc_kind, bc_value, rho);
+        for (int axis = 0; axis < 2; ++axis) {
+            oracle_axis_solve_2d(axis, nx, ny, n_sub, dx, dt, D, lambda, rho);
+            oracle_apply_dirichlet_2d(nx, ny, n_sub, bc_kind, bc_value, rho);
+        }
+        oracle_apply_sources(nx, ny, 1, n_sub, dx, dt, n_cells, pos, vol, S, U,
+                             rho_star, rho);
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
 /* Reverse mode of oracle_run: the literal adjoint of every operation  */
 /* of every step, taken in reverse.                                     */
 /*                                                                      */

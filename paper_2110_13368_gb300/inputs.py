@@ -67,6 +67,7 @@ class Problem:
     precision: int = 64
     name: str = ""
     meta: dict = field(default_factory=dict)
+    dims: int = 3                     # 2: the 2-D variant (nz == 1, x and y sweeps only)
 
     @property
     def n_sub(self) -> int:
@@ -110,7 +111,7 @@ def make_problem(nx, ny, nz, *, n_sub=1, D=1e5, lam=0.1, dx=20.0, dt=0.01,
                  bc_kind=0, bc_value=38.0, field_mode="noise", n_cells=0,
                  cell_mode="uniform", sphere_radius=None, vol_mode="fixed",
                  U=10.0, S=0.0, rho_star=38.0, steps=1, seed=0, precision=64,
-                 name="custom"):
+                 name="custom", dims=3):
     """A generic problem; scalars broadcast over substrates, per-cell rates
     are the given constants broadcast to [n_cells][n_sub]."""
     rng = np.random.default_rng(seed)
@@ -125,8 +126,10 @@ def make_problem(nx, ny, nz, *, n_sub=1, D=1e5, lam=0.1, dx=20.0, dt=0.01,
         rho0 = np.zeros(shape)
     else:
         raise ValueError(field_mode)
+    if dims == 2 and nz != 1:
+        raise ValueError("the 2-D variant needs nz == 1")
     p = Problem(nx, ny, nz, float(dx), float(dt), D, lam, kind, val, _arr(rho0),
-                steps=int(steps), precision=int(precision), name=name)
+                steps=int(steps), precision=int(precision), name=name, dims=int(dims))
     if n_cells > 0:
         extent = (nx * dx, ny * dx, nz * dx)
         if cell_mode == "uniform":

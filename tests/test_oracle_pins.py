@@ -330,3 +330,88 @@ def test_oracle_threads_do_not_change_bits():
     a = oracle.run(p, n_steps=3, n_threads=1)
     b = oracle.run(p, n_steps=3, n_threads=4)
     np.testing.assert_array_equal(a, b)
+
+
+# ------------------------------------------------------------ 2-D variant
+def test_2d_uniform_field_decays_by_closed_form():
+    """2-D variant: two sweeps, each with half of the decay: (1 + lambda dt/2)^-2."""
+    p = inputs.make_problem(9, 6, 1, D=1e5, lam=0.1, field_mode="zero", dims=2)
+    p.rho0[:] = 38.0
+    ell = p.lam[0] * p.dt / 2
+    np.testing.assert_allclose(oracle.run(p, n_steps=1), 38.0 * (1 + ell) ** -2, rtol=1e-14)
+    np.testing.assert_allclose(oracle.run(p, n_steps=4), 38.0 * (1 + ell) ** -8, rtol=1e-13)
+
+
+@pytest.mark.parametrize("dims,ks", [((12, 7), (3, 1)), ((5, 16), (0, 5)), ((1, 9), (0, 4))])
+def test_2d_cosine_modes_are_eigenfunctions(dims, ks):
+    nx, ny = dims
+    p = inputs.make_problem(nx, ny, 1, D=3e4, lam=0.05, field_mode="zero", dims=2)
+    cx = np.cos(np.pi * ks[0] * (np.arange(nx) + 0.5) / nx)
+    cy = np.cos(np.pi * ks[1] * (np.arange(ny) + 0.5) / ny)
+    mode = (cy[:, None] * cx[None, :])[None]
+    p.rho0[0] = mode
+    c = p.D[0] * p.dt / p.dx ** 2
+    ell = p.lam[0] * p.dt / 2
+    fac = 1.0
+    for n, k in zip(dims, ks):
+        fac /= 1 + ell + 2 * c * (1 - np.cos(np.pi * k / n))
+    r = oracle.run(p, n_steps=2)[0]
+    np.testing.assert_allclose(r, fac ** 2 * mode, rtol=0, atol=1e-14 * np.abs(mode).max())
+
+
+def _dense_run_2d(p, n_steps):
+    nx, ny = p.nx, p.ny
+    y, x = np.meshgrid(np.arange(ny), np.arange(nx), indexing="ij")
+    shell = ((x == 0) | (x == nx - 1) | (y == 0) | (y == ny - 1)).ravel()
+    rho = p.rho0.reshape(p.n_sub, -1).copy()
+    vvox = p.dx ** 3
+    for _ in range(n_steps):
+        for s in range(p.n_sub):
+            c = p.D[s] * p.dt / p.dx ** 2
+            ell = p.lam[s] * p.dt / 2
+            Ax = (1 + ell) * np.eye(nx) + c * _laplacian_from_fluxes(nx)
+            Ay = (1 + ell) * np.eye(ny) + c * _laplacian_from_fluxes(ny)
+            ops = [np.kron(np.eye(ny), Ax), np.kron(Ay, np.eye(nx))]
+            u = rho[s]
+            dir_ = p.bc_kind[s] == 1
+            if dir_:
+                u[shell] = p.bc_value[s]
+            for M in ops:
+                u = sla.lu_solve(sla.lu_factor(M), u)
+                if dir_:
+                    u[shell] = p.bc_value[s]
+            rho[s] = u
+        for i in range(p.n_cells):
+            v = [min(int(np.floor(p.pos[i, a] / p.dx)), n - 1) for a, n in enumerate((nx, ny, 1))]
+            lin = v[1] * nx + v[0]
+            w = p.dt * p.vol[i] / vvox
+            for s in range(p.n_sub):
+                rho[s, lin] = ((rho[s, lin] + w * p.S[i, s] * p.rho_star[i, s])
+                               / (1 + w * (p.S[i, s] + p.U[i, s])))
+    return rho.reshape(p.rho0.shape)
+
+
+@pytest.mark.parametrize("dims", [(3, 4), (1, 7), (2, 2), (6, 5)])
+def test_2d_dense_lu_tiny_grids(dims):
+    """2-D step against Kronecker-assembled dense solves with the 2-D shell
+    (four edges, not the z layer) and the same cell sources."""
+    nx, ny = dims
+    p = inputs.make_problem(nx, ny, 1, n_sub=3, D=[1e5, 2e3, 4e4], lam=[0.1, 0.0, 0.9],
+                            bc_kind=[1, 0, 1], bc_value=[38.0, 0.0, 5.0], n_cells=5,
+                            U=[10.0, 1.0, 0.0], S=[0.0, 3.0, 7.0], rho_star=[1.0, 38.0, 2.0],
+                            seed=13, dims=2)
+    ref = _dense_run_2d(p, 3)
+    got = oracle.run(p, n_steps=3)
+    np.testing.assert_allclose(got, ref, rtol=0, atol=1e-13 * np.abs(ref).max())
+
+
+def test_2d_equals_3d_step_without_decay():
+    """With lambda = 0 and zero-flux faces the 3-D step on an nx x ny x 1
+    grid is the 2-D step (the z line matrix is [1]); mass is conserved."""
+    p3 = inputs.make_problem(11, 8, 1, n_sub=2, D=[1e5, 3e2], lam=0.0, n_cells=7,
+                             U=[2.0, 0.0], S=[0.0, 4.0], rho_star=[1.0, 2.0], seed=4)
+    p2 = p3.with_(dims=2)
+    np.testing.assert_array_equal(oracle.run(p2, n_steps=5), oracle.run(p3, n_steps=5))
+    q = p3.with_(pos=None, vol=None, S=None, U=None, rho_star=None, dims=2)
+    m0 = q.rho0.sum(axis=(1, 2, 3))
+    np.testing.assert_allclose(oracle.run(q, n_steps=6).sum(axis=(1, 2, 3)), m0, rtol=1e-13)
