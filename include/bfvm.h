@@ -176,7 +176,7 @@ const char* bfvm_status_string(int32_t status);
  *  6 number of source voxels, 7 steps taken since create,
  *  8 sweep variant in use (0 plain, 1 rescaled), 9 rescale period,
  *  10 device kernel launches issued since create, 11 recorded steps,
- *  12..15 reserved (0).
+ *  12 dimensions (3, or 2 for the 2-D variant), 13..15 reserved (0).
  */
 bfvm_status bfvm_get_info(const bfvm_ctx* ctx, int64_t* info);
 
@@ -201,6 +201,14 @@ bfvm_status bfvm_get_info(const bfvm_ctx* ctx, int64_t* info);
  *          warp pairs take (axis, substrate, 32-line block) tasks in order,
  *          a task starting once the previous axis of its substrate is
  *          complete; 0 launches one kernel per axis
+ *   key 10 dimensions: 3 (the default) or 2, the 2-D variant of the step
+ *          (the paper ports BioFVM's 2-D diffusion too): for an nx x ny x 1
+ *          grid, an x-solve and a y-solve per step, each line matrix with
+ *          decay share lambda dt / 2; the Dirichlet shell is the outer layer
+ *          of the four edges (the z layer is not a boundary); sources as in
+ *          3-D with V_vox = dx^3.  Needs nz == 1; FP64 then runs the plain
+ *          Thomas form (option 1 = 0).  2-D contexts cannot record for the
+ *          adjoint or join a batch (BFVM_ESTATE).
  *   key 9  test of the bounded device waits of key 8's launch: a value
  *          v > 0 makes every dependency wait unreachable and give up after
  *          v polls, so the next synchronising call reports BFVM_ETIMEOUT

@@ -32,6 +32,7 @@ OPT_GRID_LIMIT = 6
 OPT_SWEEP_KERNEL = 7
 OPT_FUSED_STEP = 8
 OPT_WAIT_TEST = 9
+OPT_DIMS = 10
 
 EXPORTED = ["bfvm_create", "bfvm_destroy", "bfvm_set_density", "bfvm_get_density",
             "bfvm_set_cells", "bfvm_step", "bfvm_sync", "bfvm_record", "bfvm_backward",
@@ -228,7 +229,7 @@ def bfvm_get_info(h):
     info = (_i64 * 16)()
     _check(load_library().bfvm_get_info(h, info), h)
     keys = ["precision", "nx", "ny", "nz", "n_sub", "pitch", "n_source_voxels",
-            "steps_taken", "variant", "period", "launches", "recorded_steps"]
+            "steps_taken", "variant", "period", "launches", "recorded_steps", "dims"]
     return {k: int(info[i]) for i, k in enumerate(keys)}
 
 
@@ -376,6 +377,8 @@ class Sim:
         import torch
         prec = p.precision if precision is None else precision
         s = cls(p.nx, p.ny, p.nz, p.dx, p.dt, p.D, p.lam, p.bc_kind, p.bc_value, prec, stream)
+        if getattr(p, "dims", 3) == 2:
+            s.set_option(OPT_DIMS, 2)
         s.set_density(torch.as_tensor(p.rho0, dtype=s.dtype, device=s.device))
         if p.n_cells:
             arrs = [p.pos, p.vol, p.S, p.U, p.rho_star]

@@ -418,6 +418,8 @@ bfvm_status bfvm_record(bfvm_ctx* h, int32_t checkpoint_every)
     if (checkpoint_every < 0) return set_err(c, BFVM_EINVAL, "checkpoint_every must be >= 0");
     if (checkpoint_every > 0 && c->precision != 64)
         return set_err(c, BFVM_EINVAL, "the adjoint needs an FP64 context");
+    if (checkpoint_every > 0 && c->dims != 3)
+        return set_err(c, BFVM_ESTATE, "the adjoint covers the 3-D step only");
     drop_recording(c);
     c->record_every = checkpoint_every;
     return BFVM_OK;
@@ -509,6 +511,7 @@ bfvm_status bfvm_get_info(const bfvm_ctx* h, int64_t* info)
     info[9] = c->coef.period;
     info[10] = c->launches;
     info[11] = c->recorded ? c->recorded_steps : 0;
+    info[12] = c->dims;
     return BFVM_OK;
 }
 
@@ -521,6 +524,8 @@ bfvm_status bfvm_set_option(bfvm_ctx* h, int32_t key, int64_t value)
             if (value != 0 && value != 1) return set_err(c, BFVM_EINVAL, "variant must be 0 or 1");
             if (value == 1 && c->precision != 64)
                 return set_err(c, BFVM_EINVAL, "the rescaled sweep is FP64 only");
+            if (value == 1 && c->dims != 3)
+                return set_err(c, BFVM_EINVAL, "the rescaled sweep renormalises in the z sweep: 3-D only");
             if (c->scale_state != 0) return set_err(c, BFVM_ESTATE, "field is mid-rescale; step to a period end first");
             c->variant = (int)value;
             drop_graphs(c);
@@ -566,6 +571,21 @@ bfvm_status bfvm_set_option(bfvm_ctx* h, int32_t key, int64_t value)
             c->wait_test_polls = (int)value;
             drop_graphs(c);
             return BFVM_OK;
+        case 10: {
+            if (value != 2 && value != 3) return set_err(c, BFVM_EINVAL, "dims must be 2 or 3");
+            if (value == c->dims) return BFVM_OK;
+            if (value == 2 && c->nz != 1) return set_err(c, BFVM_EINVAL, "the 2-D variant needs nz == 1");
+            if (c->scale_state != 0) return set_err(c, BFVM_ESTATE, "field is mid-rescale; step to a period end first");
+            if (c->record_every != 0) return set_err(c, BFVM_ESTATE, "the adjoint covers the 3-D step only");
+            c->dims = (int)value;
+            // the rescaled form renormalises in the z sweep: 2-D runs the plain form
+            c->variant = (c->precision == 64 && c->dims == 3) ? 1 : 0;
+            drop_graphs(c);
+            c->free_line_tables();
+            bfvm_status st = build_coefficients(c);
+            if (st != BFVM_OK) return st;
+            return build_line_tables(c);
+        }
         default:
             return set_err(c, BFVM_EINVAL, "unknown option key");
     }

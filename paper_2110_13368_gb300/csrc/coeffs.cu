@@ -30,6 +30,7 @@ struct CoefParams {
     int off[3];
     int L;
     int n_sub;
+    int dims;          // 3, or 2 for the 2-D variant (decay share lambda dt / dims per axis)
     double dx, dt;
     const double* D;
     const double* lambda;
@@ -44,7 +45,7 @@ __global__ void k_pivots(CoefParams P, double* r, double* cr, double* cvec,
     int s = t / 3, a = t % 3;
     int n = P.n[a];
     double c = P.D[s] * P.dt / (P.dx * P.dx);
-    double ell = P.lambda[s] * P.dt / 3.0;
+    double ell = P.lambda[s] * P.dt / (double)P.dims;
     cvec[s * 3 + a] = c;
     int64_t base = (int64_t)s * P.L + P.off[a];
     double den_prev = 1.0;
@@ -117,7 +118,7 @@ static int rescale_period(const Ctx* c)
     double worst = 0.0;
     for (int s = 0; s < c->n_sub; ++s) {
         double cc = c->D[s] * c->dt / (c->dx * c->dx);
-        double ell = c->lambda[s] * c->dt / 3.0;
+        double ell = c->lambda[s] * c->dt / (double)c->dims;
         double g = 3.0 * log10(1.0 + ell + 2.0 * cc);
         if (g > worst) worst = g;
     }
@@ -150,6 +151,7 @@ bfvm_status build_coefficients(Ctx* c)
                                  cudaMemcpyHostToDevice, c->stream));
     P.D = dD;
     P.lambda = dl;
+    P.dims = c->dims;
     BFVM_CUDA(c, cudaMalloc(&T.r, sizeof(double) * n_tab));
     BFVM_CUDA(c, cudaMalloc(&T.cr, sizeof(double) * n_tab));
     BFVM_CUDA(c, cudaMalloc(&T.c, sizeof(double) * c->n_sub * 3));

@@ -89,6 +89,8 @@ struct Ctx {
     int grid_limit = 0;           // cap on persistent sweep CTAs (0 = one per SM)
     int sweep_kernel = 0;         // FP64: 0 warp pairs, 1 one warp per buffer
     int fused_step = 1;           // FP64 rescaled pairs: 1 one launch for x, y, z
+    int dims = 3;                 // 2: the 2-D variant (nz == 1; x and y sweeps,
+                                  // lambda dt / 2 each, four-edge Dirichlet shell)
     int wait_test_polls = 0;      // > 0: the step's dependency waits cannot end and
                                   // give up after this many polls (tests only)
     int scale_state = 0;          // rescale state p of the stored field

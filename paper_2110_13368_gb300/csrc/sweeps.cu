@@ -88,6 +88,7 @@ struct SweepArgs {
     const double* isc_p1;  // [s][L] inverses of state p + 1
     const int32_t* bc_kind;
     const double* bc_value;
+    int dims;              // 3, or 2: the single z layer of a 2-D grid is not a boundary
 };
 
 // MODE 0: plain Thomas (3 flops per element: FMA + MUL forward, FMA back).
@@ -132,7 +133,7 @@ __device__ __forceinline__ void sweep_one_line(const SweepArgs<T>& A, int64_t li
         ox = -1;
         base = (((int64_t)s * A.nz + oz) * A.ny + oy) * A.pitch;
         stride = 1;
-        other_shell = (oy == 0 || oy == A.ny - 1 || oz == 0 || oz == A.nz - 1);
+        other_shell = (oy == 0 || oy == A.ny - 1 || (A.dims == 3 && (oz == 0 || oz == A.nz - 1)));
     } else if (AXIS == 1) {
         int64_t t = line;
         ox = (int)(t % A.nx); t /= A.nx;
@@ -140,7 +141,7 @@ __device__ __forceinline__ void sweep_one_line(const SweepArgs<T>& A, int64_t li
         oy = -1;
         base = (((int64_t)s * A.nz + oz) * A.ny) * A.pitch + ox;
         stride = A.pitch;
-        other_shell = (ox == 0 || ox == A.nx - 1 || oz == 0 || oz == A.nz - 1);
+        other_shell = (ox == 0 || ox == A.nx - 1 || (A.dims == 3 && (oz == 0 || oz == A.nz - 1)));
     } else {
         int64_t t = line;
         ox = (int)(t % A.nx); t /= A.nx;
@@ -386,6 +387,7 @@ SweepArgs<T> make_args(Ctx* c, int axis, int p, const T* r, const T* cr,
     }
     A.bc_kind = c->d_bc_kind;
     A.bc_value = c->d_bc_value;
+    A.dims = c->dims;
     return A;
 }
 
@@ -474,7 +476,7 @@ bfvm_status launch_step_fused(Ctx* c, int p, bool renorm)
     // also runs the step's Dirichlet shell and cell sources (its epilogue)
     constexpr int G = persistent::Groups<double>::G;
     if (!c->fused_step || c->sweep_kernel != 0 || !c->d_task_first || !c->d_sched ||
-        c->n_sub > 64)
+        c->n_sub > 64 || c->dims != 3)
         return BFVM_ESTATE;
     for (int a = 0; a < 3; ++a)
         if (!c->line_tables_ready[a]) return BFVM_ESTATE;
@@ -562,6 +564,7 @@ bfvm_status launch_xyz(Ctx* c, int p, const T* r, const T* cr, const T* cv)
     bfvm_status st;
     if ((st = launch_axis<T, 0, M>(c, make_args<T>(c, 0, p, r, cr, cv))) != BFVM_OK) return st;
     if ((st = launch_axis<T, 1, M>(c, make_args<T>(c, 1, p, r, cr, cv))) != BFVM_OK) return st;
+    if (c->dims == 2) return BFVM_OK;   // 2-D variant: x and y sweeps only
     return launch_axis<T, 2, MODE_Z>(c, make_args<T>(c, 2, p, r, cr, cv));
 }
 
@@ -604,12 +607,16 @@ bfvm_status build_line_tables(Ctx* c)
         first[0] = 0;
         for (int s = 0; s < c->n_sub; ++s) {
             bool dir = c->bc_kind[s] == BFVM_BC_DIRICHLET;
-            int ca = dir ? ea - 2 : ea, cb = dir ? eb - 2 : eb;
+            // 2-D variant: z is not a boundary coordinate (the slow other
+            // coordinate of the x and y lines), and there is no z sweep
+            const bool b_dir = dir && !(c->dims == 2 && axis < 2);
+            int ca = dir ? ea - 2 : ea, cb = b_dir ? eb - 2 : eb;
             if (ca < 0) ca = 0;
             if (cb < 0) cb = 0;
+            if (c->dims == 2 && axis == 2) ca = cb = 0;
             c->lines_lo_a[axis][s] = dir ? 1 : 0;
             c->lines_cnt_a[axis][s] = ca > 0 ? ca : 1;
-            c->lines_lo_b[axis][s] = dir ? 1 : 0;
+            c->lines_lo_b[axis][s] = b_dir ? 1 : 0;
             first[s + 1] = first[s] + (int64_t)ca * cb;
         }
         BFVM_CUDA(c, c->ensure_line_tables(axis, first));
@@ -683,11 +690,11 @@ bfvm_status launch_shell_fill(Ctx* c, int p_scale)
     if (c->precision == 64)
         persistent::k_shell_fill<double><<<grid, 256, 0, c->stream>>>(
             reinterpret_cast<double*>(c->field), c->nx, c->ny, c->nz, c->n_sub, c->pitch,
-            c->d_bc_kind, c->d_bc_value, c->coef.L, sc);
+            c->d_bc_kind, c->d_bc_value, c->coef.L, sc, c->dims);
     else
         persistent::k_shell_fill<float><<<grid, 256, 0, c->stream>>>(
             reinterpret_cast<float*>(c->field), c->nx, c->ny, c->nz, c->n_sub, c->pitch,
-            c->d_bc_kind, c->d_bc_value, c->coef.L, nullptr);
+            c->d_bc_kind, c->d_bc_value, c->coef.L, nullptr, c->dims);
     c->launches += 1;
     BFVM_CUDA(c, cudaGetLastError());
     return BFVM_OK;

@@ -288,3 +288,67 @@ def test_invalid_cells_rejected(bf):
     got = sim.get_density().cpu().numpy()
     sim.close()
     assert np.all(rel_inf(got, oracle.run(p)) <= TOL64)
+
+
+# ------------------------------------------------------------ 2-D variant
+CASES_2D = {
+    "ragged_37x45": lambda: mixed(37, 45, 1, dims=2),
+    "thin_1x9": lambda: mixed(1, 9, 1, n_cells=3, dims=2),
+    "thin_2x3": lambda: mixed(2, 3, 1, n_cells=4, dims=2),
+    "flat_64x2": lambda: mixed(64, 2, 1, dims=2),
+    "long_x_300": lambda: mixed(300, 6, 1, n_cells=50, steps=3, dims=2),
+    "long_y_1000": lambda: mixed(3, 1000, 1, n_cells=50, steps=3, dims=2),
+    "no_cells_3sub": lambda: inputs.make_problem(23, 17, 1, n_sub=3, D=[1e5, 3e2, 4e4],
+                                                 lam=[0.1, 0.0, 0.9], bc_kind=[1, 0, 1],
+                                                 bc_value=[38.0, 0.0, 5.0], steps=5, seed=2,
+                                                 dims=2),
+}
+
+
+@pytest.mark.parametrize("grid_limit", [0, 2])
+@pytest.mark.parametrize("precision,tol", [(64, TOL64), (32, TOL32)])
+@pytest.mark.parametrize("case", sorted(CASES_2D))
+def test_2d_variant_matches_oracle(bf, case, precision, tol, grid_limit):
+    """The 2-D variant (option 10): x and y sweeps with half the decay each
+    and the four-edge Dirichlet shell, against the 2-D oracle; lines from 1
+    voxel to longer than shared memory (the generic one-thread-per-line
+    sweep)."""
+    p = CASES_2D[case]()
+    ref = oracle.run(p)
+    sim = bf.Sim.from_problem(p, precision=precision)
+    if grid_limit:
+        sim.set_option(bf.OPT_GRID_LIMIT, grid_limit)
+    info = sim.info()
+    assert info["dims"] == 2 and info["variant"] == 0
+    sim.step(p.steps)
+    got = sim.get_density().double().cpu().numpy()
+    sim.close()
+    err = rel_inf(got, ref)
+    assert np.all(err <= tol), (case, precision, err)
+
+
+def test_2d_variant_option_rules(bf):
+    p3 = mixed(10, 9, 4)
+    sim = bf.Sim.from_problem(p3)
+    with pytest.raises(bf.BfvmError) as ei:
+        sim.set_option(bf.OPT_DIMS, 2)                  # nz != 1
+    assert ei.value.status == 1
+    sim.close()
+    p = mixed(10, 9, 1, dims=2)
+    sim = bf.Sim.from_problem(p)
+    with pytest.raises(bf.BfvmError):
+        sim.set_option(bf.OPT_VARIANT, 1)               # rescaled form needs the z sweep
+    with pytest.raises(bf.BfvmError) as ei:
+        sim.record(2)
+    assert ei.value.status == 4
+    with pytest.raises(bf.BfvmError):
+        bf.Batch([sim])
+    # back to 3-D on the same single-layer grid: the 3-D step again
+    sim.set_option(bf.OPT_DIMS, 3)
+    import torch
+    sim.set_density(torch.as_tensor(p.rho0, device=sim.device))
+    sim.step(p.steps)
+    got = sim.get_density().cpu().numpy()
+    sim.close()
+    ref = oracle.run(p.with_(dims=3))
+    assert np.all(rel_inf(got, ref) <= TOL64)
