@@ -90,6 +90,10 @@ def _load():
             lib.oracle_run.restype = ctypes.c_int
             lib.oracle_run_2d.argtypes = common + [ctypes.c_int, ctypes.c_int, _dp]
             lib.oracle_run_2d.restype = ctypes.c_int
+            _lp = ctypes.POINTER(ctypes.c_int64)
+            lib.oracle_run_nodes.argtypes = (common + [ctypes.c_int64, _lp, _ip, _dp]
+                                             + [ctypes.c_int, ctypes.c_int, _dp])
+            lib.oracle_run_nodes.restype = ctypes.c_int
             lib.oracle_apply_dirichlet_2d.argtypes = [ctypes.c_int] * 3 + [_ip, _dp, _dp]
             lib.oracle_apply_dirichlet_2d.restype = None
             lib.oracle_axis_solve_2d.argtypes = ([ctypes.c_int] * 4 + [ctypes.c_double] * 2
@@ -176,6 +180,21 @@ def run(p, rho0=None, n_steps=None, n_threads: int = 0):
     rho = _f64(p.rho0 if rho0 is None else rho0).copy()
     steps = int(p.steps if n_steps is None else n_steps)
     args, keep = _common(p)
+    nodes = getattr(p, "nodes", None)
+    if nodes is not None and len(nodes[0]) > 0:
+        if getattr(p, "dims", 3) == 2:
+            raise ValueError("Dirichlet nodes are defined for the 3-D step")
+        vox = np.ascontiguousarray(nodes[0], dtype=np.int64)
+        sub = np.ascontiguousarray(nodes[1], dtype=np.int32)
+        val = _f64(nodes[2])
+        rc = lib.oracle_run_nodes(*args, ctypes.c_int64(len(vox)),
+                                  vox.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                  sub.ctypes.data_as(_ip), _d(val), steps,
+                                  int(n_threads or max_threads()), _d(rho))
+        if rc != 0:
+            raise ValueError(f"oracle_run_nodes failed ({rc})")
+        del keep
+        return rho
     fn = lib.oracle_run_2d if getattr(p, "dims", 3) == 2 else lib.oracle_run
     rc = fn(*args, steps, int(n_threads or max_threads()), _d(rho))
     if rc != 0:

