@@ -125,6 +125,27 @@ bfvm_status bfvm_set_cells(bfvm_ctx* ctx, int64_t n_cells, const double* pos,
                            const double* vol, const double* S, const double* U,
                            const double* rho_star, int32_t on_device);
 
+/*
+ * Dirichlet nodes inside the domain, e.g. vessels that hold a substrate at a
+ * fixed level (an extension: the paper's models place such sources in the
+ * tissue).  Node i holds substrate substrate[i] of voxel voxel[i]
+ * (x + nx (y + ny z)) at value[i]: like the Dirichlet shell, the nodes are
+ * set before the x-solve and after every solve (after the shell), so they
+ * take part in each line solve and are overwritten after it; the cell
+ * sources follow as usual.  Of two nodes on one voxel and substrate the
+ * later one holds.  n_nodes = 0 removes all nodes.
+ *   voxel[n]      int64, 0 <= voxel < nx ny nz
+ *   substrate[n]  int32, 0 <= substrate < n_sub
+ *   value[n]      FP64, finite
+ * Arrays follow on_device like the other setters and are copied.  3-D
+ * contexts only (BFVM_EINVAL for the 2-D variant); a context with nodes
+ * runs its sweeps as one launch per axis and cannot record for the adjoint
+ * or join a batch (BFVM_ESTATE).  Resets any recorded forward run.
+ */
+bfvm_status bfvm_set_dirichlet_nodes(bfvm_ctx* ctx, int64_t n_nodes, const int64_t* voxel,
+                                     const int32_t* substrate, const double* value,
+                                     int32_t on_device);
+
 /* Advance n_steps >= 0 full steps (prologue, x, y, z, sources) on the
  * context's stream.  Asynchronous: errors of the kernels themselves surface
  * at the next synchronising call (bfvm_sync, bfvm_get_density with a host

@@ -40,7 +40,7 @@ EXPORTED = ["bfvm_create", "bfvm_destroy", "bfvm_set_density", "bfvm_get_density
             "bfvm_kernel_times",
             "bfvm_batch_create", "bfvm_batch_step", "bfvm_batch_sync", "bfvm_batch_destroy",
             "bfvm_batch_last_error", "bfvm_batch_info", "bfvm_batch_shape",
-            "bfvm_batch_set_shape", "bfvm_apply_sources_noalloc"]
+            "bfvm_batch_set_shape", "bfvm_apply_sources_noalloc", "bfvm_set_dirichlet_nodes"]
 
 
 class BfvmError(RuntimeError):
@@ -77,6 +77,8 @@ def load_library(path: Optional[str] = None):
         lib.bfvm_set_density.argtypes = [_vp, _vp, _i32]
         lib.bfvm_get_density.argtypes = [_vp, _vp, _i32]
         lib.bfvm_set_cells.argtypes = [_vp, _i64, _vp, _vp, _vp, _vp, _vp, _i32]
+        lib.bfvm_set_dirichlet_nodes.argtypes = [_vp, _i64, _vp, _vp, _vp, _i32]
+        lib.bfvm_set_dirichlet_nodes.restype = ctypes.c_int
         lib.bfvm_step.argtypes = [_vp, _i32]
         lib.bfvm_sync.argtypes = [_vp]
         lib.bfvm_record.argtypes = [_vp, _i32]
@@ -198,6 +200,32 @@ def bfvm_set_cells(h, pos, vol, S, U, rho_star):
     if len(devs) != 1:
         raise ValueError("cell arrays must all be on the host or all on the device")
     _check(load_library().bfvm_set_cells(h, n, *[p for p, _, _ in ps], devs.pop()), h)
+    del ps
+
+
+def bfvm_set_dirichlet_nodes(h, voxel, substrate, value):
+    """Dirichlet nodes (int64 voxel x + nx (y + ny z), int32 substrate, FP64
+    value), all on the host or all on the device; empty arrays remove them."""
+    n = 0 if voxel is None else int(np.shape(voxel)[0])
+    if n == 0:
+        _check(load_library().bfvm_set_dirichlet_nodes(h, 0, None, None, None, 0), h)
+        return
+    try:
+        import torch
+        if isinstance(voxel, torch.Tensor):
+            ps = [_ptr(voxel.to(torch.int64).contiguous()), _ptr(substrate.to(torch.int32).contiguous()),
+                  _ptr(value.to(torch.float64).contiguous())]
+        else:
+            raise TypeError
+    except (ImportError, TypeError):
+        ps = [_ptr(np.ascontiguousarray(voxel, dtype=np.int64)),
+              _ptr(np.ascontiguousarray(substrate, dtype=np.int32)),
+              _ptr(np.ascontiguousarray(value, dtype=np.float64))]
+    devs = {d for _, d, _ in ps}
+    if len(devs) != 1:
+        raise ValueError("node arrays must all be on the host or all on the device")
+    _check(load_library().bfvm_set_dirichlet_nodes(h, n, ps[0][0], ps[1][0], ps[2][0],
+                                                   devs.pop()), h)
     del ps
 
 
@@ -379,6 +407,8 @@ class Sim:
         s = cls(p.nx, p.ny, p.nz, p.dx, p.dt, p.D, p.lam, p.bc_kind, p.bc_value, prec, stream)
         if getattr(p, "dims", 3) == 2:
             s.set_option(OPT_DIMS, 2)
+        if getattr(p, "nodes", None) is not None and len(p.nodes[0]) > 0:
+            bfvm_set_dirichlet_nodes(s.handle, *p.nodes)
         s.set_density(torch.as_tensor(p.rho0, dtype=s.dtype, device=s.device))
         if p.n_cells:
             arrs = [p.pos, p.vol, p.S, p.U, p.rho_star]

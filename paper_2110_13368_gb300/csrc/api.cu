@@ -7,6 +7,8 @@
 #include <algorithm>
 #include <string>
 
+#include <unordered_map>
+
 #include "internal.cuh"
 
 namespace bfvm {
@@ -270,6 +272,7 @@ void bfvm_destroy(bfvm_ctx* h)
     for (cudaEvent_t e : c->ev_stop) cudaEventDestroy(e);
     free_sources(c);
     free_coefficients(c);
+    c->free_nodes();
     c->free_line_tables();
     if (c->field) cudaFree(c->field);
     if (c->d_bc_kind) cudaFree(c->d_bc_kind);
@@ -420,6 +423,8 @@ bfvm_status bfvm_record(bfvm_ctx* h, int32_t checkpoint_every)
         return set_err(c, BFVM_EINVAL, "the adjoint needs an FP64 context");
     if (checkpoint_every > 0 && c->dims != 3)
         return set_err(c, BFVM_ESTATE, "the adjoint covers the 3-D step only");
+    if (checkpoint_every > 0 && c->n_nodes > 0)
+        return set_err(c, BFVM_ESTATE, "the adjoint does not cover Dirichlet nodes");
     drop_recording(c);
     c->record_every = checkpoint_every;
     return BFVM_OK;
@@ -494,6 +499,77 @@ bfvm_status bfvm_kernel_times(bfvm_ctx* h, double* ms, int64_t* counts, int32_t 
             c->kt_n[k] = 0;
         }
     }
+    return BFVM_OK;
+}
+
+bfvm_status bfvm_set_dirichlet_nodes(bfvm_ctx* h, int64_t n_nodes, const int64_t* voxel,
+                                     const int32_t* substrate, const double* value,
+                                     int32_t on_device)
+{
+    if (!h) return BFVM_EINVAL;
+    Ctx* c = &h->impl;
+    if (n_nodes < 0) return set_err(c, BFVM_EINVAL, "n_nodes must be >= 0");
+    if (n_nodes > 0 && (!voxel || !substrate || !value)) return set_err(c, BFVM_EINVAL, "NULL node array");
+    if (n_nodes > 0 && c->dims != 3)
+        return set_err(c, BFVM_EINVAL, "Dirichlet nodes are defined for the 3-D step");
+    if (n_nodes > 0 && c->record_every != 0)
+        return set_err(c, BFVM_ESTATE, "the adjoint does not cover Dirichlet nodes");
+    std::vector<int64_t> hv(n_nodes);
+    std::vector<int32_t> hs(n_nodes);
+    std::vector<double> hval(n_nodes);
+    if (n_nodes > 0) {
+        cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost;
+        if (on_device) BFVM_CUDA(c, cudaStreamSynchronize(c->stream));
+        BFVM_CUDA(c, cudaMemcpy(hv.data(), voxel, sizeof(int64_t) * n_nodes, k));
+        BFVM_CUDA(c, cudaMemcpy(hs.data(), substrate, sizeof(int32_t) * n_nodes, k));
+        BFVM_CUDA(c, cudaMemcpy(hval.data(), value, sizeof(double) * n_nodes, k));
+    }
+    const int64_t n_vox = (int64_t)c->nx * c->ny * c->nz;
+    for (int64_t i = 0; i < n_nodes; ++i) {
+        if (hv[i] < 0 || hv[i] >= n_vox) return set_err(c, BFVM_EINVAL, "node voxel out of range");
+        if (hs[i] < 0 || hs[i] >= c->n_sub) return set_err(c, BFVM_EINVAL, "node substrate out of range");
+        if (!isfinite(hval[i])) return set_err(c, BFVM_EINVAL, "node value must be finite");
+    }
+    // one node per (voxel, substrate): the later one holds
+    std::vector<int64_t> key_order;
+    std::unordered_map<int64_t, size_t> slot;
+    std::vector<int64_t> off;
+    std::vector<int32_t> vox32, sub32;
+    std::vector<double> val;
+    for (int64_t i = 0; i < n_nodes; ++i) {
+        const int64_t key = (int64_t)hs[i] * n_vox + hv[i];
+        auto it = slot.find(key);
+        if (it != slot.end()) {
+            val[it->second] = hval[i];
+            continue;
+        }
+        slot.emplace(key, val.size());
+        const int64_t v = hv[i];
+        const int x = (int)(v % c->nx), y = (int)((v / c->nx) % c->ny), z = (int)(v / ((int64_t)c->nx * c->ny));
+        off.push_back((((int64_t)hs[i] * c->nz + z) * c->ny + y) * c->pitch + x);
+        vox32.push_back((int32_t)v);
+        sub32.push_back(hs[i]);
+        val.push_back(hval[i]);
+    }
+    drop_recording(c);
+    drop_graphs(c);
+    BFVM_CUDA(c, cudaStreamSynchronize(c->stream));
+    c->free_nodes();
+    const int64_t m = (int64_t)val.size();
+    if (m == 0) return BFVM_OK;
+    cudaError_t e;
+    if ((e = cudaMalloc(&c->d_node_off, sizeof(int64_t) * m)) != cudaSuccess ||
+        (e = cudaMalloc(&c->d_node_vox, sizeof(int32_t) * m)) != cudaSuccess ||
+        (e = cudaMalloc(&c->d_node_sub, sizeof(int32_t) * m)) != cudaSuccess ||
+        (e = cudaMalloc(&c->d_node_val, sizeof(double) * m)) != cudaSuccess) {
+        c->free_nodes();
+        return cuda_err(c, e, "node tables");
+    }
+    BFVM_CUDA(c, cudaMemcpy(c->d_node_off, off.data(), sizeof(int64_t) * m, cudaMemcpyHostToDevice));
+    BFVM_CUDA(c, cudaMemcpy(c->d_node_vox, vox32.data(), sizeof(int32_t) * m, cudaMemcpyHostToDevice));
+    BFVM_CUDA(c, cudaMemcpy(c->d_node_sub, sub32.data(), sizeof(int32_t) * m, cudaMemcpyHostToDevice));
+    BFVM_CUDA(c, cudaMemcpy(c->d_node_val, val.data(), sizeof(double) * m, cudaMemcpyHostToDevice));
+    c->n_nodes = m;
     return BFVM_OK;
 }
 
@@ -575,6 +651,8 @@ bfvm_status bfvm_set_option(bfvm_ctx* h, int32_t key, int64_t value)
             if (value != 2 && value != 3) return set_err(c, BFVM_EINVAL, "dims must be 2 or 3");
             if (value == c->dims) return BFVM_OK;
             if (value == 2 && c->nz != 1) return set_err(c, BFVM_EINVAL, "the 2-D variant needs nz == 1");
+            if (value == 2 && c->n_nodes > 0)
+                return set_err(c, BFVM_ESTATE, "Dirichlet nodes are defined for the 3-D step");
             if (c->scale_state != 0) return set_err(c, BFVM_ESTATE, "field is mid-rescale; step to a period end first");
             if (c->record_every != 0) return set_err(c, BFVM_ESTATE, "the adjoint covers the 3-D step only");
             c->dims = (int)value;

@@ -91,6 +91,24 @@ struct Ctx {
     int fused_step = 1;           // FP64 rescaled pairs: 1 one launch for x, y, z
     int dims = 3;                 // 2: the 2-D variant (nz == 1; x and y sweeps,
                                   // lambda dt / 2 each, four-edge Dirichlet shell)
+    // Dirichlet nodes inside the domain (bfvm_set_dirichlet_nodes): one per
+    // (voxel, substrate), the caller's later node kept where two coincide
+    int64_t n_nodes = 0;
+    int64_t* d_node_off = nullptr;   // pitched field offset
+    int32_t* d_node_vox = nullptr;   // x + nx (y + ny z)
+    int32_t* d_node_sub = nullptr;
+    double* d_node_val = nullptr;
+    void free_nodes()
+    {
+        if (d_node_off) cudaFree(d_node_off);
+        if (d_node_vox) cudaFree(d_node_vox);
+        if (d_node_sub) cudaFree(d_node_sub);
+        if (d_node_val) cudaFree(d_node_val);
+        d_node_off = nullptr;
+        d_node_vox = d_node_sub = nullptr;
+        d_node_val = nullptr;
+        n_nodes = 0;
+    }
     int wait_test_polls = 0;      // > 0: the step's dependency waits cannot end and
                                   // give up after this many polls (tests only)
     int scale_state = 0;          // rescale state p of the stored field

@@ -476,7 +476,7 @@ bfvm_status launch_step_fused(Ctx* c, int p, bool renorm)
     // also runs the step's Dirichlet shell and cell sources (its epilogue)
     constexpr int G = persistent::Groups<double>::G;
     if (!c->fused_step || c->sweep_kernel != 0 || !c->d_task_first || !c->d_sched ||
-        c->n_sub > 64 || c->dims != 3)
+        c->n_sub > 64 || c->dims != 3 || c->n_nodes > 0)
         return BFVM_ESTATE;
     for (int a = 0; a < 3; ++a)
         if (!c->line_tables_ready[a]) return BFVM_ESTATE;
@@ -557,14 +557,70 @@ bfvm_status launch_step_fused(Ctx* c, int p, bool renorm)
     return BFVM_OK;
 }
 
+// Dirichlet nodes inside the domain: field <- value at each node, times the
+// scales the field carries at that point of a rescaled step (the axes
+// already swept in state p + 1, the others in state p; plain values after a
+// renormalising z sweep and in the plain forms).
+template <typename T>
+__global__ void k_nodes(T* __restrict__ field, int64_t n, const int64_t* __restrict__ off,
+                        const int32_t* __restrict__ vox, const int32_t* __restrict__ sub,
+                        const double* __restrict__ val, int nx, int ny, int64_t L,
+                        const double* __restrict__ sx, const double* __restrict__ sy,
+                        const double* __restrict__ sz)
+{
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    double v = val[e];
+    if (sx) {
+        const int32_t vv = vox[e];
+        const int x = vv % nx, y = (vv / nx) % ny, z = vv / (nx * ny);
+        const int64_t row = (int64_t)sub[e] * L;
+        v = v * (sx[row + x] * sy[row + nx + y] * sz[row + nx + ny + z]);
+    }
+    field[off[e]] = (T)v;
+}
+
+// stage 0: before the x sweep, 1: after x, 2: after y, 3: after z and the
+// Dirichlet shell
+bfvm_status launch_nodes(Ctx* c, int p, bool renorm, int stage)
+{
+    if (c->n_nodes == 0) return BFVM_OK;
+    const double *sx = nullptr, *sy = nullptr, *sz = nullptr;
+    if (c->precision == 64 && c->variant == 1 && !(renorm && stage == 3)) {
+        const int64_t per = (int64_t)c->n_sub * c->coef.L;
+        const double* s0 = c->coef.sc + (int64_t)p * per;
+        const double* s1 = c->coef.sc + (int64_t)(p + 1) * per;
+        sx = stage >= 1 ? s1 : s0;
+        sy = stage >= 2 ? s1 : s0;
+        sz = stage >= 3 ? s1 : s0;
+    }
+    KernelTimer timer(c, 3);
+    const unsigned grid = (unsigned)ceil_div(c->n_nodes, 256);
+    if (c->precision == 64)
+        k_nodes<double><<<grid, 256, 0, c->stream>>>(
+            reinterpret_cast<double*>(c->field), c->n_nodes, c->d_node_off, c->d_node_vox,
+            c->d_node_sub, c->d_node_val, c->nx, c->ny, c->coef.L, sx, sy, sz);
+    else
+        k_nodes<float><<<grid, 256, 0, c->stream>>>(
+            reinterpret_cast<float*>(c->field), c->n_nodes, c->d_node_off, c->d_node_vox,
+            c->d_node_sub, c->d_node_val, c->nx, c->ny, c->coef.L, nullptr, nullptr, nullptr);
+    c->launches += 1;
+    BFVM_CUDA(c, cudaGetLastError());
+    return BFVM_OK;
+}
+
 template <typename T, int MODE_Z>
 bfvm_status launch_xyz(Ctx* c, int p, const T* r, const T* cr, const T* cv)
 {
     constexpr int M = MODE_Z == 0 ? 0 : 1;
+    constexpr bool RN = MODE_Z == 2;
     bfvm_status st;
+    if ((st = launch_nodes(c, p, RN, 0)) != BFVM_OK) return st;
     if ((st = launch_axis<T, 0, M>(c, make_args<T>(c, 0, p, r, cr, cv))) != BFVM_OK) return st;
+    if ((st = launch_nodes(c, p, RN, 1)) != BFVM_OK) return st;
     if ((st = launch_axis<T, 1, M>(c, make_args<T>(c, 1, p, r, cr, cv))) != BFVM_OK) return st;
     if (c->dims == 2) return BFVM_OK;   // 2-D variant: x and y sweeps only
+    if ((st = launch_nodes(c, p, RN, 2)) != BFVM_OK) return st;
     return launch_axis<T, 2, MODE_Z>(c, make_args<T>(c, 2, p, r, cr, cv));
 }
 
@@ -709,12 +765,14 @@ bfvm_status launch_step(Ctx* c, int p, bool renorm)
         st = launch_xyz<float, 0>(c, 0, c->coef.r32, c->coef.cr32, c->coef.c32);
         if (st != BFVM_OK) return st;
         if ((st = launch_shell_fill(c, -1)) != BFVM_OK) return st;
+        if ((st = launch_nodes(c, 0, true, 3)) != BFVM_OK) return st;
         return launch_sources(c, 0, true);
     }
     if (c->variant == 0) {
         st = launch_xyz<double, 0>(c, 0, c->coef.r, c->coef.cr, c->coef.c);
         if (st != BFVM_OK) return st;
         if ((st = launch_shell_fill(c, -1)) != BFVM_OK) return st;
+        if ((st = launch_nodes(c, 0, true, 3)) != BFVM_OK) return st;
         return launch_sources(c, 0, true);
     }
     st = launch_step_fused(c, p, renorm);
@@ -725,6 +783,7 @@ bfvm_status launch_step(Ctx* c, int p, bool renorm)
     }
     if (st != BFVM_OK) return st;
     if ((st = launch_shell_fill(c, renorm ? -1 : p + 1)) != BFVM_OK) return st;
+    if ((st = launch_nodes(c, p, renorm, 3)) != BFVM_OK) return st;
     return launch_sources(c, p + 1, renorm);
 }
 

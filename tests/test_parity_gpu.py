@@ -352,3 +352,69 @@ def test_2d_variant_option_rules(bf):
     sim.close()
     ref = oracle.run(p.with_(dims=3))
     assert np.all(rel_inf(got, ref) <= TOL64)
+
+
+# ---------------------------------------------------- Dirichlet nodes
+def _with_nodes(p, extra_dup=True):
+    n_vox = p.nx * p.ny * p.nz
+    vox, sub, val = inputs.vessel_nodes(p.nx, p.ny, p.nz, substrate=0, value=45.0)
+    vox = list(vox) + [0, n_vox // 3]
+    sub = list(sub) + [1, 1]
+    val = list(val) + [2.0, 7.0]
+    if extra_dup:                       # a repeat on one voxel: the later value holds
+        vox.append(n_vox // 3)
+        sub.append(1)
+        val.append(11.0)
+    return p.with_(nodes=(np.array(vox, dtype=np.int64), np.array(sub, dtype=np.int32),
+                          np.array(val)))
+
+
+NODE_CASES = {
+    "ragged_37x45x50": lambda: _with_nodes(mixed(37, 45, 50)),
+    "cube_33": lambda: _with_nodes(mixed(33, 33, 33, n_cells=300, steps=9)),
+    "thin_1x1x7": lambda: _with_nodes(mixed(1, 1, 7, n_cells=3)),
+    "long_z_260": lambda: _with_nodes(mixed(9, 7, 260, n_cells=50, steps=3)),
+}
+
+
+@pytest.mark.parametrize("precision,variant,period,tol",
+                         [(64, 1, 0, TOL64), (64, 1, 3, TOL64), (64, 0, 0, TOL64),
+                          (32, None, 0, TOL32)])
+@pytest.mark.parametrize("case", sorted(NODE_CASES))
+def test_dirichlet_nodes_match_oracle(bf, case, precision, variant, period, tol):
+    """Dirichlet nodes (a vessel column, a node on the shell, a repeated
+    node) in the rescaled form across rescale periods, the plain form and
+    FP32, against the oracle."""
+    p = NODE_CASES[case]()
+    ref = oracle.run(p)
+    sim = bf.Sim.from_problem(p, precision=precision)
+    if variant is not None:
+        sim.set_option(bf.OPT_VARIANT, variant)
+    if period:
+        sim.set_option(bf.OPT_PERIOD, period)
+    sim.step(p.steps)
+    got = sim.get_density().double().cpu().numpy()
+    sim.close()
+    err = rel_inf(got, ref)
+    assert np.all(err <= tol), (case, precision, variant, err)
+
+
+def test_dirichlet_node_rules(bf):
+    p = mixed(10, 9, 8)
+    sim = bf.Sim.from_problem(p)
+    with pytest.raises(bf.BfvmError) as ei:
+        bf.bfvm_set_dirichlet_nodes(sim.handle, [10 * 9 * 8], [0], [1.0])    # voxel out of range
+    assert ei.value.status == 1
+    with pytest.raises(bf.BfvmError):
+        bf.bfvm_set_dirichlet_nodes(sim.handle, [3], [2], [1.0])             # substrate out of range
+    with pytest.raises(bf.BfvmError):
+        bf.bfvm_set_dirichlet_nodes(sim.handle, [3], [0], [float("nan")])
+    bf.bfvm_set_dirichlet_nodes(sim.handle, [3], [0], [1.0])
+    with pytest.raises(bf.BfvmError) as ei:
+        sim.record(2)
+    assert ei.value.status == 4
+    with pytest.raises(bf.BfvmError):
+        bf.Batch([sim])
+    bf.bfvm_set_dirichlet_nodes(sim.handle, [], [], [])                      # removed again
+    sim.record(2)
+    sim.close()
