@@ -146,6 +146,27 @@ bfvm_status bfvm_set_dirichlet_nodes(bfvm_ctx* ctx, int64_t n_nodes, const int64
                                      const int32_t* substrate, const double* value,
                                      int32_t on_device);
 
+/*
+ * Move, resize or re-rate the cells of the last bfvm_set_cells without a
+ * host round trip (an extension: the paper's agents move and grow on a
+ * slower mechanics cadence than the diffusion steps, and names the host-side
+ * cell handling its next bottleneck).  Same arrays and layout as
+ * bfvm_set_cells, all DEVICE pointers, and n_cells must equal the count of
+ * the last bfvm_set_cells (BFVM_EINVAL otherwise; BFVM_ESTATE if there were
+ * no cells or a forward run is being recorded).
+ * The cells are re-binned, re-sorted and their maps recomposed on the
+ * context's stream, in tables sized by bfvm_set_cells: the call allocates
+ * nothing, reads nothing back and returns at once.  The cells are checked
+ * on the device: invalid ones (positions outside [0, n_a*dx], non-positive
+ * volumes, negative or non-finite rates) make the next synchronising call
+ * (bfvm_sync, bfvm_get_density to a host buffer) return BFVM_EINVAL, and
+ * the field is then not valid; positions outside the domain are binned to
+ * the nearest voxel meanwhile.
+ */
+bfvm_status bfvm_update_cells(bfvm_ctx* ctx, int64_t n_cells, const double* pos,
+                              const double* vol, const double* S, const double* U,
+                              const double* rho_star);
+
 /* Advance n_steps >= 0 full steps (prologue, x, y, z, sources) on the
  * context's stream.  Asynchronous: errors of the kernels themselves surface
  * at the next synchronising call (bfvm_sync, bfvm_get_density with a host

@@ -40,7 +40,8 @@ EXPORTED = ["bfvm_create", "bfvm_destroy", "bfvm_set_density", "bfvm_get_density
             "bfvm_kernel_times",
             "bfvm_batch_create", "bfvm_batch_step", "bfvm_batch_sync", "bfvm_batch_destroy",
             "bfvm_batch_last_error", "bfvm_batch_info", "bfvm_batch_shape",
-            "bfvm_batch_set_shape", "bfvm_apply_sources_noalloc", "bfvm_set_dirichlet_nodes"]
+            "bfvm_batch_set_shape", "bfvm_apply_sources_noalloc", "bfvm_set_dirichlet_nodes",
+            "bfvm_update_cells"]
 
 
 class BfvmError(RuntimeError):
@@ -77,6 +78,8 @@ def load_library(path: Optional[str] = None):
         lib.bfvm_set_density.argtypes = [_vp, _vp, _i32]
         lib.bfvm_get_density.argtypes = [_vp, _vp, _i32]
         lib.bfvm_set_cells.argtypes = [_vp, _i64, _vp, _vp, _vp, _vp, _vp, _i32]
+        lib.bfvm_update_cells.argtypes = [_vp, _i64, _vp, _vp, _vp, _vp, _vp]
+        lib.bfvm_update_cells.restype = ctypes.c_int
         lib.bfvm_set_dirichlet_nodes.argtypes = [_vp, _i64, _vp, _vp, _vp, _i32]
         lib.bfvm_set_dirichlet_nodes.restype = ctypes.c_int
         lib.bfvm_step.argtypes = [_vp, _i32]
@@ -200,6 +203,17 @@ def bfvm_set_cells(h, pos, vol, S, U, rho_star):
     if len(devs) != 1:
         raise ValueError("cell arrays must all be on the host or all on the device")
     _check(load_library().bfvm_set_cells(h, n, *[p for p, _, _ in ps], devs.pop()), h)
+    del ps
+
+
+def bfvm_update_cells(h, pos, vol, S, U, rho_star):
+    """Re-bin the cells of the last bfvm_set_cells from new device arrays
+    (same count), on the stream, without allocating or synchronising."""
+    ps = [_ptr(a) for a in (pos, vol, S, U, rho_star)]
+    if any(d != 1 for _, d, _ in ps):
+        raise ValueError("bfvm_update_cells takes device tensors only")
+    n = int(pos.shape[0])
+    _check(load_library().bfvm_update_cells(h, n, *[p for p, _, _ in ps]), h)
     del ps
 
 
@@ -431,6 +445,9 @@ class Sim:
     def set_cells(self, pos, vol, S, U, rho_star):
         bfvm_set_cells(self.handle, pos, vol, S, U, rho_star)
         self.n_cells = 0 if pos is None else int(pos.shape[0])
+
+    def update_cells(self, pos, vol, S, U, rho_star):
+        bfvm_update_cells(self.handle, pos, vol, S, U, rho_star)
 
     def step(self, n=1):
         bfvm_step(self.handle, n)

@@ -29,15 +29,19 @@ bfvm_status cuda_err(Ctx* c, cudaError_t e, const char* what)
     return set_err(c, e == cudaErrorMemoryAllocation ? BFVM_ENOMEM : BFVM_ECUDA, m);
 }
 
-// Flag 1 of d_err: a bounded device wait of the one-launch step gave up.
-// Read (and cleared) after the stream is idle.
+// Device flags, read (and cleared) after the stream is idle: d_err[1] a
+// bounded device wait of the one-launch step gave up; d_err[2] a cell
+// update (bfvm_update_cells) had invalid cells.
 bfvm_status check_wait_flag(Ctx* c)
 {
     if (!c->d_err) return BFVM_OK;
-    int flag = 0;
-    BFVM_CUDA(c, cudaMemcpy(&flag, c->d_err + 1, sizeof(int), cudaMemcpyDeviceToHost));
-    if (!flag) return BFVM_OK;
-    BFVM_CUDA(c, cudaMemset(c->d_err + 1, 0, sizeof(int)));
+    int flag[2] = {0, 0};
+    BFVM_CUDA(c, cudaMemcpy(flag, c->d_err + 1, sizeof(flag), cudaMemcpyDeviceToHost));
+    if (!flag[0] && !flag[1]) return BFVM_OK;
+    BFVM_CUDA(c, cudaMemset(c->d_err + 1, 0, sizeof(flag)));
+    if (flag[1])
+        return set_err(c, BFVM_EINVAL, "a cell update had invalid cells (positions outside the "
+                                       "domain were binned to the nearest voxel); field not valid");
     return set_err(c, BFVM_ETIMEOUT, "a device wait of the step kernel gave up (result not valid)");
 }
 
@@ -425,6 +429,10 @@ bfvm_status bfvm_record(bfvm_ctx* h, int32_t checkpoint_every)
         return set_err(c, BFVM_ESTATE, "the adjoint covers the 3-D step only");
     if (checkpoint_every > 0 && c->n_nodes > 0)
         return set_err(c, BFVM_ESTATE, "the adjoint does not cover Dirichlet nodes");
+    if (checkpoint_every > 0) {
+        bfvm_status st = sync_source_counts(c);
+        if (st != BFVM_OK) return st;
+    }
     drop_recording(c);
     c->record_every = checkpoint_every;
     return BFVM_OK;
@@ -500,6 +508,23 @@ bfvm_status bfvm_kernel_times(bfvm_ctx* h, double* ms, int64_t* counts, int32_t 
         }
     }
     return BFVM_OK;
+}
+
+bfvm_status bfvm_update_cells(bfvm_ctx* h, int64_t n_cells, const double* pos,
+                              const double* vol, const double* S, const double* U,
+                              const double* rho_star)
+{
+    if (!h) return BFVM_EINVAL;
+    Ctx* c = &h->impl;
+    if (c->src.cap == 0) return set_err(c, BFVM_ESTATE, "no cells to update (bfvm_set_cells first)");
+    if (n_cells != c->src.cap)
+        return set_err(c, BFVM_EINVAL, "bfvm_update_cells keeps the cell count of the last bfvm_set_cells");
+    if (!pos || !vol || !S || !U || !rho_star) return set_err(c, BFVM_EINVAL, "NULL cell array");
+    if (c->record_every != 0)
+        return set_err(c, BFVM_ESTATE, "cells cannot move while a forward run is recorded for the adjoint");
+    // graphs captured with host-side entry counts would keep stale grids
+    if (c->src.counts_on_host) drop_graphs(c);
+    return update_sources(c, pos, vol, S, U, rho_star);
 }
 
 bfvm_status bfvm_set_dirichlet_nodes(bfvm_ctx* h, int64_t n_nodes, const int64_t* voxel,
@@ -581,6 +606,7 @@ bfvm_status bfvm_get_info(const bfvm_ctx* h, int64_t* info)
     info[0] = c->precision;
     info[1] = c->nx; info[2] = c->ny; info[3] = c->nz; info[4] = c->n_sub;
     info[5] = c->pitch;
+    sync_source_counts(const_cast<Ctx*>(c));
     info[6] = c->src.n_seg;
     info[7] = c->steps_taken;
     info[8] = (c->precision == 64) ? c->variant : 0;

@@ -90,6 +90,10 @@ bfvm_status bfvm_batch_create(bfvm_batch** out, bfvm_ctx* const* members, int32_
             return BFVM_EINVAL;
         }
         Ctx* c = &members[i]->impl;
+        if (sync_source_counts(c) != BFVM_OK) {
+            delete h;
+            return BFVM_ECUDA;
+        }
         if (i == 0) b->precision = c->precision;
         if (c->precision != b->precision || c->scale_state != 0 || c->record_every != 0 ||
             c->dims != 3 || c->n_nodes > 0) {

@@ -60,6 +60,20 @@ struct SourceTable {
     double* cw = nullptr;       // [n_cells] w = dt V / V_vox
     double* crs = nullptr;      // [n_cells][n_sub] rho*
     int64_t* seg_of_entry = nullptr;  // [n_entries] segment of each entry
+    // Tables are sized for `cap` cells (at most cap occupied voxels), so a
+    // cell update of the same count (bfvm_update_cells) re-bins in place,
+    // on the stream, without allocating or reading anything back:
+    // d_count = [n_seg, n_entries] on the device; after such an update the
+    // host copies n_seg / n_entries are stale (counts_on_host false) until
+    // sync_source_counts() reads them.
+    int64_t cap = 0;
+    int64_t* d_count = nullptr;
+    bool counts_on_host = true;
+    int64_t n_pad = 0;
+    uint64_t* keys = nullptr;   // [n_pad] sort keys
+    int64_t* heads = nullptr;   // [cap] segment head flags
+    int64_t* seg_id = nullptr;  // [cap] exclusive scan of the flags
+    int64_t* scan_ws = nullptr; // block sums of the scan
 };
 
 struct Ctx {
@@ -237,6 +251,9 @@ bfvm_status build_sources(Ctx* c, int64_t n_cells, const double* pos,
                           const double* rho_star);
 void free_sources(Ctx* c);
 bfvm_status launch_sources(Ctx* c, int p_next, bool renormed);
+bfvm_status update_sources(Ctx* c, const double* pos, const double* vol, const double* S,
+                           const double* U, const double* rho_star);
+bfvm_status sync_source_counts(Ctx* c);
 
 // adjoint (adjoint.cu)
 bfvm_status run_backward(Ctx* c, const double* g_final_dev, double* dD_dev,

@@ -183,7 +183,7 @@ __global__ void k_cell_terms(int64_t n, int n_sub, double dt, double vvox,
     }
 }
 
-__global__ void k_compose(int64_t n_seg, int n_sub, int nx, int ny, int nz,
+__global__ void k_compose(const int64_t* count, int n_sub, int nx, int ny, int nz,
                           int64_t pitch, const int64_t* seg_start,
                           const int64_t* seg_vox, const double* ca,
                           const double* cb, int64_t* off, double* alpha,
@@ -191,7 +191,7 @@ __global__ void k_compose(int64_t n_seg, int n_sub, int nx, int ny, int nz,
                           int64_t* seg_of_entry)
 {
     int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (e >= n_seg * n_sub) return;
+    if (e >= count[1]) return;
     int64_t g = e / n_sub;
     int s = (int)(e % n_sub);
     double al = 1.0, be = 0.0;
@@ -212,36 +212,44 @@ __global__ void k_compose(int64_t n_seg, int n_sub, int nx, int ny, int nz,
     seg_of_entry[e] = g;
 }
 
-bfvm_status scan_exclusive(Ctx* c, const int64_t* in, int64_t* out, int64_t n,
-                           int64_t* total_host)
+// Number of occupied voxels (segments) and entries, and the end of the last
+// segment, from the scanned head flags.
+__global__ void k_count(int64_t n, int n_sub, const int64_t* heads, const int64_t* seg_id,
+                        int64_t* seg_start, int64_t* count)
 {
-    int64_t nb = ceil_div(n, kScanBlock);
-    int64_t* sums = nullptr;
-    int64_t* sums_scan = nullptr;
-    BFVM_CUDA(c, cudaMalloc(&sums, sizeof(int64_t) * (nb + 1)));
-    BFVM_CUDA(c, cudaMalloc(&sums_scan, sizeof(int64_t) * (nb + 1)));
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    const int64_t ns = seg_id[n - 1] + heads[n - 1];
+    count[0] = ns;
+    count[1] = ns * n_sub;
+    seg_start[ns] = n;
+}
+
+// Exclusive scan with a preallocated workspace (block sums, recursively):
+// no allocation and no host read.
+void scan_ws(Ctx* c, const int64_t* in, int64_t* out, int64_t n, int64_t* ws)
+{
+    const int64_t nb = ceil_div(n, kScanBlock);
+    int64_t* sums = ws;
+    int64_t* sums_scan = ws + nb + 1;
     k_scan_block<<<(unsigned)nb, 256, 0, c->stream>>>(in, out, sums, n);
     c->launches += 1;
-    bfvm_status st = BFVM_OK;
     if (nb > 1) {
-        int64_t dummy = 0;
-        st = scan_exclusive(c, sums, sums_scan, nb, &dummy);
-        if (st == BFVM_OK) {
-            k_scan_add<<<(unsigned)ceil_div(n, 256), 256, 0, c->stream>>>(out, sums_scan, n);
-            c->launches += 1;
-        }
+        scan_ws(c, sums, sums_scan, nb, ws + 2 * (nb + 1));
+        k_scan_add<<<(unsigned)ceil_div(n, 256), 256, 0, c->stream>>>(out, sums_scan, n);
+        c->launches += 1;
     }
-    if (st == BFVM_OK && total_host) {
-        int64_t last_in = 0, last_out = 0;
-        cudaMemcpyAsync(&last_in, in + n - 1, sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream);
-        cudaMemcpyAsync(&last_out, out + n - 1, sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream);
-        cudaError_t e = cudaStreamSynchronize(c->stream);
-        if (e != cudaSuccess) st = cuda_err(c, e, "scan total");
-        *total_host = last_in + last_out;
+}
+
+int64_t scan_ws_size(int64_t n)
+{
+    int64_t total = 0;
+    while (true) {
+        const int64_t nb = ceil_div(n, kScanBlock);
+        total += 2 * (nb + 1);
+        if (nb <= 1) break;
+        n = nb;
     }
-    cudaFree(sums);
-    cudaFree(sums_scan);
-    return st;
+    return total;
 }
 
 bfvm_status sort_keys(Ctx* c, uint64_t* keys, int64_t n_pad)
@@ -269,11 +277,64 @@ void free_sources(Ctx* c)
 {
     SourceTable& S = c->src;
     void* ptrs[] = {S.off, S.alpha, S.beta, S.vox, S.sub, S.seg_start, S.seg_vox,
-                    S.cell_sorted, S.ca, S.cb, S.cw, S.crs, S.seg_of_entry};
+                    S.cell_sorted, S.ca, S.cb, S.cw, S.crs, S.seg_of_entry,
+                    S.d_count, S.keys, S.heads, S.seg_id, S.scan_ws};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     S = SourceTable();
 }
+
+namespace {
+
+// Bin, sort and compose the S.cap cells (device arrays) into the tables.
+// validate_sync: check the cells first and report EINVAL synchronously
+// (bfvm_set_cells); otherwise the check ORs its findings into the sticky
+// device flag d_err[2], read by the next synchronising call, and nothing
+// is read back (bfvm_update_cells).  Invalid positions are binned to the
+// clamped voxel either way.
+bfvm_status bin_cells(Ctx* c, const double* pos, const double* vol, const double* Sr,
+                      const double* Ur, const double* rs, bool validate_sync)
+{
+    SourceTable& S = c->src;
+    const int64_t n = S.cap;
+    const int n_sub = c->n_sub;
+    int* flag = validate_sync ? c->d_err : c->d_err + 2;
+    if (validate_sync) BFVM_CUDA(c, cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
+    k_validate_cells<<<(unsigned)ceil_div(n, 256), 256, 0, c->stream>>>(
+        n, n_sub, pos, vol, Sr, Ur, rs, c->nx * c->dx, c->ny * c->dx, c->nz * c->dx, flag);
+    c->launches += 1;
+    if (validate_sync) {
+        int f = 0;
+        BFVM_CUDA(c, cudaMemcpyAsync(&f, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+        BFVM_CUDA(c, cudaStreamSynchronize(c->stream));
+        if (f & 1) return set_err(c, BFVM_EINVAL, "cell position outside [0, n*dx] on some axis");
+        if (f & 2) return set_err(c, BFVM_EINVAL, "cell volume must be finite and > 0");
+        if (f & 4) return set_err(c, BFVM_EINVAL, "secretion/uptake rates must be finite and >= 0");
+        if (f & 8) return set_err(c, BFVM_EINVAL, "rho_star must be finite");
+    }
+    k_keys<<<(unsigned)ceil_div(S.n_pad, 256), 256, 0, c->stream>>>(
+        n, S.n_pad, pos, c->dx, c->nx, c->ny, c->nz, S.keys);
+    c->launches += 1;
+    bfvm_status st = sort_keys(c, S.keys, S.n_pad);
+    if (st != BFVM_OK) return st;
+    k_heads<<<(unsigned)ceil_div(n, 256), 256, 0, c->stream>>>(n, S.keys, S.heads);
+    c->launches += 1;
+    scan_ws(c, S.heads, S.seg_id, n, S.scan_ws);
+    k_count<<<1, 32, 0, c->stream>>>(n, n_sub, S.heads, S.seg_id, S.seg_start, S.d_count);
+    k_segments<<<(unsigned)ceil_div(n, 256), 256, 0, c->stream>>>(
+        n, S.keys, S.heads, S.seg_id, S.seg_start, S.seg_vox, S.cell_sorted);
+    k_cell_terms<<<(unsigned)ceil_div(n, 256), 256, 0, c->stream>>>(
+        n, n_sub, c->dt, c->dx * c->dx * c->dx, S.cell_sorted, vol, Sr, Ur, rs,
+        S.ca, S.cb, S.cw, S.crs);
+    k_compose<<<(unsigned)ceil_div(n * n_sub, 128), 128, 0, c->stream>>>(
+        S.d_count, n_sub, c->nx, c->ny, c->nz, c->pitch, S.seg_start, S.seg_vox, S.ca,
+        S.cb, S.off, S.alpha, S.beta, S.vox, S.sub, S.seg_of_entry);
+    c->launches += 4;
+    BFVM_CUDA(c, cudaGetLastError());
+    return BFVM_OK;
+}
+
+}  // namespace
 
 // pos, vol, S, U, rho_star are device pointers here.
 bfvm_status build_sources(Ctx* c, int64_t n, const double* pos, const double* vol,
@@ -284,69 +345,59 @@ bfvm_status build_sources(Ctx* c, int64_t n, const double* pos, const double* vo
     if (n > (int64_t)kIdxMask)
         return set_err(c, BFVM_EINVAL, "too many cells (limit 2^31 - 1)");
     const int n_sub = c->n_sub;
-    BFVM_CUDA(c, cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
-    k_validate_cells<<<(unsigned)ceil_div(n, 256), 256, 0, c->stream>>>(
-        n, n_sub, pos, vol, Sr, Ur, rs, c->nx * c->dx, c->ny * c->dx, c->nz * c->dx, c->d_err);
-    c->launches += 1;
-    int flag = 0;
-    BFVM_CUDA(c, cudaMemcpyAsync(&flag, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
-    BFVM_CUDA(c, cudaStreamSynchronize(c->stream));
-    if (flag & 1) return set_err(c, BFVM_EINVAL, "cell position outside [0, n*dx] on some axis");
-    if (flag & 2) return set_err(c, BFVM_EINVAL, "cell volume must be finite and > 0");
-    if (flag & 4) return set_err(c, BFVM_EINVAL, "secretion/uptake rates must be finite and >= 0");
-    if (flag & 8) return set_err(c, BFVM_EINVAL, "rho_star must be finite");
-
-    int64_t n_pad = kSortBlock;
-    while (n_pad < n) n_pad *= 2;
-    uint64_t* keys = nullptr;
-    int64_t *flags = nullptr, *seg_id = nullptr;
-    BFVM_CUDA(c, cudaMalloc(&keys, sizeof(uint64_t) * n_pad));
-    BFVM_CUDA(c, cudaMalloc(&flags, sizeof(int64_t) * n));
-    BFVM_CUDA(c, cudaMalloc(&seg_id, sizeof(int64_t) * n));
-    k_keys<<<(unsigned)ceil_div(n_pad, 256), 256, 0, c->stream>>>(
-        n, n_pad, pos, c->dx, c->nx, c->ny, c->nz, keys);
-    c->launches += 1;
-    bfvm_status st = sort_keys(c, keys, n_pad);
-    if (st != BFVM_OK) return st;
-    k_heads<<<(unsigned)ceil_div(n, 256), 256, 0, c->stream>>>(n, keys, flags);
-    c->launches += 1;
-    int64_t n_seg = 0;
-    st = scan_exclusive(c, flags, seg_id, n, &n_seg);
-    if (st != BFVM_OK) return st;
-
     SourceTable& S = c->src;
+    S.cap = n;
     S.n_cells = n;
-    S.n_seg = n_seg;
-    S.n_entries = n_seg * n_sub;
-    BFVM_CUDA(c, cudaMalloc(&S.seg_start, sizeof(int64_t) * (n_seg + 1)));
-    BFVM_CUDA(c, cudaMalloc(&S.seg_vox, sizeof(int64_t) * n_seg));
+    S.n_pad = kSortBlock;
+    while (S.n_pad < n) S.n_pad *= 2;
+    const int64_t ne = n * n_sub;   // at most one entry per cell and substrate
+    BFVM_CUDA(c, cudaMalloc(&S.keys, sizeof(uint64_t) * S.n_pad));
+    BFVM_CUDA(c, cudaMalloc(&S.heads, sizeof(int64_t) * n));
+    BFVM_CUDA(c, cudaMalloc(&S.seg_id, sizeof(int64_t) * n));
+    BFVM_CUDA(c, cudaMalloc(&S.scan_ws, sizeof(int64_t) * scan_ws_size(n)));
+    BFVM_CUDA(c, cudaMalloc(&S.d_count, sizeof(int64_t) * 2));
+    BFVM_CUDA(c, cudaMalloc(&S.seg_start, sizeof(int64_t) * (n + 1)));
+    BFVM_CUDA(c, cudaMalloc(&S.seg_vox, sizeof(int64_t) * n));
     BFVM_CUDA(c, cudaMalloc(&S.cell_sorted, sizeof(int64_t) * n));
     BFVM_CUDA(c, cudaMalloc(&S.ca, sizeof(double) * n * n_sub));
     BFVM_CUDA(c, cudaMalloc(&S.cb, sizeof(double) * n * n_sub));
     BFVM_CUDA(c, cudaMalloc(&S.crs, sizeof(double) * n * n_sub));
     BFVM_CUDA(c, cudaMalloc(&S.cw, sizeof(double) * n));
-    BFVM_CUDA(c, cudaMalloc(&S.off, sizeof(int64_t) * S.n_entries));
-    BFVM_CUDA(c, cudaMalloc(&S.alpha, sizeof(double) * S.n_entries));
-    BFVM_CUDA(c, cudaMalloc(&S.beta, sizeof(double) * S.n_entries));
-    BFVM_CUDA(c, cudaMalloc(&S.vox, sizeof(int32_t) * S.n_entries));
-    BFVM_CUDA(c, cudaMalloc(&S.sub, sizeof(int32_t) * S.n_entries));
-    BFVM_CUDA(c, cudaMalloc(&S.seg_of_entry, sizeof(int64_t) * S.n_entries));
-    BFVM_CUDA(c, cudaMemcpyAsync(S.seg_start + n_seg, &n, sizeof(int64_t),
-                                 cudaMemcpyHostToDevice, c->stream));
-    k_segments<<<(unsigned)ceil_div(n, 256), 256, 0, c->stream>>>(
-        n, keys, flags, seg_id, S.seg_start, S.seg_vox, S.cell_sorted);
-    k_cell_terms<<<(unsigned)ceil_div(n, 256), 256, 0, c->stream>>>(
-        n, n_sub, c->dt, c->dx * c->dx * c->dx, S.cell_sorted, vol, Sr, Ur, rs,
-        S.ca, S.cb, S.cw, S.crs);
-    k_compose<<<(unsigned)ceil_div(S.n_entries, 128), 128, 0, c->stream>>>(
-        n_seg, n_sub, c->nx, c->ny, c->nz, c->pitch, S.seg_start, S.seg_vox, S.ca,
-        S.cb, S.off, S.alpha, S.beta, S.vox, S.sub, S.seg_of_entry);
-    c->launches += 3;
-    BFVM_CUDA(c, cudaGetLastError());
+    BFVM_CUDA(c, cudaMalloc(&S.off, sizeof(int64_t) * ne));
+    BFVM_CUDA(c, cudaMalloc(&S.alpha, sizeof(double) * ne));
+    BFVM_CUDA(c, cudaMalloc(&S.beta, sizeof(double) * ne));
+    BFVM_CUDA(c, cudaMalloc(&S.vox, sizeof(int32_t) * ne));
+    BFVM_CUDA(c, cudaMalloc(&S.sub, sizeof(int32_t) * ne));
+    BFVM_CUDA(c, cudaMalloc(&S.seg_of_entry, sizeof(int64_t) * ne));
+    bfvm_status st = bin_cells(c, pos, vol, Sr, Ur, rs, true);
+    if (st != BFVM_OK) {
+        free_sources(c);
+        return st;
+    }
+    S.counts_on_host = false;
+    return sync_source_counts(c);
+}
+
+bfvm_status update_sources(Ctx* c, const double* pos, const double* vol, const double* S,
+                           const double* U, const double* rho_star)
+{
+    if (c->src.cap == 0) return set_err(c, BFVM_ESTATE, "no cells to update (bfvm_set_cells first)");
+    bfvm_status st = bin_cells(c, pos, vol, S, U, rho_star, false);
+    if (st != BFVM_OK) return st;
+    c->src.counts_on_host = false;
+    return BFVM_OK;
+}
+
+bfvm_status sync_source_counts(Ctx* c)
+{
+    SourceTable& S = c->src;
+    if (S.counts_on_host || S.cap == 0) return BFVM_OK;
+    int64_t cnt[2] = {0, 0};
+    BFVM_CUDA(c, cudaMemcpyAsync(cnt, S.d_count, sizeof(cnt), cudaMemcpyDeviceToHost, c->stream));
     BFVM_CUDA(c, cudaStreamSynchronize(c->stream));
-    cudaFree(keys);
-    cudaFree(flags);
-    cudaFree(seg_id);
+    S.n_seg = cnt[0];
+    S.n_entries = cnt[1];
+    S.counts_on_host = true;
     return BFVM_OK;
 }
 

@@ -79,6 +79,7 @@ struct EpiArgs {
     int64_t pitch, L;
     const double* sc;       // [s][L] scales of state p + 1, or null
     int64_t n_seg;          // occupied voxels; entry g * n_sub + s is voxel g, substrate s
+    const int64_t* d_nseg;  // or null; else the exact count, n_seg being an upper bound
     const int64_t* off;     // field offset of each (voxel, substrate) entry
     const double* alpha;
     const double* beta;
@@ -456,6 +457,7 @@ __device__ __forceinline__ void step_epilogue(const StepSched& Q, const EpiArgs&
     const int64_t per = shell_count(E);
     const int sh_chunks = (int)epi_shell_chunks(E.nx, E.ny, E.nz);
     const int src_chunks = (int)epi_src_chunks(E.n_seg);
+    const int64_t n_seg = E.d_nseg ? *E.d_nseg : E.n_seg;   // written before this launch
     unsigned long long got = 0ull;   // bit s: sweeps of s acquired; bit 32 + s: shell of s
     for (;;) {
         unsigned c = 0;
@@ -498,7 +500,7 @@ __device__ __forceinline__ void step_epilogue(const StepSched& Q, const EpiArgs&
             }
         }
         const int64_t lo = (int64_t)k * kEpiChunk;
-        const int64_t hi = min(E.n_seg, lo + kEpiChunk);
+        const int64_t hi = min(n_seg, lo + kEpiChunk);
         for (int64_t g0 = lo + lane; g0 < hi; g0 += 32 * kEpiUnroll) {
             // all reads of kEpiUnroll entries first (entries are distinct
             // voxel-substrate pairs, so no two touch one field element)

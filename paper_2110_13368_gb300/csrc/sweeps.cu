@@ -319,7 +319,7 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs<T> A)
 // In the rescaled form the field carries the scale X(x) Y(y) Z(z) of the
 // current state, so beta is scaled alike.
 template <typename T, bool SCALED>
-__global__ void k_sources(T* __restrict__ field, int64_t n_entries,
+__global__ void k_sources(T* __restrict__ field, int64_t n_entries, const int64_t* count,
                           const int64_t* __restrict__ off,
                           const double* __restrict__ alpha,
                           const double* __restrict__ beta,
@@ -329,6 +329,7 @@ __global__ void k_sources(T* __restrict__ field, int64_t n_entries,
                           const double* __restrict__ sc)
 {
     int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (count) n_entries = count[1];   // tables re-binned on the device since the host counted
     if (e >= n_entries) return;
     int64_t o = off[e];
     double b = beta[e];
@@ -522,7 +523,9 @@ bfvm_status launch_step_fused(Ctx* c, int p, bool renorm)
     Q.extra_need = c->wait_test_polls > 0 ? 1u : 0u;
     Q.eclaim = c->d_sched + 2 + 3 * c->n_sub;
     Q.shell_done = Q.eclaim + 1;
-    const int64_t n_seg = c->n_sub > 0 ? c->src.n_entries / c->n_sub : 0;
+    // occupied voxels: exact, or (after a device-only cell update) the
+    // capacity, with the exact count read by the kernel
+    const int64_t n_seg = c->src.counts_on_host ? c->src.n_seg : c->src.cap;
     int64_t n_epi = 0;
     for (int s = 0; s < c->n_sub; ++s)
         n_epi += (c->bc_kind[s] == BFVM_BC_DIRICHLET ? persistent::epi_shell_chunks(c->nx, c->ny, c->nz) : 0) +
@@ -537,6 +540,7 @@ bfvm_status launch_step_fused(Ctx* c, int p, bool renorm)
     E.L = c->coef.L;
     E.sc = renorm ? nullptr : A[0].sc_p1;
     E.n_seg = n_seg;
+    E.d_nseg = c->src.counts_on_host ? nullptr : c->src.d_count;
     E.off = c->src.off;
     E.alpha = c->src.alpha;
     E.beta = c->src.beta;
@@ -701,9 +705,14 @@ bfvm_status build_line_tables(Ctx* c)
 bfvm_status launch_sources(Ctx* c, int p_next, bool renormed)
 {
     const SourceTable& S = c->src;
-    if (S.n_entries == 0) return BFVM_OK;
+    if (S.cap == 0) return BFVM_OK;
+    // with counts only on the device, cover the capacity and let the kernel
+    // read the entry count
+    const int64_t* dcount = S.counts_on_host ? nullptr : S.d_count;
+    const int64_t n_ent = S.counts_on_host ? S.n_entries : S.cap * c->n_sub;
+    if (n_ent == 0) return BFVM_OK;
     int blk = 256;
-    unsigned grid = (unsigned)ceil_div(S.n_entries, blk);
+    unsigned grid = (unsigned)ceil_div(n_ent, blk);
     int off_y = c->nx, off_z = c->nx + c->ny;
     bool scaled = (c->variant == 1 && c->precision == 64 && !renormed);
     KernelTimer timer(c, 3);
@@ -712,17 +721,17 @@ bfvm_status launch_sources(Ctx* c, int p_next, bool renormed)
         if (scaled) {
             const double* sc = c->coef.sc + (int64_t)p_next * c->n_sub * c->coef.L;
             k_sources<double, true><<<grid, blk, 0, c->stream>>>(
-                f, S.n_entries, S.off, S.alpha, S.beta, S.vox, S.sub, c->nx, c->ny,
+                f, n_ent, dcount, S.off, S.alpha, S.beta, S.vox, S.sub, c->nx, c->ny,
                 c->coef.L, off_y, off_z, sc);
         } else {
             k_sources<double, false><<<grid, blk, 0, c->stream>>>(
-                f, S.n_entries, S.off, S.alpha, S.beta, S.vox, S.sub, c->nx, c->ny,
+                f, n_ent, dcount, S.off, S.alpha, S.beta, S.vox, S.sub, c->nx, c->ny,
                 c->coef.L, off_y, off_z, nullptr);
         }
     } else {
         float* f = reinterpret_cast<float*>(c->field);
         k_sources<float, false><<<grid, blk, 0, c->stream>>>(
-            f, S.n_entries, S.off, S.alpha, S.beta, S.vox, S.sub, c->nx, c->ny,
+            f, n_ent, dcount, S.off, S.alpha, S.beta, S.vox, S.sub, c->nx, c->ny,
             c->coef.L, off_y, off_z, nullptr);
     }
     c->launches += 1;
