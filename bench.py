@@ -252,6 +252,75 @@ def measure_forms(args, plain_ups, dev, stream, flush):
             "speedup_vs_one_by_one": mss / msb,
             "speedup_vs_plain_fp64_tumour": (n_upd * K / (msb / 1e3)) / plain_ups,
             "steps": K}
+    # 2-D variant: a 1000 x 1000 x 1 x 2 grid, oxygen Dirichlet + a
+    # zero-flux factor, 20k cells (lines of 1000 voxels: the one-thread-per-
+    # line sweep that keeps the intermediates in the field)
+    p2 = inputs.make_problem(1000, 1000, 1, n_sub=2, D=[1e5, 1e3], lam=[0.1, 0.01],
+                             bc_kind=[1, 0], bc_value=[38.0, 0.0], field_mode="zero",
+                             n_cells=20_000, U=[10.0, 0.0], S=[0.0, 10.0],
+                             rho_star=[1.0, 1.0], steps=K, seed=0, dims=2)
+    s2 = bfvm.Sim.from_problem(p2)
+    s2.step(3)
+    ms2 = timed_steps(lambda: s2.step(1), K, stream, flush)
+    s2.close()
+    ups2 = p2.updates_per_step * K / (ms2 / 1e3)
+    out["two_d"] = {"value": ups2, "grid": [p2.nx, p2.ny, 1], "n_sub": 2, "steps": K,
+                    "form": "plain Thomas, x and y sweeps", "ratio_vs_plain_fp64_3d": ups2 / plain_ups,
+                    "hbm_frac_32B_per_update": ups2 * 4 * 8 / 1e9 / peaks()[0]}
+    # Dirichlet nodes: the 200^3 x 2 workload with 40 vessel columns of
+    # oxygen nodes (per-axis launches plus node fills)
+    pt = inputs.tumour_200(steps=K)
+    rng = np.random.default_rng(5)
+    vox, sub, val = [], [], []
+    for _ in range(40):
+        x, y = rng.integers(10, 190, size=2)
+        v, sb, vl = inputs.vessel_nodes(pt.nx, pt.ny, pt.nz, substrate=0, value=38.0, x=int(x), y=int(y))
+        vox.append(v); sub.append(sb); val.append(vl)
+    pn = pt.with_(nodes=(np.concatenate(vox), np.concatenate(sub), np.concatenate(val)))
+    sn = bfvm.Sim.from_problem(pn)
+    sn.step(3)
+    msn = timed_steps(lambda: sn.step(1), K, stream, flush)
+    sn.close()
+    upsn = pn.updates_per_step * K / (msn / 1e3)
+    out["dirichlet_nodes"] = {"value": upsn, "nodes": int(len(pn.nodes[0])), "steps": K,
+                              "ratio_vs_plain_fp64_no_nodes": upsn / plain_ups}
+    # moving cells: re-binning the 250k tumour cells on the device
+    # (bfvm_update_cells) against bfvm_set_cells, and a run that moves the
+    # cells every 10 steps
+    sc_ = bfvm.Sim.from_problem(pt)
+    t = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)
+    arrs = [t(pt.pos), t(pt.vol), t(pt.S), t(pt.U), t(pt.rho_star)]
+    moved = [t(np.clip(pt.pos + rng.normal(0, 5.0, pt.pos.shape), 0, 200 * pt.dx))] + arrs[1:]
+    sc_.update_cells(*moved)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(5):
+        sc_.update_cells(*(moved if i % 2 == 0 else arrs))
+    e1.record(stream)
+    torch.cuda.synchronize()
+    upd_ms = e0.elapsed_time(e1) / 5
+    t0 = time.perf_counter()
+    for i in range(3):
+        sc_.set_cells(*(moved if i % 2 == 0 else arrs))
+    torch.cuda.synchronize()
+    set_ms = (time.perf_counter() - t0) * 1e3 / 3
+    sc_.set_cells(*arrs)
+    sc_.step(10)
+    torch.cuda.synchronize()
+    n_cad = 10
+    e0.record(stream)
+    for i in range(n_cad):
+        sc_.update_cells(*(moved if i % 2 == 0 else arrs))
+        sc_.step(10)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    cad_ms = e0.elapsed_time(e1)
+    sc_.close()
+    out["moving_cells"] = {"cells": pt.n_cells, "update_cells_ms": upd_ms,
+                           "set_cells_ms_host_timed": set_ms,
+                           "cadence_value": pt.updates_per_step * 10 * n_cad / (cad_ms / 1e3),
+                           "cadence": "cells re-binned on the device every 10 steps, 100 steps"}
     # adjoint: forward with checkpoints every 20 steps, then the backward
     p, q = inputs.adjoint_problem()
     target = None

@@ -129,10 +129,12 @@ bfvm_status copy_in_dense(Ctx* c, const void* src, bool on_device)
 {
     size_t es = elem_size(c);
     int64_t rows = (int64_t)c->n_sub * c->nz * c->ny;
-    BFVM_CUDA(c, cudaMemcpy2DAsync(c->field, c->pitch * es, src, c->nx * es, c->nx * es,
-                                   rows, on_device ? cudaMemcpyDeviceToDevice
-                                                   : cudaMemcpyHostToDevice,
-                                   c->stream));
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    if (c->pitch == c->nx)   // rows are contiguous: one linear copy
+        BFVM_CUDA(c, cudaMemcpyAsync(c->field, src, es * rows * c->nx, kind, c->stream));
+    else
+        BFVM_CUDA(c, cudaMemcpy2DAsync(c->field, c->pitch * es, src, c->nx * es, c->nx * es,
+                                       rows, kind, c->stream));
     if (!on_device) BFVM_CUDA(c, cudaStreamSynchronize(c->stream));
     return BFVM_OK;
 }
@@ -141,24 +143,35 @@ bfvm_status copy_out_dense(Ctx* c, void* dst, bool on_device)
 {
     size_t es = elem_size(c);
     int64_t rows = (int64_t)c->n_sub * c->nz * c->ny;
+    const size_t bytes = es * rows * c->nx;
     if (c->scale_state != 0) {
         // the stored field carries a rescale: divide it out while copying
+        // (through the context's staging buffer when the target is the host)
         void* tmp = dst;
-        if (!on_device) BFVM_CUDA(c, cudaMalloc(&tmp, es * rows * c->nx));
+        if (!on_device) {
+            if (c->staging_bytes < bytes) {
+                if (c->staging) cudaFree(c->staging);
+                c->staging = nullptr;
+                c->staging_bytes = 0;
+                BFVM_CUDA(c, cudaMalloc(&c->staging, bytes));
+                c->staging_bytes = bytes;
+            }
+            tmp = c->staging;
+        }
         bfvm_status st = launch_unscale_copy(c, tmp, c->scale_state);
         if (st == BFVM_OK && !on_device) {
-            cudaError_t e = cudaMemcpyAsync(dst, tmp, es * rows * c->nx,
-                                            cudaMemcpyDeviceToHost, c->stream);
+            cudaError_t e = cudaMemcpyAsync(dst, tmp, bytes, cudaMemcpyDeviceToHost, c->stream);
             if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
             if (e != cudaSuccess) st = cuda_err(c, e, "copy out");
         }
-        if (!on_device) cudaFree(tmp);
         return st;
     }
-    BFVM_CUDA(c, cudaMemcpy2DAsync(dst, c->nx * es, c->field, c->pitch * es, c->nx * es,
-                                   rows, on_device ? cudaMemcpyDeviceToDevice
-                                                   : cudaMemcpyDeviceToHost,
-                                   c->stream));
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (c->pitch == c->nx)
+        BFVM_CUDA(c, cudaMemcpyAsync(dst, c->field, bytes, kind, c->stream));
+    else
+        BFVM_CUDA(c, cudaMemcpy2DAsync(dst, c->nx * es, c->field, c->pitch * es, c->nx * es,
+                                       rows, kind, c->stream));
     if (!on_device) BFVM_CUDA(c, cudaStreamSynchronize(c->stream));
     return BFVM_OK;
 }
@@ -276,6 +289,7 @@ void bfvm_destroy(bfvm_ctx* h)
     for (cudaEvent_t e : c->ev_stop) cudaEventDestroy(e);
     free_sources(c);
     free_coefficients(c);
+    if (c->staging) cudaFree(c->staging);
     c->free_nodes();
     c->free_line_tables();
     if (c->field) cudaFree(c->field);
@@ -291,16 +305,28 @@ bfvm_status bfvm_set_density(bfvm_ctx* h, const void* rho, int32_t on_device)
     Ctx* c = &h->impl;
     if (!rho) return set_err(c, BFVM_EINVAL, "rho is NULL");
     if (!on_device) {
-        int64_t n = (int64_t)c->n_sub * c->nz * c->ny * c->nx;
-        if (c->precision == 64) {
-            const double* a = static_cast<const double*>(rho);
-            for (int64_t i = 0; i < n; ++i)
-                if (!isfinite(a[i])) return set_err(c, BFVM_ENONFINITE, "rho holds a NaN or Inf");
-        } else {
-            const float* a = static_cast<const float*>(rho);
-            for (int64_t i = 0; i < n; ++i)
-                if (!isfinite(a[i])) return set_err(c, BFVM_ENONFINITE, "rho holds a NaN or Inf");
+        // host input: copied into the staging buffer and checked for NaN and
+        // Inf there, on the GPU; the field is only replaced when it is clean
+        const size_t es = elem_size(c);
+        const int64_t n = (int64_t)c->n_sub * c->nz * c->ny * c->nx;
+        const size_t bytes = es * n;
+        if (c->staging_bytes < bytes) {
+            if (c->staging) cudaFree(c->staging);
+            c->staging = nullptr;
+            c->staging_bytes = 0;
+            BFVM_CUDA(c, cudaMalloc(&c->staging, bytes));
+            c->staging_bytes = bytes;
         }
+        BFVM_CUDA(c, cudaMemcpyAsync(c->staging, rho, bytes, cudaMemcpyHostToDevice, c->stream));
+        int bad = 0;
+        bfvm_status st = launch_check_finite(c, c->staging, n, &bad);
+        if (st != BFVM_OK) return st;
+        if (bad) return set_err(c, BFVM_ENONFINITE, "rho holds a NaN or Inf");
+        drop_recording(c);
+        st = copy_in_dense(c, c->staging, true);
+        if (st != BFVM_OK) return st;
+        c->scale_state = 0;
+        return BFVM_OK;
     }
     drop_recording(c);
     bfvm_status st = copy_in_dense(c, rho, on_device != 0);

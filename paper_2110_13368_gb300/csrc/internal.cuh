@@ -107,6 +107,8 @@ struct Ctx {
                                   // lambda dt / 2 each, four-edge Dirichlet shell)
     // Dirichlet nodes inside the domain (bfvm_set_dirichlet_nodes): one per
     // (voxel, substrate), the caller's later node kept where two coincide
+    void* staging = nullptr;         // device buffer for unscaled copies to the host
+    size_t staging_bytes = 0;
     int64_t n_nodes = 0;
     int64_t* d_node_off = nullptr;   // pitched field offset
     int32_t* d_node_vox = nullptr;   // x + nx (y + ny z)
@@ -244,6 +246,7 @@ bfvm_status launch_step(Ctx* c, int p, bool renorm);
 bfvm_status launch_shell_fill(Ctx* c, int p_scale);
 bfvm_status build_line_tables(Ctx* c);
 bfvm_status launch_unscale_copy(Ctx* c, void* out_dev, int p);
+bfvm_status launch_check_finite(Ctx* c, const void* a, int64_t n, int* bad);
 
 // sources (sources.cu)
 bfvm_status build_sources(Ctx* c, int64_t n_cells, const double* pos,

@@ -823,6 +823,37 @@ __global__ void k_unscale_copy(const T* __restrict__ field, T* __restrict__ out,
 
 }  // namespace
 
+namespace {
+template <typename T>
+__global__ void k_check_finite(const T* __restrict__ a, int64_t n, int* flag)
+{
+    int bad = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        bad |= !isfinite((double)a[i]);
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(flag, 1);
+}
+}  // namespace
+
+// Does the dense buffer `a` (n elements of the context's type) hold a NaN or
+// an Inf?  Synchronises the stream.
+bfvm_status launch_check_finite(Ctx* c, const void* a, int64_t n, int* bad)
+{
+    BFVM_CUDA(c, cudaMemsetAsync(c->d_err + 3, 0, sizeof(int), c->stream));
+    const unsigned grid = (unsigned)std::min<int64_t>(ceil_div(n, 256), (int64_t)c->sm_count * 8);
+    if (c->precision == 64)
+        k_check_finite<double><<<grid, 256, 0, c->stream>>>(static_cast<const double*>(a), n,
+                                                             c->d_err + 3);
+    else
+        k_check_finite<float><<<grid, 256, 0, c->stream>>>(static_cast<const float*>(a), n,
+                                                           c->d_err + 3);
+    c->launches += 1;
+    BFVM_CUDA(c, cudaGetLastError());
+    BFVM_CUDA(c, cudaMemcpyAsync(bad, c->d_err + 3, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    BFVM_CUDA(c, cudaStreamSynchronize(c->stream));
+    return BFVM_OK;
+}
+
 // Copy the field into a dense device buffer, removing the rescale of state p.
 bfvm_status launch_unscale_copy(Ctx* c, void* out_dev, int p)
 {
