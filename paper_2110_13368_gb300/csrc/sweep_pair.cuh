@@ -82,6 +82,24 @@ struct PairSweeper {
         }
     }
 
+    // One forward / backward recurrence step.  Plain form (MODE 0):
+    // d'_k = (d_k + c d'_{k-1}) r_k, x_k = d'_k + (c r_k) x_{k+1}; in FP32
+    // every coefficient is an unevaluated hi + lo pair and each step is a
+    // compensated multiply-add (comp_axpy).  Rescaled form: one FMA each.
+    __device__ __forceinline__ T fwd_op(const CoefRow<T>& C, T prev, T d, int k) const
+    {
+        if (MODE != 0) return fma(C.a[k], prev, d);
+        if (sizeof(T) == 8) return fma(C.c, prev, d) * C.a[k];
+        const float t = comp_axpy((float)C.c, (float)C.c_lo, (float)prev, (float)d);
+        return (T)__fmaf_rn(t, (float)C.a[k], __fmul_rn(t, (float)C.a_lo[k]));
+    }
+    __device__ __forceinline__ T bwd_op(const CoefRow<T>& C, T x, T w, int k) const
+    {
+        if (MODE == 0 && sizeof(T) == 4)
+            return (T)comp_axpy((float)C.b[k], (float)C.b_lo[k], (float)x, (float)w);
+        return fma(C.b[k], x, w);
+    }
+
     // F: forward elimination of group g (parity Q); prev carries the chain
     template <int Q>
     __device__ __forceinline__ void fwd_group(const Line& L, const CoefRow<T>& C, T& prev,
@@ -98,8 +116,8 @@ struct PairSweeper {
                 T dk = d[u];
                 if (L.dir && k == 0) dk = (T)L.end0;
                 if (L.dir && k == n - 1) dk = (T)L.end1;
-                if (MODE == 0) prev = fma(C.c, prev, dk) * C.a[k];
-                else prev = (k == 0) ? dk : fma(C.a[k], prev, dk);
+                if (MODE == 0) prev = fwd_op(C, prev, dk, k);
+                else prev = (k == 0) ? dk : fwd_op(C, prev, dk, k);
                 if (k < n - 1) *own<Q>(k, u) = prev;
             }
         }
@@ -137,14 +155,12 @@ struct PairSweeper {
     __device__ __forceinline__ void fwd_fast(const CoefRow<T>& C, T& prev, int g) const
     {
         T* p = W + slot<Q>(g * G) * 32;
-        const T* a = C.a + g * G;
         T d[G];
 #pragma unroll
         for (int u = 0; u < G; ++u) d[u] = p[off<Q>(u)];
 #pragma unroll
         for (int u = 0; u < G; ++u) {
-            if (MODE == 0) prev = fma(C.c, prev, d[u]) * a[u];
-            else prev = fma(a[u], prev, d[u]);
+            prev = fwd_op(C, prev, d[u], g * G + u);
             p[off<Q>(u)] = prev;
         }
     }
@@ -155,13 +171,12 @@ struct PairSweeper {
     {
         const int k0 = h * G;
         T* p = W + slot<Q>(k0) * 32;
-        const T* b = C.b + k0;
         T w[G], o[G];
 #pragma unroll
         for (int u = 0; u < G; ++u) w[u] = p[off<Q>(u)];
 #pragma unroll
         for (int u = G - 1; u >= 0; --u) {
-            x = fma(b[u], x, w[u]);
+            x = bwd_op(C, x, w[u], k0 + u);
             o[u] = (MODE == 2) ? (T)(((double)x * C.o[k0 + u]) * L.inv_other) : x;
         }
         if (AXIS == 0) {
@@ -286,7 +301,7 @@ struct PairSweeper {
         for (int u = G - 1; u >= 0; --u) {
             const int k = h * G + u;
             if (k < n) {
-                if (k < n - 1) x = fma(C.b[k], x, w[u]);
+                if (k < n - 1) x = bwd_op(C, x, w[u], k);
                 o[u] = (MODE == 2) ? (T)(((double)x * C.o[k]) * L.inv_other) : x;
             }
         }
@@ -323,7 +338,6 @@ __global__ void __launch_bounds__(256, 1) k_sweep_pair(SweepArgs<T> A, LineSet S
                                                        int64_t n_blocks, int n_slots)
 {
     constexpr int G = Groups<T>::G;
-    constexpr int LG = Groups<T>::LAG_GROUPS;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
@@ -337,7 +351,7 @@ __global__ void __launch_bounds__(256, 1) k_sweep_pair(SweepArgs<T> A, LineSet S
     const int ns = n_slots;
     const int n_sub = A.n_sub;
 
-    const int ncoef = 2;
+    const int ncoef = (MODE == 0 && sizeof(T) == 4) ? 4 : 2;   // FP32: hi and lo parts
     T* cbase = reinterpret_cast<T*>(smem_raw);
     const int per_sub = ncoef * n;
     const size_t coef_bytes = (size_t)n_sub * per_sub * sizeof(T);
@@ -354,6 +368,10 @@ __global__ void __launch_bounds__(256, 1) k_sweep_pair(SweepArgs<T> A, LineSet S
         if (MODE == 0) {
             dst[k] = A.r[src];
             dst[n + k] = A.cr[src];
+            if (sizeof(T) == 4) {
+                dst[2 * n + k] = A.r_lo[src];
+                dst[3 * n + k] = A.cr_lo[src];
+            }
         } else {
             dst[k] = (T)A.fa[src];
             dst[n + k] = (T)A.fb[src];
@@ -384,11 +402,11 @@ __global__ void __launch_bounds__(256, 1) k_sweep_pair(SweepArgs<T> A, LineSet S
         const T* r = cbase + (size_t)s * per_sub;
         C.a = r;
         C.b = r + n;
-        C.a_lo = r;
-        C.b_lo = r;
+        C.a_lo = (ncoef == 4) ? r + 2 * n : r;
+        C.b_lo = (ncoef == 4) ? r + 3 * n : r;
         C.o = obase + (size_t)s * n;
         C.c = (MODE == 0) ? A.cvec[s * 3 + AXIS] : (T)0;
-        C.c_lo = (T)0;
+        C.c_lo = (ncoef == 4) ? A.cvec_lo[s * 3 + AXIS] : (T)0;
         return C;
     };
     const int gcount = (n + G - 1) / G;

@@ -1,4 +1,4 @@
-// The three sweeps of one step (FP64, rescaled form) as one persistent
+// The three sweeps of one step (any form and precision) as one persistent
 // launch (included by sweeps.cu after sweep_pair.cuh, whose PairSweeper it
 // drives).
 //
@@ -73,8 +73,9 @@ struct StepSched {
 
 // Everything the epilogue reads: grid, the scales of state p + 1 (null when
 // the step renormalises: plain values) and the composed cell maps.
+template <typename T>
 struct EpiArgs {
-    double* field;
+    T* field;
     int nx, ny, nz;
     int64_t pitch, L;
     const double* sc;       // [s][L] scales of state p + 1, or null
@@ -206,15 +207,15 @@ __device__ __forceinline__ void task_done(const StepSched& Q, TaskRef r, int lan
 
 // Line of this lane in task r (padding lanes past the set's end repeat its
 // last line and are not stored)
-template <int AXIS, int MODE>
-__device__ __forceinline__ Line task_line(const SweepArgs<double>& A, const LineSet& S,
+template <typename T, int AXIS, int MODE>
+__device__ __forceinline__ Line task_line(const SweepArgs<T>& A, const LineSet& S,
                                           const int64_t* fs, TaskRef r, int lane)
 {
     const int64_t hi = fs[r.s + 1];
     int64_t line = fs[r.s] + (int64_t)r.j * 32 + lane;
     const bool valid = line < hi;
     if (!valid) line = hi - 1;
-    Line L = make_line<double, AXIS, MODE>(A, S, fs, line);
+    Line L = make_line<T, AXIS, MODE>(A, S, fs, line);
     L.valid = valid;
     return L;
 }
@@ -232,8 +233,8 @@ struct LinePre {
     double v, sa, sb, se0, se1, ia, ib;
 };
 
-template <int AXIS, int MODE>
-__device__ __forceinline__ LinePre issue_line(const SweepArgs<double>& A, const LineSet& S,
+template <typename T, int AXIS, int MODE>
+__device__ __forceinline__ LinePre issue_line(const SweepArgs<T>& A, const LineSet& S,
                                               const int64_t* fs, const int* bck,
                                               const double* bcv, TaskRef r, int lane)
 {
@@ -303,27 +304,43 @@ __device__ __forceinline__ Line finish_line(const LinePre& P)
     return L;
 }
 
-// Coefficient rows of substrate s on this axis: the forward and backward
-// coefficients from the kernel's shared copies cfa / cfb ([s][L]; every lane
-// of a task has the same s, so each read is a broadcast), the output scales
-// of a renormalising z sweep from global memory
-__device__ __forceinline__ CoefRow<double> step_coef_row(const SweepArgs<double>& A,
-                                                         const double* cfa, const double* cfb,
-                                                         int s)
+// The kernel's shared copies of the coefficients, [s][L] per table: the
+// forward and backward coefficients (fa / fb of the rescaled form, r / cr of
+// the plain form) and, for the FP32 plain form, their low parts.
+template <typename T>
+struct CoefTabs {
+    const T* a;
+    const T* b;
+    const T* a_lo;
+    const T* b_lo;
+};
+
+// Coefficient rows of substrate s on this axis from the shared tables
+// (every lane of a task has the same s, so each read is a broadcast); the
+// plain form's off-diagonal c and the output scales of a renormalising z
+// sweep from global memory
+template <typename T, int AXIS, int MODE>
+__device__ __forceinline__ CoefRow<T> step_coef_row(const SweepArgs<T>& A, const CoefTabs<T>& K,
+                                                    int s)
 {
-    CoefRow<double> C;
+    CoefRow<T> C;
     const int64_t row = (int64_t)s * A.L + A.axis_off;
-    C.a = cfa + row;
-    C.b = cfb + row;
-    C.a_lo = C.a;
-    C.b_lo = C.b;
+    C.a = K.a + row;
+    C.b = K.b + row;
+    C.a_lo = K.a_lo + row;
+    C.b_lo = K.b_lo + row;
     C.o = A.isc_p1 + row;
-    C.c = 0.0;
-    C.c_lo = 0.0;
+    C.c = (T)0;
+    C.c_lo = (T)0;
+    if (MODE == 0) {
+        C.c = A.cvec[s * 3 + AXIS];
+        if (sizeof(T) == 4) C.c_lo = A.cvec_lo[s * 3 + AXIS];
+    }
     return C;
 }
 
-__device__ __forceinline__ int64_t axis_stride(const SweepArgs<double>& A, int axis)
+template <typename T>
+__device__ __forceinline__ int64_t axis_stride(const SweepArgs<T>& A, int axis)
 {
     return axis == 0 ? 1 : (axis == 1 ? A.pitch : (int64_t)A.ny * A.pitch);
 }
@@ -332,22 +349,20 @@ __device__ __forceinline__ int64_t axis_stride(const SweepArgs<double>& A, int a
 // the whole task on its own, else next to B's back substitution with
 // `iters` pair-barrier meetings.  Returns the chain value of the last
 // element (handed to B).
-template <int AXIS, int MODE>
-__device__ __forceinline__ double f_task(const SweepArgs<double>& A, const Line& L, double* field,
-                                         const double* cfa, const double* cfb, double* W, int ns,
-                                         int lane, int bar_id, int64_t* rbF, int q, bool solo,
-                                         int iters)
+template <typename T, int AXIS, int MODE>
+__device__ __forceinline__ T f_task(const SweepArgs<T>& A, const Line& L, T* field,
+                                    const CoefTabs<T>& K, T* W, int ns, int lane, int bar_id,
+                                    int64_t* rbF, int q, bool solo, int iters)
 {
-    constexpr int G = Groups<double>::G;
-    PairSweeper<double, AXIS, MODE> sw{A, W, field, field, axis_stride(A, AXIS), A.n, ns, lane,
-                                       bar_id};
-    const CoefRow<double> C = step_coef_row(A, cfa, cfb, L.s);
+    constexpr int G = Groups<T>::G;
+    PairSweeper<T, AXIS, MODE> sw{A, W, field, field, axis_stride(A, AXIS), A.n, ns, lane, bar_id};
+    const CoefRow<T> C = step_coef_row<T, AXIS, MODE>(A, K, L.s);
     __syncwarp();
     rbF[lane] = L.base;
     __syncwarp();
     int64_t rv[G];
     sw.load_rows(rbF, rv);
-    double prev;
+    T prev;
     if (solo) {
         const int gcount = (A.n + G - 1) / G;
         for (int g = 0; g < gcount; ++g) {
@@ -370,17 +385,15 @@ __device__ __forceinline__ double f_task(const SweepArgs<double>& A, const Line&
 // without F next to it.  The line bases (-1 for padding lanes) and the
 // substrate come from F through shared memory (rbB, hs): F built them when
 // it eliminated the task.  `rel` publishes the task's completion.
-template <int AXIS, int MODE, typename Rel>
-__device__ __forceinline__ void b_task(const SweepArgs<double>& A, const LineSet& S,
+template <typename T, int AXIS, int MODE, typename Rel>
+__device__ __forceinline__ void b_task(const SweepArgs<T>& A, const LineSet& S,
                                        const int64_t* fs, const int* bck, const double* bcv,
-                                       double* field, const double* cfa,
-                                       const double* cfb, double* W, int ns, int lane,
+                                       T* field, const CoefTabs<T>& K, T* W, int ns, int lane,
                                        int bar_id, TaskRef r, const int64_t* rbB, const int* hs,
-                                       int q, double x, bool paired, int iters, const Rel& rel)
+                                       int q, T x, bool paired, int iters, const Rel& rel)
 {
-    constexpr int G = Groups<double>::G;
-    PairSweeper<double, AXIS, MODE> sw{A, W, field, field, axis_stride(A, AXIS), A.n, ns, lane,
-                                       bar_id};
+    constexpr int G = Groups<T>::G;
+    PairSweeper<T, AXIS, MODE> sw{A, W, field, field, axis_stride(A, AXIS), A.n, ns, lane, bar_id};
     Line L;
     const int64_t hb = rbB[lane];
     L.valid = hb >= 0;
@@ -389,8 +402,8 @@ __device__ __forceinline__ void b_task(const SweepArgs<double>& A, const LineSet
     L.dir = false;
     L.end0 = L.end1 = 0.0;
     L.inv_other = 1.0;
-    if (MODE == 2) L.inv_other = finish_line<MODE>(issue_line<AXIS, MODE>(A, S, fs, bck, bcv, r, lane)).inv_other;
-    const CoefRow<double> C = step_coef_row(A, cfa, cfb, L.s);
+    if (MODE == 2) L.inv_other = finish_line<MODE>(issue_line<T, AXIS, MODE>(A, S, fs, bck, bcv, r, lane)).inv_other;
+    const CoefRow<T> C = step_coef_row<T, AXIS, MODE>(A, K, L.s);
     int64_t rv[G];
     sw.load_rows(rbB, rv);
     if (q) sw.template b_block<1>(L, C, x, rbB, rv, paired, iters, rel);
@@ -400,12 +413,14 @@ __device__ __forceinline__ void b_task(const SweepArgs<double>& A, const LineSet
 // Shell voxels of one Dirichlet substrate, enumerated as z planes (2 nx ny),
 // y rows of the other planes (2 nx nz), x columns (2 ny nz); overlaps are
 // written twice with the same value.
-__device__ __forceinline__ int64_t shell_count(const EpiArgs& E)
+template <typename T>
+__device__ __forceinline__ int64_t shell_count(const EpiArgs<T>& E)
 {
     return 2 * ((int64_t)E.nx * E.ny + (int64_t)E.nx * E.nz + (int64_t)E.ny * E.nz);
 }
 
-__device__ __forceinline__ void shell_voxel(const EpiArgs& E, int s, double v, int64_t t)
+template <typename T>
+__device__ __forceinline__ void shell_voxel(const EpiArgs<T>& E, int s, double v, int64_t t)
 {
     const int64_t fz = 2 * (int64_t)E.nx * E.ny, fy = 2 * (int64_t)E.nx * E.nz;
     int x, y, z;
@@ -421,7 +436,7 @@ __device__ __forceinline__ void shell_voxel(const EpiArgs& E, int s, double v, i
         const double* q = E.sc + (int64_t)s * E.L;
         v = v * (__ldg(q + x) * __ldg(q + E.nx + y) * __ldg(q + E.nx + E.ny + z));
     }
-    E.field[(((int64_t)s * E.nz + z) * E.ny + y) * E.pitch + x] = v;
+    E.field[(((int64_t)s * E.nz + z) * E.ny + y) * E.pitch + x] = (T)v;
 }
 
 // Wait (bounded) until counter p reaches need; lane 0 polls, then every
@@ -449,7 +464,8 @@ __device__ __forceinline__ void wait_count(const StepSched& Q, const unsigned* p
 // of s is complete too (a cell may sit in a shell voxel).  A chunk waits
 // only on sweep tasks and on earlier chunks that never wait on it, and a
 // warp acquires each completion at most once.
-__device__ __forceinline__ void step_epilogue(const StepSched& Q, const EpiArgs& E,
+template <typename T>
+__device__ __forceinline__ void step_epilogue(const StepSched& Q, const EpiArgs<T>& E,
                                               const int* tf, const int* bck, const double* bcv,
                                               int lane)
 {
@@ -505,7 +521,8 @@ __device__ __forceinline__ void step_epilogue(const StepSched& Q, const EpiArgs&
             // all reads of kEpiUnroll entries first (entries are distinct
             // voxel-substrate pairs, so no two touch one field element)
             int64_t o[kEpiUnroll];
-            double a[kEpiUnroll], b[kEpiUnroll], f[kEpiUnroll];
+            double a[kEpiUnroll], b[kEpiUnroll];
+            T f[kEpiUnroll];
 #pragma unroll
             for (int u = 0; u < kEpiUnroll; ++u) {
                 const int64_t g = g0 + 32 * u;
@@ -530,7 +547,7 @@ __device__ __forceinline__ void step_epilogue(const StepSched& Q, const EpiArgs&
                 if (o[u] >= 0) f[u] = E.field[o[u]];
 #pragma unroll
             for (int u = 0; u < kEpiUnroll; ++u)
-                if (o[u] >= 0) E.field[o[u]] = fma(a[u], f[u], b[u]);
+                if (o[u] >= 0) E.field[o[u]] = (T)fma(a[u], (double)f[u], b[u]);
         }
     }
 }
@@ -541,25 +558,26 @@ __device__ __forceinline__ void pair_sync(int bar_id)
 }
 
 // What a pair's two warps share besides the column buffer.
+template <typename T>
 struct PairShared {
     const int* bck;        // shared copy of the substrates' boundary kinds
     const double* bcv;     // and Dirichlet values
-    double* field;         // the field (read and written in place)
-    const double* cfa;     // shared forward coefficients [s][L]
-    const double* cfb;     // shared backward coefficients [s][L]
+    T* field;              // the field (read and written in place)
+    CoefTabs<T> K;         // shared coefficient tables
     int64_t* rbF;          // [32] row bases of F's task (x tasks)
     int64_t* rbB;          // [32] line bases of B's task (-1: padding), written by F
     int* hs;               // [32] substrate of each lane's line in B's task, written by F
-    double* handover;      // [32] chain values of the task handed to B
+    T* handover;           // [32] chain values of the task handed to B
     volatile int* ho;      // task handed over, next task, paired (0/1)
-    double* W;             // column buffer
+    T* W;                  // column buffer
     int ns, lane, bar_id;
 };
 
 // Group count of an axis' lines
-__device__ __forceinline__ int axis_groups(const SweepArgs<double>* sA, int a)
+template <typename T>
+__device__ __forceinline__ int axis_groups(const SweepArgs<T>* sA, int a)
 {
-    constexpr int G = Groups<double>::G;
+    constexpr int G = Groups<T>::G;
     return (sA[a].n + G - 1) / G;
 }
 
@@ -567,9 +585,10 @@ __device__ __forceinline__ int axis_groups(const SweepArgs<double>* sA, int a)
 // a_f while B back-substitutes one of axis a_b: B meets once per group of
 // its task; F copies group j after meeting j and eliminates it LG meetings
 // later.
-__device__ __forceinline__ int phase_iters(const SweepArgs<double>* sA, int a_f, int a_b)
+template <typename T>
+__device__ __forceinline__ int phase_iters(const SweepArgs<T>* sA, int a_f, int a_b)
 {
-    constexpr int LG = Groups<double>::LAG_GROUPS;
+    constexpr int LG = Groups<T>::LAG_GROUPS;
     return max(axis_groups(sA, a_f) + LG, axis_groups(sA, a_b));
 }
 
@@ -599,19 +618,19 @@ __device__ __forceinline__ void mark_acquired(FState& f, int i)
 // dependency count, so neither round trip is on the pair's path at the
 // hand-over (an acquire fence there completes the acquire pattern; only when
 // the early read was short does F read the count again).
-template <int AXIS, int MODE>
-__device__ __forceinline__ void f_axis(FState& f, const SweepArgs<double>& A, const LineSet& S,
-                                       const int64_t* fs, const SweepArgs<double>* sA,
-                                       const StepSched& Q, const int* tf, const PairShared& P)
+template <typename T, int AXIS, int MODE>
+__device__ __forceinline__ void f_axis(FState& f, const SweepArgs<T>& A, const LineSet& S,
+                                       const int64_t* fs, const SweepArgs<T>* sA,
+                                       const StepSched& Q, const int* tf, const PairShared<T>& P)
 {
-    const int T = Q.n_tasks;
-    while (f.t < T) {
+    const int NT = Q.n_tasks;
+    while (f.t < NT) {
         const TaskRef r = decode_task(tf, Q.n_sub, f.t);
         if (r.a != AXIS) return;
         const Line L = finish_line<MODE>(
-            f.have_line ? f.pre : issue_line<AXIS, MODE>(A, S, fs, P.bck, P.bcv, r, P.lane));
+            f.have_line ? f.pre : issue_line<T, AXIS, MODE>(A, S, fs, P.bck, P.bcv, r, P.lane));
         f.have_line = false;
-        const bool has_next = f.tn < T;
+        const bool has_next = f.tn < NT;
         TaskRef rn{0, 0, 0};
         unsigned need = 0, seen = 0, raw2 = 0;
         int dep = -1;              // completion counter tn waits on (-1: none or acquired)
@@ -626,12 +645,12 @@ __device__ __forceinline__ void f_axis(FState& f, const SweepArgs<double>& A, co
             if (P.lane == 0) raw2 = atomicAdd(Q.claim, 1u);
             if (rn.a == AXIS) {
                 // the next task's lines: their global reads overlap this task
-                f.pre = issue_line<AXIS, MODE>(A, S, fs, P.bck, P.bcv, rn, P.lane);
+                f.pre = issue_line<T, AXIS, MODE>(A, S, fs, P.bck, P.bcv, rn, P.lane);
                 f.have_line = true;
             }
         }
-        const double prev = f_task<AXIS, MODE>(A, L, P.field, P.cfa, P.cfb, P.W, P.ns, P.lane,
-                                                P.bar_id, P.rbF, f.k & 1, f.solo, f.iters);
+        const T prev = f_task<T, AXIS, MODE>(A, L, P.field, P.K, P.W, P.ns, P.lane, P.bar_id,
+                                             P.rbF, f.k & 1, f.solo, f.iters);
         bool paired = false;
         if (has_next) {
             if (dep < 0) {
@@ -656,7 +675,7 @@ __device__ __forceinline__ void f_axis(FState& f, const SweepArgs<double>& A, co
         }
         pair_sync(P.bar_id);                            // hand-over of task f.t
         if (!has_next) {
-            f.t = T;
+            f.t = NT;
             return;
         }
         if (paired) {
@@ -671,31 +690,31 @@ __device__ __forceinline__ void f_axis(FState& f, const SweepArgs<double>& A, co
         }
         const unsigned t2 = __shfl_sync(0xffffffffu, raw2, 0);
         f.t = f.tn;
-        f.tn = t2 < (unsigned)T ? (int)t2 : T;
+        f.tn = t2 < (unsigned)NT ? (int)t2 : NT;
         ++f.k;
     }
 }
 
 // State of a pair's B warp: the task handed over last
+template <typename T>
 struct BState {
     int t, t_next;
     bool paired;
     int k;
-    double x;
+    T x;
 };
 
 // B warp: back substitutions of consecutive tasks on axis AXIS
-template <int AXIS, int MODE>
-__device__ __forceinline__ void b_axis(BState& b, const SweepArgs<double>& A, const LineSet& S,
-                                       const int64_t* fs, const SweepArgs<double>* sA,
-                                       const StepSched& Q, const int* tf, const PairShared& P)
+template <typename T, int AXIS, int MODE>
+__device__ __forceinline__ void b_axis(BState<T>& b, const SweepArgs<T>& A, const LineSet& S,
+                                       const int64_t* fs, const SweepArgs<T>* sA,
+                                       const StepSched& Q, const int* tf, const PairShared<T>& P)
 {
-    constexpr int LG = Groups<double>::LAG_GROUPS;
-    const int T = Q.n_tasks;
-    while (b.t < T) {
+    const int NT = Q.n_tasks;
+    while (b.t < NT) {
         const TaskRef r = decode_task(tf, Q.n_sub, b.t);
         if (r.a != AXIS) return;
-        const bool more = b.t_next < T;
+        const bool more = b.t_next < NT;
         const bool paired = more && b.paired;
         int iters = 0;
         if (paired) {
@@ -704,10 +723,10 @@ __device__ __forceinline__ void b_axis(BState& b, const SweepArgs<double>& A, co
         }
         const int lane = P.lane;
         auto rel = [&]() { task_done(Q, r, lane); };
-        b_task<AXIS, MODE>(A, S, fs, P.bck, P.bcv, P.field, P.cfa, P.cfb, P.W, P.ns, P.lane,
-                           P.bar_id, r, P.rbB, P.hs, b.k & 1, b.x, paired, iters, rel);
+        b_task<T, AXIS, MODE>(A, S, fs, P.bck, P.bcv, P.field, P.K, P.W, P.ns, P.lane, P.bar_id,
+                              r, P.rbB, P.hs, b.k & 1, b.x, paired, iters, rel);
         if (!more) {
-            b.t = T;
+            b.t = NT;
             return;
         }
         if (!b.paired) pair_sync(P.bar_id);             // buffer free for F
@@ -720,20 +739,53 @@ __device__ __forceinline__ void b_axis(BState& b, const SweepArgs<double>& A, co
     }
 }
 
-// Dynamic shared memory: [copies of the 3 axes' SweepArgs and LineSets]
-// [task_first] [line-set prefixes of the 3 axes] [forward and backward
-// coefficients of state p, all substrates and axes: 2 x n_sub x L]
-// [boundary values and kinds: n_sub doubles, n_sub ints] [per pair: column buffer, 4 x 32 row/line bases, 32 chain values,
-// 4 hand-over words, 32 substrates]
-// [per pair: column buffer (n_slots x 32), 4 x 32 row bases, 32 chain
-// values, 4 hand-over words].  n_slots = G * max over axes of ceil(n/G), so
-// the slot schedule of PairSweeper holds for any two axes.
-template <bool RENORM>
-__global__ void __launch_bounds__(256, 1)
-    k_step_pair(SweepArgs<double> A0, SweepArgs<double> A1, SweepArgs<double> A2, LineSet S0,
-                LineSet S1, LineSet S2, StepSched Q, EpiArgs E, int n_slots)
+// Dynamic shared memory, in this order: copies of the 3 axes' SweepArgs and
+// LineSets; task_first; the line-set prefixes of the 3 axes; the
+// coefficient tables of all substrates and axes (ncoef x n_sub x L: forward
+// and backward, and their FP32 low parts); the boundary values (n_sub
+// doubles) and kinds (n_sub ints); then per pair: the column buffer
+// (n_slots x 32), 4 x 32 row / line bases, 32 chain values, 4 hand-over
+// words and 32 substrates.  n_slots = G * max over axes of ceil(n / G), so
+// the slot schedule of PairSweeper holds for any two axes.  Every part
+// starts on a 16-byte boundary.
+struct StepSmem {
+    size_t args, tf, fs, coef, bc, fixed, pair;
+};
+
+__host__ __device__ inline size_t round16(size_t b) { return (b + 15) & ~(size_t)15; }
+
+template <typename T>
+__host__ __device__ inline StepSmem step_smem(int n_sub, int64_t L, int ncoef, int ns)
 {
-    constexpr int MZ = RENORM ? 2 : 1;
+    StepSmem m;
+    m.args = round16(3 * sizeof(SweepArgs<T>) + 3 * sizeof(LineSet));
+    m.tf = round16(((size_t)3 * n_sub + 1) * sizeof(int));
+    m.fs = round16((size_t)3 * (n_sub + 1) * sizeof(int64_t));
+    m.coef = round16((size_t)ncoef * n_sub * L * sizeof(T));
+    m.bc = round16((size_t)n_sub * (sizeof(double) + sizeof(int)));
+    m.fixed = m.args + m.tf + m.fs + m.coef + m.bc;
+    m.pair = round16((size_t)ns * 32 * sizeof(T) + 4 * 32 * sizeof(int64_t) + 32 * sizeof(T) +
+                     4 * sizeof(int) + 32 * sizeof(int));
+    return m;
+}
+
+// Coefficient tables the step kernel stages: fa / fb in the rescaled form;
+// r / cr in the plain form, with their low parts in FP32.
+template <typename T, int MODE>
+__host__ __device__ constexpr int step_ncoef()
+{
+    return (MODE == 0 && sizeof(T) == 4) ? 4 : 2;
+}
+
+// The step kernel.  T: element type; MXY: form of the x and y sweeps (0
+// plain, 1 rescaled); MZ: form of the z sweep (MXY, or 2: rescaled and
+// renormalising).
+template <typename T, int MXY, int MZ>
+__global__ void __launch_bounds__(256, 1)
+    k_step_pair(SweepArgs<T> A0, SweepArgs<T> A1, SweepArgs<T> A2, LineSet S0, LineSet S1,
+                LineSet S2, StepSched Q, EpiArgs<T> E, int n_slots)
+{
+    constexpr int NC = step_ncoef<T, MXY>();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
@@ -742,27 +794,21 @@ __global__ void __launch_bounds__(256, 1)
     const bool is_b = warp >= pairs;
     const int n_sub = Q.n_sub;
     const int ns = n_slots;
-    const int T = Q.n_tasks;
+    const int NT = Q.n_tasks;
+    const StepSmem M = step_smem<T>(n_sub, A0.L, NC, ns);
 
     // the launch arguments of the three axes are read from shared copies:
     // the loop body stores to shared memory, so the compiler reloads them
     // per task instead of keeping all three axes' values live in registers
-    SweepArgs<double>* sA = reinterpret_cast<SweepArgs<double>*>(smem_raw);
-    LineSet* sS = reinterpret_cast<LineSet*>(smem_raw + 3 * sizeof(SweepArgs<double>));
-    const size_t args_bytes =
-        (3 * sizeof(SweepArgs<double>) + 3 * sizeof(LineSet) + 15) & ~(size_t)15;
-    int* tf = reinterpret_cast<int*>(smem_raw + args_bytes);
-    const size_t tf_bytes = (((size_t)3 * n_sub + 1) * sizeof(int) + 15) & ~(size_t)15;
-    int64_t* fs = reinterpret_cast<int64_t*>(smem_raw + args_bytes + tf_bytes);  // [3][n_sub+1]
-    const size_t fs_bytes = ((size_t)3 * (n_sub + 1) * sizeof(int64_t) + 15) & ~(size_t)15;
+    SweepArgs<T>* sA = reinterpret_cast<SweepArgs<T>*>(smem_raw);
+    LineSet* sS = reinterpret_cast<LineSet*>(smem_raw + 3 * sizeof(SweepArgs<T>));
+    int* tf = reinterpret_cast<int*>(smem_raw + M.args);
+    int64_t* fs = reinterpret_cast<int64_t*>(smem_raw + M.args + M.tf);  // [3][n_sub+1]
     const int64_t n_coef = (int64_t)n_sub * A0.L;
-    double* cfa = reinterpret_cast<double*>(smem_raw + args_bytes + tf_bytes + fs_bytes);
-    double* cfb = cfa + n_coef;
-    double* bcv = cfb + n_coef;                                   // [n_sub]
+    T* cf = reinterpret_cast<T*>(smem_raw + M.args + M.tf + M.fs);
+    double* bcv = reinterpret_cast<double*>(smem_raw + M.args + M.tf + M.fs + M.coef);
     int* bck = reinterpret_cast<int*>(bcv + n_sub);               // [n_sub]
-    const size_t bc_bytes = (n_sub * (sizeof(double) + sizeof(int)) + 15) & ~(size_t)15;
-    unsigned char* pair_area =
-        smem_raw + args_bytes + tf_bytes + fs_bytes + 2 * n_coef * sizeof(double) + bc_bytes;
+    unsigned char* pair_area = smem_raw + M.fixed;
     if (threadIdx.x == 0) {
         sA[0] = A0;
         sA[1] = A1;
@@ -772,9 +818,19 @@ __global__ void __launch_bounds__(256, 1)
         sS[2] = S2;
     }
     for (int i = threadIdx.x; i <= 3 * n_sub; i += blockDim.x) tf[i] = Q.task_first[i];
+    // the three axes share one table per kind ([s][L], axis offsets within L)
     for (int64_t i = threadIdx.x; i < n_coef; i += blockDim.x) {
-        cfa[i] = A0.fa[i];   // the three axes share one table per state
-        cfb[i] = A0.fb[i];
+        if (MXY >= 1) {
+            cf[i] = A0.fa[i];
+            cf[n_coef + i] = A0.fb[i];
+        } else {
+            cf[i] = A0.r[i];
+            cf[n_coef + i] = A0.cr[i];
+            if (NC == 4) {
+                cf[2 * n_coef + i] = A0.r_lo[i];
+                cf[3 * n_coef + i] = A0.cr_lo[i];
+            }
+        }
     }
     for (int i = threadIdx.x; i < n_sub; i += blockDim.x) {
         bcv[i] = A0.bc_value[i];
@@ -790,23 +846,23 @@ __global__ void __launch_bounds__(256, 1)
     const int64_t* fs1 = fs + (n_sub + 1);
     const int64_t* fs2 = fs + 2 * (n_sub + 1);
 
-    const size_t pair_bytes = (size_t)ns * 32 * sizeof(double) + 4 * 32 * sizeof(int64_t) +
-                              32 * sizeof(double) + 4 * sizeof(int) + 32 * sizeof(int);
-    unsigned char* my = pair_area + (size_t)pair * pair_bytes;
-    double* W = reinterpret_cast<double*>(my);
-    int64_t* rbF = reinterpret_cast<int64_t*>(my + (size_t)ns * 32 * sizeof(double));
+    unsigned char* my = pair_area + (size_t)pair * M.pair;
+    T* W = reinterpret_cast<T*>(my);
+    int64_t* rbF = reinterpret_cast<int64_t*>(my + (size_t)ns * 32 * sizeof(T));
     int64_t* rbB = rbF + 64;
-    double* handover = reinterpret_cast<double*>(rbF + 128);
+    T* handover = reinterpret_cast<T*>(rbF + 128);
     volatile int* ho = reinterpret_cast<volatile int*>(handover + 32);  // t_cur, t_next, paired
     int* hs = const_cast<int*>(ho) + 4;                                  // [32] substrates
     const int bar_id = 1 + pair;
 
-    PairShared P;
+    PairShared<T> P;
     P.bck = bck;
     P.bcv = bcv;
     P.field = A0.field;
-    P.cfa = cfa;
-    P.cfb = cfb;
+    P.K.a = cf;
+    P.K.b = cf + n_coef;
+    P.K.a_lo = NC == 4 ? cf + 2 * n_coef : cf;
+    P.K.b_lo = NC == 4 ? cf + 3 * n_coef : cf + n_coef;
     P.rbF = rbF;
     P.rbB = rbB;
     P.hs = hs;
@@ -820,39 +876,39 @@ __global__ void __launch_bounds__(256, 1)
     if (!is_b) {
         FState f;
         f.t = claim_task(Q, lane);
-        f.tn = f.t < T ? claim_task(Q, lane) : T;
+        f.tn = f.t < NT ? claim_task(Q, lane) : NT;
         f.k = 0;
         f.solo = true;
         f.iters = 0;
         f.have_line = false;
         f.acq = 0ull;
-        if (f.t < T) {
+        if (f.t < NT) {
             const TaskRef r0 = decode_task(tf, n_sub, f.t);
             task_wait(Q, tf, r0, lane);
             const int d0 = dep_index(tf, n_sub, r0.a, r0.s);
             if (d0 >= 0) mark_acquired(f, d0);
         } else {
             if (lane == 0) {
-                ho[0] = T;
-                ho[1] = T;
+                ho[0] = NT;
+                ho[1] = NT;
                 ho[2] = 0;
             }
             pair_sync(bar_id);                          // nothing for B
         }
-        f_axis<0, 1>(f, sA[0], sS[0], fs0, sA, Q, tf, P);
-        f_axis<1, 1>(f, sA[1], sS[1], fs1, sA, Q, tf, P);
-        f_axis<2, MZ>(f, sA[2], sS[2], fs2, sA, Q, tf, P);
+        f_axis<T, 0, MXY>(f, sA[0], sS[0], fs0, sA, Q, tf, P);
+        f_axis<T, 1, MXY>(f, sA[1], sS[1], fs1, sA, Q, tf, P);
+        f_axis<T, 2, MZ>(f, sA[2], sS[2], fs2, sA, Q, tf, P);
     } else {
-        BState b;
+        BState<T> b;
         pair_sync(bar_id);                              // first hand-over
         b.t = ho[0];
         b.t_next = ho[1];
         b.paired = ho[2] != 0;
         b.x = handover[lane];
         b.k = 0;
-        b_axis<0, 1>(b, sA[0], sS[0], fs0, sA, Q, tf, P);
-        b_axis<1, 1>(b, sA[1], sS[1], fs1, sA, Q, tf, P);
-        b_axis<2, MZ>(b, sA[2], sS[2], fs2, sA, Q, tf, P);
+        b_axis<T, 0, MXY>(b, sA[0], sS[0], fs0, sA, Q, tf, P);
+        b_axis<T, 1, MXY>(b, sA[1], sS[1], fs1, sA, Q, tf, P);
+        b_axis<T, 2, MZ>(b, sA[2], sS[2], fs2, sA, Q, tf, P);
     }
 
     // sweep tasks exhausted for this warp: the step's epilogue

@@ -418,12 +418,12 @@ bfvm_status launch_axis(Ctx* c, const SweepArgs<T>& A)
         S.lo_a = c->d_lo_a[AXIS];
         S.cnt_a = c->d_cnt_a[AXIS];
         S.lo_b = c->d_lo_b[AXIS];
-        // FP64: one column buffer per warp pair (see sweep_pair.cuh)
+        // one column buffer per warp pair (see sweep_pair.cuh)
         const size_t per_pair = (size_t)32 * ns * sizeof(T) + 4 * 32 * sizeof(int64_t) +
                                 32 * sizeof(T);
         int pairs = (int)((c->smem_optin - fixed) / per_pair);
         if (pairs > 4) pairs = 4;
-        if (sizeof(T) == 8 && c->sweep_kernel == 0 && pairs >= 1) {
+        if (c->sweep_kernel == 0 && pairs >= 1) {
             size_t smem = fixed + per_pair * pairs;
             auto kern = persistent::k_sweep_pair<T, AXIS, MODE>;
             BFVM_CUDA(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -469,13 +469,17 @@ bfvm_status launch_axis(Ctx* c, const SweepArgs<T>& A)
     return BFVM_OK;
 }
 
-// The x, y and z sweeps of a rescaled FP64 step as one persistent launch
-// (sweep_step.cuh).  Returns BFVM_ESTATE without launching when the context
-// does not qualify (the caller then launches the axes one by one).
-bfvm_status launch_step_fused(Ctx* c, int p, bool renorm)
+// The x, y and z sweeps of a step as one persistent launch (sweep_step.cuh):
+// the rescaled FP64 form (MXY 1), the plain FP64 form and the FP32 form
+// (MXY 0).  Returns BFVM_ESTATE without launching when the context does not
+// qualify (the caller then launches the axes one by one).
+template <typename T, int MXY>
+bfvm_status launch_step_fused(Ctx* c, int p, bool renorm, const T* r, const T* cr,
+                              const T* cvec)
 {
     // also runs the step's Dirichlet shell and cell sources (its epilogue)
-    constexpr int G = persistent::Groups<double>::G;
+    constexpr int G = persistent::Groups<T>::G;
+    constexpr int NC = persistent::step_ncoef<T, MXY>();
     if (!c->fused_step || c->sweep_kernel != 0 || !c->d_task_first || !c->d_sched ||
         c->n_sub > 64 || c->dims != 3 || c->n_nodes > 0)
         return BFVM_ESTATE;
@@ -484,27 +488,20 @@ bfvm_status launch_step_fused(Ctx* c, int p, bool renorm)
     const int ext[3] = {c->nx, c->ny, c->nz};
     int ns = 0;
     for (int a = 0; a < 3; ++a) ns = std::max(ns, (int)ceil_div(ext[a], G) * G);
-    const size_t fixed =
-        ((3 * sizeof(SweepArgs<double>) + 3 * sizeof(persistent::LineSet) + 15) & ~(size_t)15) +
-        ((((size_t)3 * c->n_sub + 1) * sizeof(int) + 15) & ~(size_t)15) +
-                         (((size_t)3 * (c->n_sub + 1) * sizeof(int64_t) + 15) & ~(size_t)15) +
-        2 * (size_t)c->n_sub * c->coef.L * sizeof(double) +
-        (((size_t)c->n_sub * (sizeof(double) + sizeof(int)) + 15) & ~(size_t)15);
-    const size_t pair_bytes = (size_t)ns * 32 * sizeof(double) + 4 * 32 * sizeof(int64_t) +
-                              32 * sizeof(double) + 4 * sizeof(int) + 32 * sizeof(int);
-    if (c->smem_optin < fixed + pair_bytes) return BFVM_ESTATE;
-    int pairs = (int)((c->smem_optin - fixed) / pair_bytes);
+    const persistent::StepSmem M = persistent::step_smem<T>(c->n_sub, c->coef.L, NC, ns);
+    if (c->smem_optin < M.fixed + M.pair) return BFVM_ESTATE;
+    int pairs = (int)((c->smem_optin - M.fixed) / M.pair);
     if (pairs > 4) pairs = 4;
     // the per-axis launches stage one axis' coefficients only; where that
     // leaves room for more pairs, they are the faster choice
-    const size_t fixed_axis = (size_t)c->n_sub * 2 * ns * sizeof(double) + 1024;
-    const int pairs_axis = (int)std::min<size_t>(4, (c->smem_optin - fixed_axis) / pair_bytes);
+    const size_t fixed_axis = (size_t)c->n_sub * NC * ns * sizeof(T) + 1024;
+    const int pairs_axis = (int)std::min<size_t>(4, (c->smem_optin - fixed_axis) / M.pair);
     if (pairs < pairs_axis) return BFVM_ESTATE;
     KernelTimer timer(c, 4);
-    SweepArgs<double> A[3];
+    SweepArgs<T> A[3];
     persistent::LineSet S[3];
     for (int a = 0; a < 3; ++a) {
-        A[a] = make_args<double>(c, a, p, c->coef.r, c->coef.cr, c->coef.c);
+        A[a] = make_args<T>(c, a, p, r, cr, cvec);
         S[a].n_sub = c->n_sub;
         S[a].first = c->d_first[a];
         S[a].lo_a = c->d_lo_a[a];
@@ -531,14 +528,14 @@ bfvm_status launch_step_fused(Ctx* c, int p, bool renorm)
         n_epi += (c->bc_kind[s] == BFVM_BC_DIRICHLET ? persistent::epi_shell_chunks(c->nx, c->ny, c->nz) : 0) +
                  persistent::epi_src_chunks(n_seg);
     Q.n_epi_chunks = (int)n_epi;
-    persistent::EpiArgs E;
-    E.field = reinterpret_cast<double*>(c->field);
+    persistent::EpiArgs<T> E;
+    E.field = reinterpret_cast<T*>(c->field);
     E.nx = c->nx;
     E.ny = c->ny;
     E.nz = c->nz;
     E.pitch = c->pitch;
     E.L = c->coef.L;
-    E.sc = renorm ? nullptr : A[0].sc_p1;
+    E.sc = (MXY == 0 || renorm) ? nullptr : A[0].sc_p1;
     E.n_seg = n_seg;
     E.d_nseg = c->src.counts_on_host ? nullptr : c->src.d_count;
     E.off = c->src.off;
@@ -546,12 +543,13 @@ bfvm_status launch_step_fused(Ctx* c, int p, bool renorm)
     E.beta = c->src.beta;
     E.vox = c->src.vox;
     E.sub = c->src.sub;
-    const size_t smem = fixed + pair_bytes * pairs;
+    const size_t smem = M.fixed + M.pair * pairs;
     int64_t grid = ceil_div(std::max<int64_t>(c->n_tasks, 1), pairs);
     grid = std::max<int64_t>(grid, ceil_div(Q.n_epi_chunks, 8 * pairs));
     if (grid > c->sm_count) grid = c->sm_count;
     if (c->grid_limit > 0 && grid > c->grid_limit) grid = c->grid_limit;
-    auto kern = renorm ? persistent::k_step_pair<true> : persistent::k_step_pair<false>;
+    auto kern = persistent::k_step_pair<T, MXY, MXY>;
+    if (MXY == 1 && renorm) kern = persistent::k_step_pair<T, MXY, 2 * MXY>;
     BFVM_CUDA(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)smem));
     kern<<<(unsigned)grid, 64 * pairs, smem, c->stream>>>(A[0], A[1], A[2], S[0], S[1], S[2], Q,
@@ -771,20 +769,24 @@ bfvm_status launch_step(Ctx* c, int p, bool renorm)
 {
     bfvm_status st;
     if (c->precision == 32) {
-        st = launch_xyz<float, 0>(c, 0, c->coef.r32, c->coef.cr32, c->coef.c32);
+        st = launch_step_fused<float, 0>(c, 0, true, c->coef.r32, c->coef.cr32, c->coef.c32);
+        if (st == BFVM_OK) return BFVM_OK;
+        if (st == BFVM_ESTATE) st = launch_xyz<float, 0>(c, 0, c->coef.r32, c->coef.cr32, c->coef.c32);
         if (st != BFVM_OK) return st;
         if ((st = launch_shell_fill(c, -1)) != BFVM_OK) return st;
         if ((st = launch_nodes(c, 0, true, 3)) != BFVM_OK) return st;
         return launch_sources(c, 0, true);
     }
     if (c->variant == 0) {
-        st = launch_xyz<double, 0>(c, 0, c->coef.r, c->coef.cr, c->coef.c);
+        st = launch_step_fused<double, 0>(c, 0, true, c->coef.r, c->coef.cr, c->coef.c);
+        if (st == BFVM_OK) return BFVM_OK;
+        if (st == BFVM_ESTATE) st = launch_xyz<double, 0>(c, 0, c->coef.r, c->coef.cr, c->coef.c);
         if (st != BFVM_OK) return st;
         if ((st = launch_shell_fill(c, -1)) != BFVM_OK) return st;
         if ((st = launch_nodes(c, 0, true, 3)) != BFVM_OK) return st;
         return launch_sources(c, 0, true);
     }
-    st = launch_step_fused(c, p, renorm);
+    st = launch_step_fused<double, 1>(c, p, renorm, c->coef.r, c->coef.cr, c->coef.c);
     if (st == BFVM_OK) return BFVM_OK;   // sweeps, shell and sources in one launch
     if (st == BFVM_ESTATE) {
         if (renorm) st = launch_xyz<double, 2>(c, p, c->coef.r, c->coef.cr, c->coef.c);

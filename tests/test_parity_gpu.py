@@ -91,9 +91,14 @@ FUSED_CASES = ["ragged_37x45x50", "cube_33", "thin_1x1x7", "thin_2x3x1", "flat_6
                "long_z_260", "no_cells_3sub", "plain_50_fullsteps"]
 
 
+# (precision, variant): the rescaled and the plain FP64 form, the FP32 form
+FORMS = {"fp64_rescaled": (64, 1), "fp64_plain": (64, 0), "fp32": (32, 0)}
+
+
+@pytest.mark.parametrize("form", sorted(FORMS))
 @pytest.mark.parametrize("grid_limit", [0, 1, 2])
 @pytest.mark.parametrize("case", FUSED_CASES)
-def test_one_launch_step_matches_per_axis_launches(bf, case, grid_limit):
+def test_one_launch_step_matches_per_axis_launches(bf, case, grid_limit, form):
     """The step's three sweeps as one persistent launch (option 8) compute
     each line exactly as the per-axis launches do, so the fields agree bit
     for bit, and both agree with the oracle.  One or two CTAs make every
@@ -102,10 +107,12 @@ def test_one_launch_step_matches_per_axis_launches(bf, case, grid_limit):
     line lengths (non-cubic grids)."""
     p = CASES[case]()
     ref = oracle.run(p)
+    precision, variant = FORMS[form]
     outs = []
     for fused in (1, 0):
-        sim = bf.Sim.from_problem(p)
-        sim.set_option(bf.OPT_VARIANT, 1)
+        sim = bf.Sim.from_problem(p, precision=precision)
+        if precision == 64:
+            sim.set_option(bf.OPT_VARIANT, variant)
         sim.set_option(bf.OPT_SWEEP_KERNEL, 0)
         sim.set_option(bf.OPT_FUSED_STEP, fused)
         if grid_limit:
@@ -118,10 +125,12 @@ def test_one_launch_step_matches_per_axis_launches(bf, case, grid_limit):
         sim.close()
         assert launches > 0
     np.testing.assert_array_equal(outs[0], outs[1])
-    assert np.all(rel_inf(outs[0], ref) <= TOL64), rel_inf(outs[0], ref)
+    tol = TOL64 if precision == 64 else TOL32
+    assert np.all(rel_inf(outs[0].astype(np.float64), ref) <= tol), rel_inf(outs[0], ref)
 
 
-def test_one_launch_step_wait_gives_up_with_status(bf):
+@pytest.mark.parametrize("precision", [64, 32])
+def test_one_launch_step_wait_gives_up_with_status(bf, precision):
     """The dependency waits of the one-launch step are bounded: with option 9
     no wait can be satisfied, each gives up after a few polls, the kernel
     still finishes, and the next synchronising call reports BFVM_ETIMEOUT.
@@ -129,7 +138,7 @@ def test_one_launch_step_wait_gives_up_with_status(bf):
     p = inputs.make_problem(12, 10, 8, n_sub=1, D=[2e4], lam=[0.1], bc_kind=[0],
                             bc_value=[0.0], n_cells=20, U=[1.0], S=[0.5], rho_star=[2.0],
                             steps=2, seed=5)
-    sim = bf.Sim.from_problem(p)
+    sim = bf.Sim.from_problem(p, precision=precision)
     sim.set_option(bf.OPT_WAIT_TEST, 200)
     sim.step(1)
     with pytest.raises(bf.BfvmError) as ei:
@@ -137,11 +146,12 @@ def test_one_launch_step_wait_gives_up_with_status(bf):
     assert ei.value.status == 5
     sim.sync()                                   # the flag was cleared
     sim.set_option(bf.OPT_WAIT_TEST, 0)
-    sim.set_density(__import__("torch").as_tensor(p.rho0, device=sim.device))
+    torch = __import__("torch")
+    sim.set_density(torch.as_tensor(p.rho0, device=sim.device).to(sim.dtype))
     sim.step(p.steps)
-    got = sim.get_density().cpu().numpy()
+    got = sim.get_density().double().cpu().numpy()
     sim.close()
-    assert np.all(rel_inf(got, oracle.run(p)) <= TOL64)
+    assert np.all(rel_inf(got, oracle.run(p)) <= (TOL64 if precision == 64 else TOL32))
 
 
 def test_rescaled_across_periods_and_mid_period_reads(bf):
