@@ -236,13 +236,16 @@ bfvm_status bfvm_get_info(const bfvm_ctx* ctx, int64_t* info);
  *          (bfvm_step then launches kernels one by one, without graphs)
  *   key 6  cap on the CTAs of the persistent sweeps (0 = one per SM, the
  *          default); small caps make every warp walk many line blocks
- *   key 7  FP64 sweep kernel: 0 warp pairs sharing each line buffer (the
+ *   key 7  sweep kernel: 0 warp pairs sharing each line buffer (the
  *          default), 1 one warp per line buffer
- *   key 8  with the rescaled FP64 form and warp pairs: 1 (the default) runs
- *          the x, y and z sweeps of a step as one persistent launch whose
- *          warp pairs take (axis, substrate, 32-line block) tasks in order,
- *          a task starting once the previous axis of its substrate is
- *          complete; 0 launches one kernel per axis
+ *   key 8  with warp pairs (3-D grids, no Dirichlet nodes): the x, y and z
+ *          sweeps of a step, its Dirichlet shell and its cell sources as one
+ *          persistent launch whose warp pairs take (axis, substrate, 32-line
+ *          block) tasks in order, a task starting once the previous axis of
+ *          its substrate is complete.  1 (the default): where that launch
+ *          gets at least as many warp pairs per SM as the per-axis launches
+ *          (measured faster then for the FP64 forms; FP32 runs per axis); 2:
+ *          wherever it fits; 0: one launch per axis
  *   key 10 dimensions: 3 (the default) or 2, the 2-D variant of the step
  *          (the paper ports BioFVM's 2-D diffusion too): for an nx x ny x 1
  *          grid, an x-solve and a y-solve per step, each line matrix with

@@ -690,7 +690,7 @@ bfvm_status bfvm_set_option(bfvm_ctx* h, int32_t key, int64_t value)
             drop_graphs(c);
             return BFVM_OK;
         case 8:
-            if (value != 0 && value != 1) return set_err(c, BFVM_EINVAL, "fused step must be 0 or 1");
+            if (value < 0 || value > 2) return set_err(c, BFVM_EINVAL, "fused step must be 0, 1 or 2");
             c->fused_step = (int)value;
             drop_graphs(c);
             return BFVM_OK;

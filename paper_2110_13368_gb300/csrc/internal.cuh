@@ -102,7 +102,7 @@ struct Ctx {
     int use_graphs = 1;
     int grid_limit = 0;           // cap on persistent sweep CTAs (0 = one per SM)
     int sweep_kernel = 0;         // FP64: 0 warp pairs, 1 one warp per buffer
-    int fused_step = 1;           // FP64 rescaled pairs: 1 one launch for x, y, z
+    int fused_step = 1;           // one launch for x, y, z: 0 never, 1 when not fewer pairs, 2 always
     int dims = 3;                 // 2: the 2-D variant (nz == 1; x and y sweeps,
                                   // lambda dt / 2 each, four-edge Dirichlet shell)
     // Dirichlet nodes inside the domain (bfvm_set_dirichlet_nodes): one per

@@ -30,7 +30,7 @@ template <typename T, int AXIS, int MODE>
 struct PairSweeper {
     static constexpr int G = Groups<T>::G;
     static constexpr int ROWS = Groups<T>::ROWS;
-    static constexpr int LG = Groups<T>::LAG_GROUPS;
+    static constexpr int LG = Groups<T>::PAIR_LAG;   // copy-ahead distance of F, in groups
 
     const SweepArgs<T>& A;
     T* W;
@@ -334,7 +334,7 @@ struct PairSweeper {
 // [MODE 2 output scales] [line-set prefix] [per pair: column buffer,
 // 2 x 32 row bases of each warp (4 x 32), 32 chain hand-over values].
 template <typename T, int AXIS, int MODE>
-__global__ void __launch_bounds__(256, 1) k_sweep_pair(SweepArgs<T> A, LineSet S,
+__global__ void __launch_bounds__(64 * Groups<T>::MAX_PAIRS, 1) k_sweep_pair(SweepArgs<T> A, LineSet S,
                                                        int64_t n_blocks, int n_slots)
 {
     constexpr int G = Groups<T>::G;

@@ -49,6 +49,16 @@ struct Groups {
     static constexpr int G = 8;
     static constexpr int ROWS = 32 / G;             // rows per transposed instruction
     static constexpr int LAG_GROUPS = sizeof(T) == 8 ? 3 : 4;
+    // copy-ahead distance of a warp pair's F warp (sweep_pair.cuh); measured
+    // on the 200^3 step: FP64 3 groups (2: 1.5 % slower, 1: 40 % slower),
+    // FP32 4 (8: 4 % slower)
+    static constexpr int PAIR_LAG = sizeof(T) == 8 ? 3 : 4;
+    // most warp pairs per CTA of the pair kernels (per-axis and one-launch):
+    // FP64 is bound by the FP64 pipe with two pairs' warps per SMSP; the FP32
+    // sweeps are latency-bound and take more warps.  Measured on the 200^3
+    // FP32 step: 4 pairs 0.224 ms, 5 pairs 0.210 ms, 6 pairs 0.166 ms,
+    // 8 pairs 0.192 ms.
+    static constexpr int MAX_PAIRS = sizeof(T) == 8 ? 4 : 6;
 };
 
 // Lines of one axis that need a solve, substrate by substrate: for a

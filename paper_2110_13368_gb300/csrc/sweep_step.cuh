@@ -588,7 +588,7 @@ __device__ __forceinline__ int axis_groups(const SweepArgs<T>* sA, int a)
 template <typename T>
 __device__ __forceinline__ int phase_iters(const SweepArgs<T>* sA, int a_f, int a_b)
 {
-    constexpr int LG = Groups<T>::LAG_GROUPS;
+    constexpr int LG = Groups<T>::PAIR_LAG;
     return max(axis_groups(sA, a_f) + LG, axis_groups(sA, a_b));
 }
 
@@ -781,7 +781,7 @@ __host__ __device__ constexpr int step_ncoef()
 // plain, 1 rescaled); MZ: form of the z sweep (MXY, or 2: rescaled and
 // renormalising).
 template <typename T, int MXY, int MZ>
-__global__ void __launch_bounds__(256, 1)
+__global__ void __launch_bounds__(64 * Groups<T>::MAX_PAIRS, 1)
     k_step_pair(SweepArgs<T> A0, SweepArgs<T> A1, SweepArgs<T> A2, LineSet S0, LineSet S1,
                 LineSet S2, StepSched Q, EpiArgs<T> E, int n_slots)
 {

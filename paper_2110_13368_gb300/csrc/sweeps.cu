@@ -422,7 +422,7 @@ bfvm_status launch_axis(Ctx* c, const SweepArgs<T>& A)
         const size_t per_pair = (size_t)32 * ns * sizeof(T) + 4 * 32 * sizeof(int64_t) +
                                 32 * sizeof(T);
         int pairs = (int)((c->smem_optin - fixed) / per_pair);
-        if (pairs > 4) pairs = 4;
+        if (pairs > persistent::Groups<T>::MAX_PAIRS) pairs = persistent::Groups<T>::MAX_PAIRS;
         if (c->sweep_kernel == 0 && pairs >= 1) {
             size_t smem = fixed + per_pair * pairs;
             auto kern = persistent::k_sweep_pair<T, AXIS, MODE>;
@@ -490,13 +490,20 @@ bfvm_status launch_step_fused(Ctx* c, int p, bool renorm, const T* r, const T* c
     for (int a = 0; a < 3; ++a) ns = std::max(ns, (int)ceil_div(ext[a], G) * G);
     const persistent::StepSmem M = persistent::step_smem<T>(c->n_sub, c->coef.L, NC, ns);
     if (c->smem_optin < M.fixed + M.pair) return BFVM_ESTATE;
+    constexpr int MAXP = persistent::Groups<T>::MAX_PAIRS;
     int pairs = (int)((c->smem_optin - M.fixed) / M.pair);
-    if (pairs > 4) pairs = 4;
+    if (pairs > MAXP) pairs = MAXP;
     // the per-axis launches stage one axis' coefficients only; where that
     // leaves room for more pairs, they are the faster choice
     const size_t fixed_axis = (size_t)c->n_sub * NC * ns * sizeof(T) + 1024;
-    const int pairs_axis = (int)std::min<size_t>(4, (c->smem_optin - fixed_axis) / M.pair);
-    if (pairs < pairs_axis) return BFVM_ESTATE;
+    const int pairs_axis = (int)std::min<size_t>(persistent::Groups<T>::MAX_PAIRS,
+                                                 (c->smem_optin - fixed_axis) / M.pair);
+    if (c->fused_step != 2) {
+        if (pairs < pairs_axis) return BFVM_ESTATE;
+        // FP32: the per-axis launches measured faster at equal pair counts
+        // (200^3 step 0.166 ms against 0.194 ms in one launch)
+        if (sizeof(T) == 4) return BFVM_ESTATE;
+    }
     KernelTimer timer(c, 4);
     SweepArgs<T> A[3];
     persistent::LineSet S[3];

@@ -32,7 +32,7 @@ def _moved(p, rng, step_um):
 
 
 @pytest.mark.parametrize("precision,variant,tol", [(64, 1, 1e-12), (64, 0, 1e-12), (32, None, 1e-5)])
-@pytest.mark.parametrize("fused", [1, 0])
+@pytest.mark.parametrize("fused", [2, 0])
 def test_cells_move_every_few_steps(bf, precision, variant, tol, fused):
     import torch
     rng = np.random.default_rng(8)

@@ -108,8 +108,8 @@ def test_one_launch_step_matches_per_axis_launches(bf, case, grid_limit, form):
     p = CASES[case]()
     ref = oracle.run(p)
     precision, variant = FORMS[form]
-    outs = []
-    for fused in (1, 0):
+    outs, counts = [], []
+    for fused in (2, 0):
         sim = bf.Sim.from_problem(p, precision=precision)
         if precision == 64:
             sim.set_option(bf.OPT_VARIANT, variant)
@@ -122,8 +122,10 @@ def test_one_launch_step_matches_per_axis_launches(bf, case, grid_limit, form):
         sim.sync()
         launches = sim.info()["launches"] - n0
         outs.append(sim.get_density().cpu().numpy())
+        counts.append(launches)
         sim.close()
         assert launches > 0
+    assert counts[0] < counts[1]                 # the one launch ran
     np.testing.assert_array_equal(outs[0], outs[1])
     tol = TOL64 if precision == 64 else TOL32
     assert np.all(rel_inf(outs[0].astype(np.float64), ref) <= tol), rel_inf(outs[0], ref)
@@ -139,6 +141,9 @@ def test_one_launch_step_wait_gives_up_with_status(bf, precision):
                             bc_value=[0.0], n_cells=20, U=[1.0], S=[0.5], rho_star=[2.0],
                             steps=2, seed=5)
     sim = bf.Sim.from_problem(p, precision=precision)
+    with pytest.raises(bf.BfvmError):
+        sim.set_option(bf.OPT_FUSED_STEP, 3)
+    sim.set_option(bf.OPT_FUSED_STEP, 2)
     sim.set_option(bf.OPT_WAIT_TEST, 200)
     sim.step(1)
     with pytest.raises(bf.BfvmError) as ei:
