@@ -253,8 +253,8 @@ def measure_forms(args, plain_ups, dev, stream, flush):
             "speedup_vs_plain_fp64_tumour": (n_upd * K / (msb / 1e3)) / plain_ups,
             "steps": K}
     # 2-D variant: a 1000 x 1000 x 1 x 2 grid, oxygen Dirichlet + a
-    # zero-flux factor, 20k cells (lines of 1000 voxels: the one-thread-per-
-    # line sweep that keeps the intermediates in the field)
+    # zero-flux factor, 20k cells (2000 lines of 1000 voxels per axis: the
+    # split line solve, 16-voxel segments joined through their end values)
     p2 = inputs.make_problem(1000, 1000, 1, n_sub=2, D=[1e5, 1e3], lam=[0.1, 0.01],
                              bc_kind=[1, 0], bc_value=[38.0, 0.0], field_mode="zero",
                              n_cells=20_000, U=[10.0, 0.0], S=[0.0, 10.0],
@@ -265,7 +265,7 @@ def measure_forms(args, plain_ups, dev, stream, flush):
     s2.close()
     ups2 = p2.updates_per_step * K / (ms2 / 1e3)
     out["two_d"] = {"value": ups2, "grid": [p2.nx, p2.ny, 1], "n_sub": 2, "steps": K,
-                    "form": "plain Thomas, x and y sweeps", "ratio_vs_plain_fp64_3d": ups2 / plain_ups,
+                    "form": "plain Thomas, x and y sweeps, split line solve", "ratio_vs_plain_fp64_3d": ups2 / plain_ups,
                     "hbm_frac_32B_per_update": ups2 * 4 * 8 / 1e9 / peaks()[0]}
     # Dirichlet nodes: the 200^3 x 2 workload with 40 vessel columns of
     # oxygen nodes (per-axis launches plus node fills)

@@ -254,6 +254,12 @@ bfvm_status bfvm_get_info(const bfvm_ctx* ctx, int64_t* info);
  *          3-D with V_vox = dx^3.  Needs nz == 1; FP64 then runs the plain
  *          Thomas form (option 1 = 0).  2-D contexts cannot record for the
  *          adjoint or join a batch (BFVM_ESTATE).
+ *   key 11 split line solve of the plain form (the FP32 form, FP64 with
+ *          key 1 = 0, and the 2-D variant): each line cut into segments
+ *          solved in parallel, joined through the affine form of the two
+ *          Thomas recurrences (three launches per axis).  1 (the default):
+ *          for the 2-D variant and for lines too long for the shared-memory
+ *          sweeps; 2: every plain-form sweep of a step; 0: never
  *   key 9  test of the bounded device waits of key 8's launch: a value
  *          v > 0 makes every dependency wait unreachable and give up after
  *          v polls, so the next synchronising call reports BFVM_ETIMEOUT

@@ -33,6 +33,7 @@ OPT_SWEEP_KERNEL = 7
 OPT_FUSED_STEP = 8
 OPT_WAIT_TEST = 9
 OPT_DIMS = 10
+OPT_SPLIT = 11
 
 EXPORTED = ["bfvm_create", "bfvm_destroy", "bfvm_set_density", "bfvm_get_density",
             "bfvm_set_cells", "bfvm_step", "bfvm_sync", "bfvm_record", "bfvm_backward",

@@ -699,6 +699,11 @@ bfvm_status bfvm_set_option(bfvm_ctx* h, int32_t key, int64_t value)
             c->wait_test_polls = (int)value;
             drop_graphs(c);
             return BFVM_OK;
+        case 11:
+            if (value < 0 || value > 2) return set_err(c, BFVM_EINVAL, "split solve must be 0, 1 or 2");
+            c->split = (int)value;
+            drop_graphs(c);
+            return BFVM_OK;
         case 10: {
             if (value != 2 && value != 3) return set_err(c, BFVM_EINVAL, "dims must be 2 or 3");
             if (value == c->dims) return BFVM_OK;

@@ -19,6 +19,8 @@
 // through a linear solve untouched, which is what keeps the scale separable.
 #include <math.h>
 
+#include <algorithm>
+
 #include "internal.cuh"
 
 namespace bfvm {
@@ -129,6 +131,46 @@ static int rescale_period(const Ctx* c)
     return m;
 }
 
+// Split line solve: prefix and suffix products of cr within the segments of
+// one axis, one thread per (substrate, segment), in FP64.
+__global__ void k_split_products(const double* cr, double* sg, double* sl, int n_sub,
+                                 int64_t L, int off, int n, int m)
+{
+    const int n_seg = (n + m - 1) / m;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_sub * n_seg) return;
+    const int s = t / n_seg, q = t % n_seg;
+    const int k0 = q * m, k1 = min(n, k0 + m);
+    const int64_t row = (int64_t)s * L + off;
+    double p = 1.0;
+    for (int k = k0; k < k1; ++k) {
+        p *= cr[row + k];
+        sg[row + k] = p;
+    }
+    p = 1.0;
+    for (int k = k1 - 1; k >= k0; --k) {
+        p *= cr[row + k];
+        sl[row + k] = p;
+    }
+}
+
+// Segment length of the split solve along an axis with n elements per line
+// and `lines` lines: enough segments for about 1024 threads per SM, at most
+// 64 segments unless that makes them longer than 64 elements (the x tile),
+// at least 8 elements each.
+int split_segment_length(int n, int64_t lines, int sm_count)
+{
+    const int64_t target = (int64_t)std::max(sm_count, 1) * 1024;
+    int64_t P = (target + lines - 1) / std::max<int64_t>(lines, 1);
+    if (P > 64) P = 64;
+    if (P < 1) P = 1;
+    int m = (int)((n + P - 1) / P);
+    if (m > 64) m = 64;
+    if (m < 8) m = 8;
+    if (m > n) m = n;
+    return std::max(m, 1);
+}
+
 bfvm_status build_coefficients(Ctx* c)
 {
     free_coefficients(c);
@@ -169,6 +211,34 @@ bfvm_status build_coefficients(Ctx* c)
     BFVM_CUDA(c, cudaGetLastError());
     c->launches += 4;
 
+    // split line solve tables and exchange buffer
+    BFVM_CUDA(c, cudaMalloc(&T.sg, sizeof(double) * n_tab));
+    BFVM_CUDA(c, cudaMalloc(&T.sl, sizeof(double) * n_tab));
+    BFVM_CUDA(c, cudaMalloc(&T.sg32, sizeof(float) * 2 * n_tab));
+    BFVM_CUDA(c, cudaMalloc(&T.sl32, sizeof(float) * 2 * n_tab));
+    {
+        const int ext[3] = {c->nx, c->ny, c->nz};
+        int64_t ex_elems = 0;
+        for (int a = 0; a < 3; ++a) {
+            const int64_t lines = (int64_t)ext[0] * ext[1] * ext[2] / ext[a] * c->n_sub;
+            const int m = split_segment_length(ext[a], lines, c->sm_count);
+            T.seg[a] = m;
+            const int n_seg = (ext[a] + m - 1) / m;
+            ex_elems = std::max(ex_elems, 2 * lines * n_seg);
+            const int nt_s = c->n_sub * n_seg;
+            k_split_products<<<ceil_div(nt_s, 64), 64, 0, c->stream>>>(T.cr, T.sg, T.sl, c->n_sub,
+                                                                       T.L, P.off[a], ext[a], m);
+            c->launches += 1;
+        }
+        BFVM_CUDA(c, cudaGetLastError());
+        k_split32<<<ceil_div(n_tab, blk), blk, 0, c->stream>>>(T.sg, T.sg32, n_tab);
+        k_split32<<<ceil_div(n_tab, blk), blk, 0, c->stream>>>(T.sl, T.sl32, n_tab);
+        BFVM_CUDA(c, cudaGetLastError());
+        c->launches += 2;
+        const size_t esz = c->precision == 64 ? sizeof(double) : sizeof(float);
+        BFVM_CUDA(c, cudaMalloc(&T.split_ex, esz * (size_t)std::max<int64_t>(ex_elems, 1)));
+    }
+
     if (c->precision == 64) {
         int m = rescale_period(c);
         T.period = m;
@@ -192,7 +262,8 @@ bfvm_status build_coefficients(Ctx* c)
 void free_coefficients(Ctx* c)
 {
     CoefTables& T = c->coef;
-    void* ptrs[] = {T.r, T.cr, T.c, T.r32, T.cr32, T.c32, T.fa, T.fb, T.sc, T.isc};
+    void* ptrs[] = {T.r, T.cr, T.c, T.r32, T.cr32, T.c32, T.fa, T.fb, T.sc, T.isc,
+                    T.sg, T.sl, T.sg32, T.sl32, T.split_ex};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     T = CoefTables();

@@ -37,6 +37,18 @@ struct CoefTables {
     double* isc = nullptr;  // 1 / sc
     int period = 0;         // number of states p
     int64_t L = 0;
+    // split (partitioned) line solve of the plain form: segments of seg[a]
+    // elements along axis a; within each segment the prefix products
+    // sg[k] = prod_{j = k0..k} cr_j and suffix products sl[k] = prod_{j =
+    // k..k1-1} cr_j ([s][L]; FP32 as hi + lo blocks like cr32), and the
+    // exchange buffer of the segments' end values (2 x lines x segments
+    // elements of the field type)
+    int seg[3] = {0, 0, 0};
+    double* sg = nullptr;
+    double* sl = nullptr;
+    float* sg32 = nullptr;
+    float* sl32 = nullptr;
+    void* split_ex = nullptr;
 };
 
 // Binned cells: every voxel that holds at least one cell, with its cells'
@@ -101,7 +113,8 @@ struct Ctx {
     int fuse_sources = 0;
     int use_graphs = 1;
     int grid_limit = 0;           // cap on persistent sweep CTAs (0 = one per SM)
-    int sweep_kernel = 0;         // FP64: 0 warp pairs, 1 one warp per buffer
+    int sweep_kernel = 0;         // 0 warp pairs, 1 one warp per buffer
+    int split = 1;                // split line solve: 0 never, 1 auto, 2 always (plain form)
     int fused_step = 1;           // one launch for x, y, z: 0 never, 1 when not fewer pairs, 2 always
     int dims = 3;                 // 2: the 2-D variant (nz == 1; x and y sweeps,
                                   // lambda dt / 2 each, four-edge Dirichlet shell)

@@ -351,6 +351,7 @@ __global__ void k_sources(T* __restrict__ field, int64_t n_entries, const int64_
 #include "sweep_persistent.cuh"
 #include "sweep_pair.cuh"
 #include "sweep_step.cuh"
+#include "sweep_split.cuh"
 
 namespace bfvm {
 namespace {
@@ -392,6 +393,42 @@ SweepArgs<T> make_args(Ctx* c, int axis, int p, const T* r, const T* cr,
     return A;
 }
 
+// The split line solve of one axis (sweep_split.cuh): three launches.
+template <typename T, int AXIS>
+bfvm_status launch_split(Ctx* c, const SweepArgs<T>& A)
+{
+    split::SplitArgs Z;
+    Z.seg = c->coef.seg[AXIS];
+    if (Z.seg < 1 || !c->coef.split_ex) return set_err(c, BFVM_ESTATE, "split tables missing");
+    Z.n_seg = (int)ceil_div(A.n, Z.seg);
+    Z.sg = c->coef.sg;
+    Z.sl = c->coef.sl;
+    Z.sg32 = c->coef.sg32;
+    Z.sl32 = c->coef.sl32;
+    Z.n_tab = (int64_t)c->n_sub * c->coef.L;
+    Z.ex = c->coef.split_ex;
+    if (A.n_lines == 0) return BFVM_OK;
+    // x lines: whole warps per segment and a staging tile of 32 x (seg + 1)
+    // elements per warp (seg <= 64, so at least 2 warps fit in 48 KB)
+    const int64_t lines = AXIS == 0 ? ceil_div(A.n_lines, 32) * 32 : A.n_lines;
+    const int64_t nt = lines * Z.n_seg;
+    int block = 256;
+    size_t smem = 0;
+    if (AXIS == 0) {
+        const size_t tile = (size_t)32 * (Z.seg + 1) * sizeof(T);
+        const int warps = (int)std::min<size_t>(8, std::max<size_t>(1, (48 << 10) / tile));
+        block = 32 * warps;
+        smem = tile * warps;
+    }
+    const unsigned grid = (unsigned)ceil_div(nt, block);
+    split::k_split_fwd<T, AXIS><<<grid, block, smem, c->stream>>>(A, Z);
+    split::k_split_bwd<T, AXIS><<<grid, block, smem, c->stream>>>(A, Z);
+    split::k_split_out<T, AXIS><<<grid, block, smem, c->stream>>>(A, Z);
+    c->launches += 3;
+    BFVM_CUDA(c, cudaGetLastError());
+    return BFVM_OK;
+}
+
 template <typename T, int AXIS, int MODE, int DIR = 0>
 bfvm_status launch_axis(Ctx* c, const SweepArgs<T>& A)
 {
@@ -408,6 +445,12 @@ bfvm_status launch_axis(Ctx* c, const SweepArgs<T>& A)
         warps = (int)((c->smem_optin - fixed) / per_warp);
     if (warps > max_warps) warps = max_warps;
     KernelTimer timer(c, AXIS);
+    // plain-form step sweeps: the split solve where one thread or one
+    // 32-line block per line cannot fill the GPU (the 2-D variant) or the
+    // lines do not fit the shared-memory kernels
+    if (MODE == 0 && DIR == 0 &&
+        (c->split == 2 || (c->split == 1 && (c->dims == 2 || warps < 1))))
+        return launch_split<T, AXIS>(c, A);
     if (warps >= 1) {
         const int64_t* first = c->lines_first[AXIS];
         if (first[A.n_sub] == 0) return BFVM_OK;   // every line is on the shell

@@ -320,17 +320,19 @@ CASES_2D = {
 }
 
 
-@pytest.mark.parametrize("grid_limit", [0, 2])
+@pytest.mark.parametrize("split,grid_limit", [(1, 0), (0, 0), (0, 2)])
 @pytest.mark.parametrize("precision,tol", [(64, TOL64), (32, TOL32)])
 @pytest.mark.parametrize("case", sorted(CASES_2D))
-def test_2d_variant_matches_oracle(bf, case, precision, tol, grid_limit):
+def test_2d_variant_matches_oracle(bf, case, precision, tol, split, grid_limit):
     """The 2-D variant (option 10): x and y sweeps with half the decay each
     and the four-edge Dirichlet shell, against the 2-D oracle; lines from 1
-    voxel to longer than shared memory (the generic one-thread-per-line
-    sweep)."""
+    voxel to longer than shared memory.  split 1 (the default) runs the
+    split line solve, split 0 the warp-pair and one-thread-per-line sweeps
+    (grid_limit 2 makes their pairs walk many blocks)."""
     p = CASES_2D[case]()
     ref = oracle.run(p)
     sim = bf.Sim.from_problem(p, precision=precision)
+    sim.set_option(bf.OPT_SPLIT, split)
     if grid_limit:
         sim.set_option(bf.OPT_GRID_LIMIT, grid_limit)
     info = sim.info()
@@ -340,6 +342,42 @@ def test_2d_variant_matches_oracle(bf, case, precision, tol, grid_limit):
     sim.close()
     err = rel_inf(got, ref)
     assert np.all(err <= tol), (case, precision, err)
+
+
+@pytest.mark.parametrize("precision,tol", [(64, TOL64), (32, TOL32)])
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_split_line_solve_matches_oracle(bf, case, precision, tol):
+    """The split line solve (option 11 = 2) on every 3-D case of the plain
+    forms: segments of 8 elements or more (ragged last segments, single
+    segments for short lines, up to 38 segments for 300-voxel lines), whole
+    shell lines, Dirichlet ends; each axis is joined through the segments'
+    end values, so any slip in the scans or the tabulated products shows
+    against the oracle."""
+    p = CASES[case]()
+    ref = oracle.run(p)
+    sim = bf.Sim.from_problem(p, precision=precision)
+    if precision == 64:
+        sim.set_option(bf.OPT_VARIANT, 0)
+        sim.set_option(bf.OPT_FUSED_STEP, 0)
+    sim.set_option(bf.OPT_SPLIT, 2)
+    n0 = sim.info()["launches"]
+    sim.step(p.steps)
+    sim.sync()
+    launches = sim.info()["launches"] - n0
+    got = sim.get_density().double().cpu().numpy()
+    sim.close()
+    assert launches >= 9 * p.steps                # three per axis
+    err = rel_inf(got, ref)
+    assert np.all(err <= tol), (case, precision, err)
+
+
+def test_split_option_rules(bf):
+    sim = bf.Sim.from_problem(mixed(6, 5, 4))
+    for bad in (-1, 3):
+        with pytest.raises(bf.BfvmError) as ei:
+            sim.set_option(bf.OPT_SPLIT, bad)
+        assert ei.value.status == 1
+    sim.close()
 
 
 def test_2d_variant_option_rules(bf):
