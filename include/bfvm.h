@@ -259,7 +259,7 @@ bfvm_status bfvm_get_info(const bfvm_ctx* ctx, int64_t* info);
  *          solved in parallel, joined through the affine form of the two
  *          Thomas recurrences (three launches per axis).  1 (the default):
  *          for the 2-D variant and for lines too long for the shared-memory
- *          sweeps; 2: every plain-form sweep of a step; 0: never
+ *          sweeps; 2: every plain-form sweep, the adjoint's included; 0: never
  *   key 9  test of the bounded device waits of key 8's launch: a value
  *          v > 0 makes every dependency wait unreachable and give up after
  *          v polls, so the next synchronising call reports BFVM_ETIMEOUT

@@ -31,6 +31,10 @@
 // a warp never straddles two segments.
 // In FP32 every table is an unevaluated hi + lo pair and every update a
 // compensated multiply-add (comp_axpy), as in the other FP32 sweeps.
+// DIR as in the one-thread-per-line sweep: 0 the step (Dirichlet ends set
+// before and after the solve); 1 ends set before only, raw solution kept;
+// 2 ends of the input zeroed, raw solution kept (the adjoint's solves, which
+// also read from A.in and write to A.field).
 #pragma once
 
 namespace bfvm {
@@ -147,15 +151,17 @@ __device__ __forceinline__ bool split_thread(const SweepArgs<T>& A, const SplitA
 }
 
 // Element k of this thread's segment: the staged tile row (x) or the field
+// (read from src, written to f)
 template <typename T, int AXIS>
 struct SegView {
-    T* f;          // field at the line's base
+    T* f;          // output field at the line's base
+    const T* src;  // input at the line's base
     int64_t stride;
     T* row;        // tile row of this lane (x)
     int k0;
     __device__ __forceinline__ T get(int k) const
     {
-        return AXIS == 0 ? row[k - k0] : f[k * stride];
+        return AXIS == 0 ? row[k - k0] : src[k * stride];
     }
     __device__ __forceinline__ void put(int k, T v) const
     {
@@ -165,7 +171,7 @@ struct SegView {
 };
 
 // 1. forward elimination of each segment from a zero incoming value
-template <typename T, int AXIS>
+template <typename T, int AXIS, int DIR>
 __global__ void __launch_bounds__(256) k_split_fwd(SweepArgs<T> A, SplitArgs Z)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -179,18 +185,20 @@ __global__ void __launch_bounds__(256) k_split_fwd(SweepArgs<T> A, SplitArgs Z)
     const int k0 = q * Z.seg, k1 = min(n, k0 + Z.seg);
     const int lane = threadIdx.x & 31, ld = Z.seg + 1;
     T* tile = reinterpret_cast<T*>(smem_raw) + (threadIdx.x >> 5) * 32 * ld;
-    const SegView<T, AXIS> V{A.field + L.base, L.stride, tile + lane * ld, k0};
-    if (AXIS == 0) tile_copy<T, true>(A.field, tile, ld, L.base, active, k0, k1 - k0, lane);
-    if (active && L.all_shell) {
+    const SegView<T, AXIS> V{A.field + L.base, A.in + L.base, L.stride, tile + lane * ld, k0};
+    const double vin = DIR == 2 ? 0.0 : L.v;   // Dirichlet input value
+    if (AXIS == 0)
+        tile_copy<T, true>(const_cast<T*>(A.in), tile, ld, L.base, active, k0, k1 - k0, lane);
+    if (active && L.all_shell && DIR != 1) {
         // the whole line is on the Dirichlet shell: the value, no solve
-        for (int k = k0; k < k1; ++k) V.put(k, (T)L.v);
+        for (int k = k0; k < k1; ++k) V.put(k, (T)vin);
     } else if (active) {
         const int64_t row = (int64_t)L.s * A.L + A.axis_off;
         const T c = A.cvec[L.s * 3 + AXIS];
         T prev = (T)0;
         for (int k = k0; k < k1; ++k) {
             T d = V.get(k);
-            if (L.dir && (k == 0 || k == n - 1)) d = (T)L.v;
+            if (L.all_shell || (L.dir && (k == 0 || k == n - 1))) d = (T)vin;
             if (sizeof(T) == 8) {
                 prev = (T)(fma((double)c, (double)prev, (double)d) * (double)A.r[row + k]);
             } else {
@@ -209,7 +217,7 @@ __global__ void __launch_bounds__(256) k_split_fwd(SweepArgs<T> A, SplitArgs Z)
 }
 
 // 2. incoming d' of each segment, then its back substitution from zero
-template <typename T, int AXIS>
+template <typename T, int AXIS, int DIR>
 __global__ void __launch_bounds__(256) k_split_bwd(SweepArgs<T> A, SplitArgs Z)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -219,12 +227,12 @@ __global__ void __launch_bounds__(256) k_split_bwd(SweepArgs<T> A, SplitArgs Z)
     bool active;
     if (!split_thread<T, AXIS>(A, Z, t, q, line, active)) return;
     const SplitLine L = split_line<T, AXIS>(A, line);
-    const bool solve = active && !L.all_shell;    // shell lines were written in pass 1
+    const bool solve = active && !(L.all_shell && DIR != 1);   // else written in pass 1
     const int n = A.n;
     const int k0 = q * Z.seg, k1 = min(n, k0 + Z.seg);
     const int lane = threadIdx.x & 31, ld = Z.seg + 1;
     T* tile = reinterpret_cast<T*>(smem_raw) + (threadIdx.x >> 5) * 32 * ld;
-    const SegView<T, AXIS> V{A.field + L.base, L.stride, tile + lane * ld, k0};
+    const SegView<T, AXIS> V{A.field + L.base, A.field + L.base, L.stride, tile + lane * ld, k0};
     if (AXIS == 0) tile_copy<T, true>(A.field, tile, ld, L.base, solve, k0, k1 - k0, lane);
     if (solve) {
         const int64_t row = (int64_t)L.s * A.L + A.axis_off;
@@ -254,7 +262,7 @@ __global__ void __launch_bounds__(256) k_split_bwd(SweepArgs<T> A, SplitArgs Z)
 }
 
 // 3. incoming x of each segment, the solution, and the Dirichlet ends
-template <typename T, int AXIS>
+template <typename T, int AXIS, int DIR>
 __global__ void __launch_bounds__(256) k_split_out(SweepArgs<T> A, SplitArgs Z)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -264,12 +272,12 @@ __global__ void __launch_bounds__(256) k_split_out(SweepArgs<T> A, SplitArgs Z)
     bool active;
     if (!split_thread<T, AXIS>(A, Z, t, q, line, active)) return;
     const SplitLine L = split_line<T, AXIS>(A, line);
-    const bool solve = active && !L.all_shell;
+    const bool solve = active && !(L.all_shell && DIR != 1);
     const int n = A.n;
     const int k0 = q * Z.seg, k1 = min(n, k0 + Z.seg);
     const int lane = threadIdx.x & 31, ld = Z.seg + 1;
     T* tile = reinterpret_cast<T*>(smem_raw) + (threadIdx.x >> 5) * 32 * ld;
-    const SegView<T, AXIS> V{A.field + L.base, L.stride, tile + lane * ld, k0};
+    const SegView<T, AXIS> V{A.field + L.base, A.field + L.base, L.stride, tile + lane * ld, k0};
     if (AXIS == 0) tile_copy<T, true>(A.field, tile, ld, L.base, solve, k0, k1 - k0, lane);
     if (solve) {
         const int64_t row = (int64_t)L.s * A.L + A.axis_off;
@@ -281,7 +289,7 @@ __global__ void __launch_bounds__(256) k_split_out(SweepArgs<T> A, SplitArgs Z)
                             exC[(int64_t)j * A.n_lines + line]);
         for (int k = k0; k < k1; ++k) {
             T x = tab_axpy<T>(Z.sl, Z.sl32, Z.n_tab, row + k, X, V.get(k));
-            if (L.dir && (k == 0 || k == n - 1)) x = (T)L.v;
+            if (DIR == 0 && L.dir && (k == 0 || k == n - 1)) x = (T)L.v;
             V.put(k, x);
         }
     }

@@ -394,7 +394,7 @@ SweepArgs<T> make_args(Ctx* c, int axis, int p, const T* r, const T* cr,
 }
 
 // The split line solve of one axis (sweep_split.cuh): three launches.
-template <typename T, int AXIS>
+template <typename T, int AXIS, int DIR>
 bfvm_status launch_split(Ctx* c, const SweepArgs<T>& A)
 {
     split::SplitArgs Z;
@@ -421,9 +421,9 @@ bfvm_status launch_split(Ctx* c, const SweepArgs<T>& A)
         smem = tile * warps;
     }
     const unsigned grid = (unsigned)ceil_div(nt, block);
-    split::k_split_fwd<T, AXIS><<<grid, block, smem, c->stream>>>(A, Z);
-    split::k_split_bwd<T, AXIS><<<grid, block, smem, c->stream>>>(A, Z);
-    split::k_split_out<T, AXIS><<<grid, block, smem, c->stream>>>(A, Z);
+    split::k_split_fwd<T, AXIS, DIR><<<grid, block, smem, c->stream>>>(A, Z);
+    split::k_split_bwd<T, AXIS, DIR><<<grid, block, smem, c->stream>>>(A, Z);
+    split::k_split_out<T, AXIS, DIR><<<grid, block, smem, c->stream>>>(A, Z);
     c->launches += 3;
     BFVM_CUDA(c, cudaGetLastError());
     return BFVM_OK;
@@ -445,12 +445,14 @@ bfvm_status launch_axis(Ctx* c, const SweepArgs<T>& A)
         warps = (int)((c->smem_optin - fixed) / per_warp);
     if (warps > max_warps) warps = max_warps;
     KernelTimer timer(c, AXIS);
-    // plain-form step sweeps: the split solve where one thread or one
-    // 32-line block per line cannot fill the GPU (the 2-D variant) or the
-    // lines do not fit the shared-memory kernels
-    if (MODE == 0 && DIR == 0 &&
-        (c->split == 2 || (c->split == 1 && (c->dims == 2 || warps < 1))))
-        return launch_split<T, AXIS>(c, A);
+    // plain-form sweeps: the split solve where one thread or one 32-line
+    // block per line cannot fill the GPU (the 2-D variant) or the step's
+    // lines are too long for the shared-memory kernels; the adjoint's solves
+    // (DIR 1, 2) only when forced: on the 100^3 adjoint workload the
+    // one-thread-per-line sweep was faster (backward 60.7 ms against 69.5)
+    if (MODE == 0 &&
+        (c->split == 2 || (c->split == 1 && DIR == 0 && (c->dims == 2 || warps < 1))))
+        return launch_split<T, AXIS, DIR>(c, A);
     if (warps >= 1) {
         const int64_t* first = c->lines_first[AXIS];
         if (first[A.n_sub] == 0) return BFVM_OK;   // every line is on the shell

@@ -19,8 +19,10 @@ def bf():
     return bfvm
 
 
-def gpu_forward(bf, p, record=0):
+def gpu_forward(bf, p, record=0, split=None):
     sim = bf.Sim.from_problem(p)
+    if split is not None:
+        sim.set_option(bf.OPT_SPLIT, split)
     if record:
         sim.record(record)
     sim.step(p.steps)
@@ -35,12 +37,14 @@ def mixed_adjoint_problem():
                                steps=9, dt=0.02)
 
 
-@pytest.mark.parametrize("every", [1, 4, 9])
-def test_adjoint_matches_oracle(bf, every):
+@pytest.mark.parametrize("every,split", [(1, None), (4, None), (9, None), (4, 2)])
+def test_adjoint_matches_oracle(bf, every, split):
+    """split 2: the replayed and adjoint line solves (Dirichlet modes 1 and
+    2, separate input and output) through the split line solve."""
     import torch
     p = mixed_adjoint_problem()
     target = p.rho0 * 0.5 + np.random.default_rng(4).uniform(0, 1, p.rho0.shape)
-    sim, fin = gpu_forward(bf, p, record=every)
+    sim, fin = gpu_forward(bf, p, record=every, split=split)
     ref_fin = oracle.run(p)
     g = 2.0 * (fin - target)
     out = sim.backward(torch.as_tensor(g, device="cuda"), want_g0=True)
