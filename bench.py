@@ -330,6 +330,15 @@ def measure_forms(args, plain_ups, dev, stream, flush):
     sa.close()
     sim = bfvm.Sim.from_problem(p)
     sim.step(p.steps)   # warm the graphs and kernels
+    # and the backward's kernels (their modules load at first launch)
+    sim.set_density(torch.as_tensor(p.rho0, device=dev))
+    sim.record(1)
+    sim.step(2)
+    sim.backward(torch.zeros_like(sim.get_density()))
+    torch.cuda.synchronize()
+    sim.close()
+    sim = bfvm.Sim.from_problem(p)
+    sim.step(p.steps)
     sim.set_density(torch.as_tensor(p.rho0, device=dev))
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
