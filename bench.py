@@ -163,6 +163,24 @@ def dist_setup(args):
     return world, rank, local
 
 
+def max_over_ranks(value, world, device=None):
+    """The job's time from each rank's own: the maximum over the ranks of
+    the initialised process group (the value itself on one rank)."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank, world, seconds):
+    """Whole-job throughput: the units every rank processed over the job's
+    time (each rank runs its own replica of the workload)."""
+    return units_per_rank * world / seconds
+
+
 def cpu_baseline(p, seconds):
     """The oracle as it stands, on this host's cores, on a bounded sample of
     the workload: whole steps of the full grid until `seconds` have passed."""
@@ -454,18 +472,13 @@ def run_ours(args):
         barrier()
         t_wall = time.perf_counter() - t_wall0
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    total_ms = float(sum(step_ms))
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(float(sum(step_ms)), world, dev)
     kms, kn = bfvm.bfvm_kernel_times(sim.handle, reset=True)
     info1 = sim.info()
     launches = info1["launches"] - info0["launches"]
 
     N = p.updates_per_step
-    ups = N * args.steps * world / (total_ms / 1e3)
+    ups = job_rate(N * args.steps, world, total_ms / 1e3)
     ms_per_step = total_ms / args.steps
     es = 8 if prec == 64 else 4
     hbm, hbm_src = peaks()
@@ -540,14 +553,9 @@ def run_ours(args):
         bfvm.bfvm_get_density(h, host_out)
     torch.cuda.synchronize()
     barrier()
-    e2e_s = time.perf_counter() - t0
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world, dev)
     nbytes = host_in.numel() * host_in.element_size()
-    e2e = {"value": N * args.e2e_steps * world / e2e_s, "unit": "voxel-substrate updates/s",
+    e2e = {"value": job_rate(N * args.e2e_steps, world, e2e_s), "unit": "voxel-substrate updates/s",
            "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
            "steps": args.e2e_steps,
            "call": "bfvm_set_density(host) + bfvm_step(1) + bfvm_get_density(host)"}
