@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--workload", default="tumour_200",
                     choices=["tumour_200", "tumour_200_fp32", "plain_50"])
     ap.add_argument("--variant", type=int, default=None, help="FP64 sweep form: 0 plain, 1 rescaled")
+    ap.add_argument("--one-launch", type=int, default=None, choices=[0, 1, 2],
+                    help="library option 8: 0 per-axis launches, 1 automatic, 2 one launch per step")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
@@ -454,6 +456,8 @@ def run_ours(args):
     sim = bfvm.Sim.from_problem(p)
     if args.variant is not None:
         sim.set_option(bfvm.OPT_VARIANT, args.variant)
+    if args.one_launch is not None:
+        sim.set_option(bfvm.OPT_FUSED_STEP, args.one_launch)
     sim.set_option(bfvm.OPT_TIME_KERNELS, 1)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
