@@ -46,7 +46,12 @@ _ip = ctypes.POINTER(ctypes.c_int)
 
 
 def build(force: bool = False) -> str:
-    """Compile oracle.c into _build/liboracle.so (gcc, OpenMP if present)."""
+    """Compile oracle.c into _build/liboracle.so (gcc, OpenMP if present).
+    BFVM_ORACLE_LIB names a prebuilt library to load instead (the mutation
+    test loads copies of the oracle with planted mistakes that way)."""
+    override = os.environ.get("BFVM_ORACLE_LIB")
+    if override:
+        return override
     os.makedirs(_BUILD, exist_ok=True)
     if (not force and os.path.exists(_LIB_PATH)
             and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
