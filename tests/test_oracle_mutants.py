@@ -1,6 +1,7 @@
 """The pins are pinned: each plausible mistake planted in a copy of the
 oracle (a dropped factor, a wrong sign, a wrong index, a transposed operand,
-a wrong unit) makes tests/test_oracle_pins.py fail.  The copy is compiled
+a wrong unit, in the 3-D and 2-D steps, the sources, the Dirichlet nodes and
+the adjoint) makes tests/test_oracle_pins.py fail.  The copy is compiled
 like the oracle and loaded through BFVM_ORACLE_LIB in a child pytest run;
 the oracle itself is untouched."""
 import os
@@ -28,6 +29,11 @@ MUTANTS = [
      "double v_vox = dx * dx * dx;", "double v_vox = dx * dx;"),
     ("explicit instead of implicit source update",
      "*r = (*r + a) / (1.0 + b);", "*r = *r + a - b * (*r);"),
+    ("2-D variant: decay share of the 3-D step",
+     "double ell = lambda[s] * dt / 2.0;", "double ell = lambda[s] * dt / 3.0;"),
+    ("Dirichlet node holds half its value",
+     "rho[(int64_t)sub[i] * n_vox + vox[i]] = val[i];",
+     "rho[(int64_t)sub[i] * n_vox + vox[i]] = 0.5 * val[i];"),
     ("adjoint: sign of the diffusion gradient",
      "dD[s] -= (dt / (dx * dx))", "dD[s] += (dt / (dx * dx))"),
     ("adjoint: decay gradient without the LOD share",
