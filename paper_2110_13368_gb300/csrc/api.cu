@@ -349,6 +349,7 @@ bfvm_status bfvm_set_cells(bfvm_ctx* h, int64_t n_cells, const double* pos, cons
                            const double* S, const double* U, const double* rho_star,
                            int32_t on_device)
 {
+    NvtxRange nvtx("bfvm_set_cells");
     if (!h) return BFVM_EINVAL;
     Ctx* c = &h->impl;
     if (n_cells < 0) return set_err(c, BFVM_EINVAL, "n_cells must be >= 0");
@@ -393,6 +394,7 @@ bfvm_status bfvm_set_cells(bfvm_ctx* h, int64_t n_cells, const double* pos, cons
 
 bfvm_status bfvm_step(bfvm_ctx* h, int32_t n_steps)
 {
+    NvtxRange nvtx("bfvm_step");
     if (!h) return BFVM_EINVAL;
     Ctx* c = &h->impl;
     if (n_steps < 0) return set_err(c, BFVM_EINVAL, "n_steps must be >= 0");
@@ -468,6 +470,7 @@ bfvm_status bfvm_backward(bfvm_ctx* h, const double* g_final, int32_t checkpoint
                           double* dD, double* dlambda, double* dS, double* dU, double* g0,
                           int32_t on_device)
 {
+    NvtxRange nvtx("bfvm_backward");
     if (!h) return BFVM_EINVAL;
     Ctx* c = &h->impl;
     if (c->precision != 64) return set_err(c, BFVM_EINVAL, "the adjoint needs an FP64 context");
@@ -540,6 +543,7 @@ bfvm_status bfvm_update_cells(bfvm_ctx* h, int64_t n_cells, const double* pos,
                               const double* vol, const double* S, const double* U,
                               const double* rho_star)
 {
+    NvtxRange nvtx("bfvm_update_cells");
     if (!h) return BFVM_EINVAL;
     Ctx* c = &h->impl;
     if (c->src.cap == 0) return set_err(c, BFVM_ESTATE, "no cells to update (bfvm_set_cells first)");

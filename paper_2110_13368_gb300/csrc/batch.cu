@@ -118,6 +118,7 @@ bfvm_status bfvm_batch_create(bfvm_batch** out, bfvm_ctx* const* members, int32_
 
 bfvm_status bfvm_batch_step(bfvm_batch* h, int32_t n_steps)
 {
+    NvtxRange nvtx("bfvm_batch_step");
     if (!h) return BFVM_EINVAL;
     BatchImpl* b = &h->impl;
     if (n_steps < 0) return berr(b, BFVM_EINVAL, "n_steps must be >= 0");

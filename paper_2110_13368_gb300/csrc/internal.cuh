@@ -10,7 +10,36 @@
 
 #include "bfvm.h"
 
+// NVTX ranges around the ABI's long-running calls, for timelines taken with
+// a profiler (NVTX v3 is header-only and costs nothing when no tool is
+// attached); compiled out where the headers are missing
+#if defined(__has_include)
+#if __has_include(<nvtx3/nvToolsExt.h>)
+#include <nvtx3/nvToolsExt.h>
+#define BFVM_HAVE_NVTX 1
+#endif
+#endif
+
 namespace bfvm {
+
+struct NvtxRange {
+    explicit NvtxRange(const char* name)
+    {
+#ifdef BFVM_HAVE_NVTX
+        nvtxRangePushA(name);
+#else
+        (void)name;
+#endif
+    }
+    ~NvtxRange()
+    {
+#ifdef BFVM_HAVE_NVTX
+        nvtxRangePop();
+#endif
+    }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // ---------------------------------------------------------------- tables
 // Per substrate s and axis a (0 = x, 1 = y, 2 = z), the line matrix of that
