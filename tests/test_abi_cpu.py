@@ -81,3 +81,19 @@ def test_product_path_does_not_import_oracle():
                 text = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in text and "from oracle" not in text, f
                 assert "oracle.c" not in text, f
+
+
+def test_option_keys_agree_between_header_code_and_binding():
+    """Every option key the library handles is documented in include/bfvm.h
+    and has a constant in the binding, and no other key is documented."""
+    import re
+    from paper_2110_13368_gb300 import bfvm
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    header = open(os.path.join(root, "include", "bfvm.h")).read()
+    api = open(os.path.join(root, "paper_2110_13368_gb300", "csrc", "api.cu")).read()
+    body = api[api.index("bfvm_set_option("):]
+    body = body[:body.index("unknown option key")]
+    handled = {int(k) for k in re.findall(r"case (\d+):", body)}
+    documented = {int(k) for k in re.findall(r"\*\s+key (\d+)\s", header)}
+    constants = {v for k, v in vars(bfvm).items() if k.startswith("OPT_")}
+    assert handled == documented == constants, (handled, documented, constants)
