@@ -31,8 +31,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 HBM_FALLBACK_GBS = 6800.0
-FP64_PEAK_TFLOPS = 1.25       # 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (nominal)
-FP64_MEASURED_TFLOPS = 1.12   # best DFMA throughput seen by a probe of dependent chains on a GB300
+DFMA_PER_CLK_PER_SM = 2       # nominal FP64 FMA lanes per clock per SM of a GB300
+SM_MAX_MHZ_FALLBACK = 2070.0
 L2_FLUSH_BYTES = 512 << 20
 
 
@@ -77,6 +77,36 @@ def peaks():
         return float(d["hbm_gbs"]), "measured"
     except Exception:
         return HBM_FALLBACK_GBS, "fallback"
+
+
+def sm_max_mhz():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["sm_max_mhz"])
+    except Exception:
+        return SM_MAX_MHZ_FALLBACK
+
+
+def fp64_pipe_peak(n_sm, stream):
+    """The FP64 FMA rate of this GPU, measured live: independent FMA chains
+    on every SM (bfvm_fp64_fma_rate) for a few warp and chain counts, the
+    best of them, as TFLOP/s (2 flop per FMA); beside it the nominal rate
+    from the unit count (SMs x 2 FMA lanes per clock x maximum SM clock)."""
+    from paper_2110_13368_gb300 import bfvm
+    runs = []
+    for warps in (4, 8, 16):
+        for chains in (1, 2, 4):
+            iters = max(1, int(1.2e10 / (n_sm * 32 * warps * 8 * chains)))
+            rate, ms = bfvm.bfvm_fp64_fma_rate(warps, chains, iters, stream)
+            runs.append({"warps_per_sm": warps, "chains": chains, "tflops": 2 * rate / 1e12,
+                         "ms": ms})
+    best = max(runs, key=lambda r: r["tflops"])
+    nominal = n_sm * DFMA_PER_CLK_PER_SM * 2 * sm_max_mhz() * 1e6 / 1e12
+    return {"measured_tflops": best["tflops"], "best": {k: best[k] for k in ("warps_per_sm", "chains")},
+            "nominal_tflops": nominal, "sms": n_sm,
+            "nominal_source": f"{n_sm} SMs x {DFMA_PER_CLK_PER_SM} FMA/clk x 2 flop x "
+                              f"{sm_max_mhz():.0f} MHz",
+            "runs": runs}
 
 
 def sweep_traffic(workload):
@@ -217,6 +247,17 @@ def cpu_baseline(p, seconds):
                             "sample": f"{steps1} full step(s), {el1:.1f} s, 1 thread"}}
 
 
+def accuracy(got, ref):
+    """Per substrate: max|got - ref| / max|ref| and ||got - ref||_2 / ||ref||_2."""
+    import numpy as np
+    mx, l2 = [], []
+    for s in range(ref.shape[0]):
+        d = got[s] - ref[s]
+        mx.append(float(np.abs(d).max() / max(np.abs(ref[s]).max(), 1e-300)))
+        l2.append(float(np.linalg.norm(d) / max(np.linalg.norm(ref[s]), 1e-300)))
+    return {"max_rel_err_per_substrate": mx, "l2_rel_err_per_substrate": l2}
+
+
 def timed_steps(step_fn, k, stream, flush):
     """Sum of CUDA-event times of k calls of step_fn, L2 flushed before each."""
     import torch
@@ -256,6 +297,18 @@ def measure_forms(args, plain_ups, dev, stream, flush):
                    "accuracy_gate": "<= 1e-5 vs the FP64 oracle (parity tests)"}
     s32.close()
     s64.close()
+    # the FP32 form of the 50^3 workload over its 100 steps, against the FP64
+    # GPU path here and against the FP64 oracle in the cpu_baseline leg
+    p50 = inputs.plain_50()
+    fields = {}
+    for prec in (32, 64):
+        sm = bfvm.Sim.from_problem(p50, precision=prec)
+        sm.step(p50.steps)
+        fields[prec] = sm.get_density().double().cpu().numpy()
+        sm.close()
+    out["fp32"]["plain_50_100_steps"] = {
+        "vs_fp64_gpu": accuracy(fields[32], fields[64])}
+    out["_plain_50_fp32_field"] = fields[32]
     # batched: 256 uneven members, one launch per phase, against the same
     # members stepped one context at a time
     for prec in (64, 32):
@@ -397,7 +450,7 @@ def measure_forms(args, plain_ups, dev, stream, flush):
                       "backward_ms": bwd_s * 1e3,
                       "fwd_plus_bwd_over_2x_fwd": (fwd_rec_s + bwd_s) / (2 * fwd_plain_ms / 1e3),
                       "dD": float(grads["dD"][0]), "dlambda": float(grads["dlambda"][0]),
-                      "accuracy_gate": "1e-10 vs the CPU adjoint, 2e-4 vs central differences (tests)"}
+                      "accuracy_gate": "1e-10 vs the CPU adjoint; 1e-4 vs central differences (tests)"}
     return out
 
 
@@ -470,6 +523,9 @@ def run_ours(args):
         flush.fill_(1.0)
         sim.step(1)
     torch.cuda.synchronize()
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    fp64 = fp64_pipe_peak(n_sm, stream) if prec == 64 else None
+    torch.cuda.synchronize()
     bfvm.bfvm_kernel_times(sim.handle, reset=True)
     info0 = sim.info()
 
@@ -519,27 +575,25 @@ def run_ours(args):
     rescaled = prec == 64 and info["variant"] == 1
     kname = "x, y and z sweeps (one launch)" if dom == 4 else f"{kinds[dom]} sweep"
     alg_bytes = 2 * es * N * dom_sweeps
+    achieved_bw = alg_bytes / (dom_avg / 1e3) / 1e9
+    roof = {"bound": "hbm", "kernel": kname, "achieved": achieved_bw, "peak": hbm,
+            "unit": "GB/s", "frac": achieved_bw / hbm,
+            "peak_source": f"{hbm_src}: MEASURED_PEAKS.json hbm_gbs (copy, burst)",
+            "bytes_per_update_per_sweep": 2 * es, "sweeps_per_launch": dom_sweeps,
+            "updates_per_launch": N, "algorithmic_bytes_per_launch": alg_bytes,
+            "avg_launch_ms": dom_avg,
+            "traffic": traffic.get(kinds[dom]) if traffic else None}
     if prec == 64:
         flops_per_elem = 4 if rescaled else 5
         achieved = flops_per_elem * N * dom_sweeps / (dom_avg / 1e3) / 1e12
-        roof = {"bound": "alu", "kernel": kname, "achieved": achieved,
-                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-                "peak_source": "FP64 pipe: 152 SMs x 2 DFMA/clk x 2.07 GHz (nominal 1.25 TFLOP/s)",
-                "measured_fp64_pipe_tflops": FP64_MEASURED_TFLOPS,
-                "frac_of_measured_fp64_pipe": achieved / FP64_MEASURED_TFLOPS,
-                "flops_per_element_per_sweep": flops_per_elem,
-                "algorithmic_flops_per_launch": flops_per_elem * N * dom_sweeps,
-                "traffic": traffic.get(kinds[dom]) if traffic else None,
-                "algorithmic_bytes_per_launch": alg_bytes,
-                "hbm_view": {"achieved": alg_bytes / (dom_avg / 1e3) / 1e9, "peak": hbm,
-                             "unit": "GB/s", "frac": alg_bytes / (dom_avg / 1e3) / 1e9 / hbm,
-                             "peak_source": hbm_src}}
-    else:
-        achieved = alg_bytes / (dom_avg / 1e3) / 1e9
-        roof = {"bound": "hbm", "kernel": kname, "achieved": achieved,
-                "peak": hbm, "unit": "GB/s", "frac": achieved / hbm, "peak_source": hbm_src,
-                "algorithmic_bytes_per_launch": alg_bytes,
-                "traffic": traffic.get(kinds[dom]) if traffic else None}
+        roof["fp64_pipe"] = {"achieved_tflops": achieved,
+                             "measured_peak_tflops": fp64["measured_tflops"],
+                             "frac_of_measured": achieved / fp64["measured_tflops"],
+                             "nominal_peak_tflops": fp64["nominal_tflops"],
+                             "frac_of_nominal": achieved / fp64["nominal_tflops"],
+                             "flops_per_element_per_sweep": flops_per_elem,
+                             "algorithmic_flops_per_launch": flops_per_elem * N * dom_sweeps,
+                             "probe": fp64}
 
     if args.skip_extras:
         sim.close()
@@ -613,8 +667,22 @@ def run_ours(args):
             line["forms"] = forms
         clocks = clk.summary()
         line["clocks"] = clocks
+        f32 = forms.pop("_plain_50_fp32_field", None) if forms is not None else None
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(p, args.cpu_seconds)
+            if f32 is not None:
+                # the FP64 oracle's 100 steps of the 50^3 workload, timed here
+                # too, against the FP32 GPU result
+                import oracle
+                from paper_2110_13368_gb300 import inputs
+                p50 = inputs.plain_50()
+                t0 = time.perf_counter()
+                ref50 = oracle.run(p50, n_threads=oracle.max_threads())
+                el = time.perf_counter() - t0
+                line["forms"]["fp32"]["plain_50_100_steps"]["vs_fp64_oracle"] = accuracy(f32, ref50)
+                line["cpu_baseline"]["plain_50"] = {
+                    "value": p50.updates_per_step * p50.steps / el, "steps": p50.steps,
+                    "cores": oracle.max_threads(), "seconds": el}
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist

@@ -334,6 +334,21 @@ bfvm_status bfvm_batch_shape(const bfvm_batch* batch, int32_t axis, int32_t* alg
 bfvm_status bfvm_batch_set_shape(bfvm_batch* batch, int32_t axis, int32_t algo, int32_t warps);
 
 /*
+ * Measured FP64 fused multiply-add rate of the current device (the paper
+ * has no counterpart: it is the denominator of the FP64-pipe roofline of
+ * the FP64 sweeps, which spend two FMAs per element and axis).  One CTA of
+ * warps_per_sm (1..32) warps per SM; every thread runs `chains` (1, 2, 4 or
+ * 8) independent chains x <- a x + b for 8 * iters (iters 1..2^24) rounds;
+ * the launch is timed with CUDA events on cuda_stream.
+ *   fma_per_second  out: FMAs (lane operations) per second
+ *   elapsed_ms      out, may be NULL: the timed launch's duration
+ * Allocates and frees a small output buffer; synchronises cuda_stream.
+ * Errors: BFVM_EINVAL (arguments), BFVM_ECUDA; text via bfvm_last_error(NULL).
+ */
+bfvm_status bfvm_fp64_fma_rate(int32_t warps_per_sm, int32_t chains, int64_t iters,
+                               void* cuda_stream, double* fma_per_second, double* elapsed_ms);
+
+/*
  * Allocation-free variant of the cell source/uptake update.  The paper has
  * no counterpart: it exists for callers that must not allocate device
  * memory, such as host loops driving many small simulations (cudaMalloc and
@@ -345,16 +360,24 @@ bfvm_status bfvm_batch_set_shape(bfvm_batch* batch, int32_t axis, int32_t algo, 
  * in ascending index order within its voxel, does
  *   rho_v <- (rho_v + dt (V_i/dx^3) S_i rho*_i) / (1 + dt (V_i/dx^3)(S_i+U_i)).
  * pos, vol, S, U, rho_star are device arrays laid out as in bfvm_set_cells.
+ * Their sizes are taken on trust: rho must hold n_sub*nz*ny*nx doubles,
+ * pos 3*n_cells, vol n_cells, and S, U, rho_star n_cells*n_sub each, all on
+ * the current device (the Python binding checks shapes, dtypes and devices
+ * before calling).
  * It allocates nothing: its only scratch (the sort keys of at most 262,144
  * cells plus a check flag, about 2 MB) is a fixed device array that every
  * GPU loading this library holds until the process exits.
  *  - n_cells > 262,144: BFVM_EINVAL with an explanatory text, nothing runs.
  *  - Bad sizes or cells (positions outside [0, n_a*dx], non-positive
  *    volumes, negative or non-finite rates): BFVM_EINVAL; the field is
- *    untouched.  The cell check synchronises cuda_stream.
+ *    untouched.  Every call synchronises cuda_stream once, to read the cell
+ *    check back before the update is launched.
  *  - Errors are reported by bfvm_last_error(NULL).
  *  - The first call on a device looks up the scratch array's device address
- *    (once per device); make that first call before any stream capture.
+ *    (once per device, with that device current) and keeps it; make that
+ *    first call before any stream capture.  The kept address belongs to the
+ *    device's primary context: do not call this entry point again in a
+ *    process after cudaDeviceReset on that device.
  *  - All calls on one device share the scratch: calls whose GPU work can
  *    overlap (different streams without ordering) race; order them on one
  *    stream.  Each call rewrites every scratch word it reads.

@@ -42,7 +42,7 @@ EXPORTED = ["bfvm_create", "bfvm_destroy", "bfvm_set_density", "bfvm_get_density
             "bfvm_batch_create", "bfvm_batch_step", "bfvm_batch_sync", "bfvm_batch_destroy",
             "bfvm_batch_last_error", "bfvm_batch_info", "bfvm_batch_shape",
             "bfvm_batch_set_shape", "bfvm_apply_sources_noalloc", "bfvm_set_dirichlet_nodes",
-            "bfvm_update_cells"]
+            "bfvm_update_cells", "bfvm_fp64_fma_rate"]
 
 
 class BfvmError(RuntimeError):
@@ -110,6 +110,8 @@ def load_library(path: Optional[str] = None):
         lib.bfvm_apply_sources_noalloc.argtypes = ([_vp] + [_i32] * 4 + [ctypes.c_double] * 2
                                                    + [_i64] + [_vp] * 5 + [_vp])
         lib.bfvm_apply_sources_noalloc.restype = ctypes.c_int
+        lib.bfvm_fp64_fma_rate.argtypes = [_i32, _i32, _i64, _vp, _dp, _dp]
+        lib.bfvm_fp64_fma_rate.restype = ctypes.c_int
         for name in ("bfvm_create", "bfvm_set_density", "bfvm_get_density", "bfvm_set_cells",
                      "bfvm_step", "bfvm_sync", "bfvm_record", "bfvm_backward", "bfvm_get_info",
                      "bfvm_set_option", "bfvm_kernel_times", "bfvm_batch_create", "bfvm_batch_step",
@@ -342,18 +344,59 @@ def bfvm_batch_set_shape(b, axis, algo, warps):
     _check(load_library().bfvm_batch_set_shape(b, int(axis), int(algo), int(warps)), b, batch=True)
 
 
+def bfvm_fp64_fma_rate(warps_per_sm, chains, iters, stream=None):
+    """(FP64 FMAs per second, timed ms) of independent FMA chains on every
+    SM of the current device (the FP64-pipe roofline's denominator)."""
+    rate = ctypes.c_double()
+    ms = ctypes.c_double()
+    st = load_library().bfvm_fp64_fma_rate(int(warps_per_sm), int(chains), int(iters),
+                                           _stream_handle(stream), ctypes.byref(rate),
+                                           ctypes.byref(ms))
+    _check(st, None)
+    return float(rate.value), float(ms.value)
+
+
 def bfvm_apply_sources_noalloc(rho, nx, ny, nz, dx_um, dt_min, pos, vol, S, U, rho_star,
                                stream=None):
     """Cell source/uptake update on a dense FP64 device field, in place,
     without any device allocation (for callers that must not allocate; see
-    include/bfvm.h).  All arrays are CUDA tensors."""
-    ptrs = [_ptr(a) for a in (rho, pos, vol, S, U, rho_star)]
-    if any(d != 1 for _, d, _ in ptrs):
-        raise ValueError("bfvm_apply_sources_noalloc takes device tensors only")
+    include/bfvm.h).  All arrays are contiguous float64 CUDA tensors on one
+    device: rho (n_sub, nz, ny, nx), pos (n, 3), vol (n,), S, U and rho_star
+    (n, n_sub).  The C entry point takes the sizes on trust, so they are
+    checked here, before the call."""
+    import torch
+    arrs = {"rho": rho, "pos": pos, "vol": vol, "S": S, "U": U, "rho_star": rho_star}
+    for name, a in arrs.items():
+        if not isinstance(a, torch.Tensor) or not a.is_cuda:
+            raise ValueError(f"bfvm_apply_sources_noalloc: {name} must be a CUDA tensor")
+        if a.dtype != torch.float64:
+            raise ValueError(f"bfvm_apply_sources_noalloc: {name} must be float64, got {a.dtype}")
+        if not a.is_contiguous():
+            raise ValueError(f"bfvm_apply_sources_noalloc: {name} must be contiguous")
+        if a.device != rho.device:
+            raise ValueError(f"bfvm_apply_sources_noalloc: {name} is on {a.device}, "
+                             f"rho on {rho.device}")
+    nx, ny, nz = int(nx), int(ny), int(nz)
+    if rho.dim() != 4 or tuple(rho.shape[1:]) != (nz, ny, nx):
+        raise ValueError(f"bfvm_apply_sources_noalloc: rho must be (n_sub, {nz}, {ny}, {nx}), "
+                         f"got {tuple(rho.shape)}")
     n_sub = int(rho.shape[0])
+    if pos.dim() != 2 or pos.shape[1] != 3:
+        raise ValueError(f"bfvm_apply_sources_noalloc: pos must be (n, 3), got {tuple(pos.shape)}")
     n_cells = int(pos.shape[0])
+    if tuple(vol.shape) != (n_cells,):
+        raise ValueError(f"bfvm_apply_sources_noalloc: vol must be ({n_cells},), "
+                         f"got {tuple(vol.shape)}")
+    for name, a in (("S", S), ("U", U), ("rho_star", rho_star)):
+        if tuple(a.shape) != (n_cells, n_sub):
+            raise ValueError(f"bfvm_apply_sources_noalloc: {name} must be ({n_cells}, {n_sub}), "
+                             f"got {tuple(a.shape)}")
+    if torch.cuda.current_device() != rho.device.index:
+        raise ValueError("bfvm_apply_sources_noalloc: the tensors' device must be the current "
+                         "CUDA device")
+    ptrs = [_ptr(a) for a in (rho, pos, vol, S, U, rho_star)]
     st = load_library().bfvm_apply_sources_noalloc(
-        ptrs[0][0], int(nx), int(ny), int(nz), n_sub, float(dx_um), float(dt_min), n_cells,
+        ptrs[0][0], nx, ny, nz, n_sub, float(dx_um), float(dt_min), n_cells,
         ptrs[1][0], ptrs[2][0], ptrs[3][0], ptrs[4][0], ptrs[5][0], _stream_handle(stream))
     _check(st, None)
     del ptrs

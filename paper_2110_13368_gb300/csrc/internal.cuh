@@ -300,6 +300,22 @@ bfvm_status update_sources(Ctx* c, const double* pos, const double* vol, const d
                            const double* U, const double* rho_star);
 bfvm_status sync_source_counts(Ctx* c);
 
+// Cell checking, sort keys and their sort on a plain stream (sources.cu),
+// shared by the context's cell binning and bfvm_apply_sources_noalloc.
+// A key is (voxel << kCellIdxBits) | cell index, unique per cell, so sorted
+// keys give voxel order with cell-index order inside each voxel; padding
+// keys (index >= n) are all ones and sort last.  The check ORs into *flag:
+// 1 position outside [0, n_a dx], 2 volume, 4 rates, 8 rho*.
+constexpr uint64_t kCellIdxBits = 31;
+constexpr int kCellSortBlock = 2048;   // keys per shared-memory sort block
+void launch_validate_cells(cudaStream_t st, int64_t n, int n_sub, const double* pos,
+                           const double* vol, const double* S, const double* U,
+                           const double* rs, double lx, double ly, double lz, int* flag);
+void launch_cell_keys(cudaStream_t st, int64_t n, int64_t n_pad, const double* pos, double dx,
+                      int nx, int ny, int nz, uint64_t* keys);
+// n_pad: a power of two >= kCellSortBlock; returns the number of launches
+int64_t launch_sort_keys(cudaStream_t st, uint64_t* keys, int64_t n_pad);
+
 // adjoint (adjoint.cu)
 bfvm_status run_backward(Ctx* c, const double* g_final_dev, double* dD_dev,
                          double* dl_dev, double* dS_dev, double* dU_dev,

@@ -28,15 +28,16 @@ namespace {
 
 constexpr int64_t kMaxCells = int64_t(1) << 18;       // 262,144 cells
 constexpr int64_t kFlagWords = 32;                     // 256 bytes after the keys
-constexpr uint64_t kNaIdxBits = 31;
-constexpr uint64_t kNaIdxMask = (uint64_t(1) << kNaIdxBits) - 1;
-constexpr int kNaSortBlock = 2048;
+constexpr uint64_t kNaIdxMask = (uint64_t(1) << bfvm::kCellIdxBits) - 1;
 
 // keys [0, kMaxCells), flag at [kMaxCells] (as an int in the first word)
-__device__ __align__(256) unsigned long long g_noalloc_scratch[kMaxCells + kFlagWords];
+__device__ __align__(256) uint64_t g_noalloc_scratch[kMaxCells + kFlagWords];
 
-// Device address of the scratch array, looked up once per device (host code
-// sees only a host-side stand-in under the array's name).
+// Device address of the scratch array, looked up once per device with that
+// device current (host code sees only a host-side stand-in under the
+// array's name).  The cached address belongs to the device's primary
+// context: after cudaDeviceReset it is stale, so the entry point must not be
+// called again in that process once the device has been reset.
 constexpr int kMaxDevices = 64;
 void* g_scratch_addr[kMaxDevices] = {};
 std::mutex g_scratch_mutex;
@@ -54,104 +55,21 @@ cudaError_t scratch_address(int device, void** out)
     return cudaSuccess;
 }
 
-__global__ void k_na_validate(int64_t n, int n_sub, const double* pos, const double* vol,
-                              const double* S, const double* U, const double* rs, double lx,
-                              double ly, double lz, int* flag)
-{
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    int bad = 0;
-    const double px = pos[3 * i], py = pos[3 * i + 1], pz = pos[3 * i + 2];
-    if (!(px >= 0.0 && px <= lx) || !(py >= 0.0 && py <= ly) || !(pz >= 0.0 && pz <= lz))
-        bad |= 1;
-    if (!(vol[i] > 0.0) || !isfinite(vol[i])) bad |= 2;
-    for (int s = 0; s < n_sub; ++s) {
-        const double a = S[i * n_sub + s], b = U[i * n_sub + s];
-        if (!(a >= 0.0) || !isfinite(a) || !(b >= 0.0) || !isfinite(b)) bad |= 4;
-        if (!isfinite(rs[i * n_sub + s])) bad |= 8;
-    }
-    if (bad) atomicOr(flag, bad);
-}
-
-// key = (voxel << 31) | cell index: unique, so sorting gives voxel order with
-// cell-index order inside each voxel
-__global__ void k_na_keys(int64_t n, int64_t n_pad, const double* pos, double dx, int nx,
-                          int ny, int nz, unsigned long long* keys)
-{
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= n_pad) return;
-    if (i >= n) {
-        keys[i] = ~0ull;
-        return;
-    }
-    const int ext[3] = {nx, ny, nz};
-    int64_t v[3];
-    for (int a = 0; a < 3; ++a) {
-        int64_t q = (int64_t)floor(pos[3 * i + a] / dx);
-        if (q > ext[a] - 1) q = ext[a] - 1;
-        if (q < 0) q = 0;
-        v[a] = q;
-    }
-    const uint64_t vox = (uint64_t)((v[2] * ny + v[1]) * (int64_t)nx + v[0]);
-    keys[i] = (vox << kNaIdxBits) | (uint64_t)i;
-}
-
-__global__ void k_na_bitonic_global(unsigned long long* a, int64_t n, int64_t size,
-                                    int64_t stride)
-{
-    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (t >= n / 2) return;
-    const int64_t i = (t / stride) * 2 * stride + (t % stride);
-    const int64_t j = i + stride;
-    const bool up = (i & size) == 0;
-    const unsigned long long x = a[i], y = a[j];
-    if ((x > y) == up) {
-        a[i] = y;
-        a[j] = x;
-    }
-}
-
-__global__ void k_na_bitonic_shared(unsigned long long* a, int64_t size_lo, int64_t size_hi)
-{
-    __shared__ unsigned long long s[kNaSortBlock];
-    const int64_t base = (int64_t)blockIdx.x * kNaSortBlock;
-    for (int k = threadIdx.x; k < kNaSortBlock; k += blockDim.x) s[k] = a[base + k];
-    __syncthreads();
-    for (int64_t size = size_lo; size <= size_hi; size *= 2) {
-        int64_t st0 = size / 2;
-        if (st0 >= kNaSortBlock) st0 = kNaSortBlock / 2;
-        for (int64_t stride = st0; stride >= 1; stride /= 2) {
-            for (int t = threadIdx.x; t < kNaSortBlock / 2; t += blockDim.x) {
-                const int i = (int)((t / stride) * 2 * stride + (t % stride));
-                const int j = i + (int)stride;
-                const bool up = ((base + i) & size) == 0;
-                const unsigned long long x = s[i], y = s[j];
-                if ((x > y) == up) {
-                    s[i] = y;
-                    s[j] = x;
-                }
-            }
-            __syncthreads();
-        }
-    }
-    for (int k = threadIdx.x; k < kNaSortBlock; k += blockDim.x) a[base + k] = s[k];
-}
-
 // The first sorted position of every voxel composes that voxel's cells in
 // index order into rho <- alpha rho + beta (FP64), per substrate, and
 // applies it: alpha <- alpha / (1 + b_i), beta <- (beta + a_i) / (1 + b_i)
 // with a_i = w S_i rho*_i, b_i = w (S_i + U_i), w = dt V_i / dx^3.
-__global__ void k_na_apply(int64_t n, const unsigned long long* keys, int n_sub, int64_t n_vox,
+__global__ void k_na_apply(int64_t n, const uint64_t* keys, int n_sub, int64_t n_vox,
                            double dt, double vvox, const double* vol, const double* S,
                            const double* U, const double* rs, double* rho)
 {
     const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (j >= n) return;
-    const uint64_t vox = keys[j] >> kNaIdxBits;
-    if (j > 0 && (keys[j - 1] >> kNaIdxBits) == vox) return;
+    const uint64_t vox = keys[j] >> bfvm::kCellIdxBits;
+    if (j > 0 && (keys[j - 1] >> bfvm::kCellIdxBits) == vox) return;
     for (int s = 0; s < n_sub; ++s) {
         double al = 1.0, be = 0.0;
-        for (int64_t q = j; q < n && (keys[q] >> kNaIdxBits) == vox; ++q) {
+        for (int64_t q = j; q < n && (keys[q] >> bfvm::kCellIdxBits) == vox; ++q) {
             const int64_t i = (int64_t)(keys[q] & kNaIdxMask);
             const double w = dt * (vol[i] / vvox);
             const double Si = S[i * n_sub + s], Ui = U[i * n_sub + s];
@@ -201,14 +119,14 @@ extern "C" bfvm_status bfvm_apply_sources_noalloc(double* rho, int32_t nx, int32
     void* base = nullptr;
     if ((e = scratch_address(device, &base)) != cudaSuccess)
         return bfvm::cuda_err(nullptr, e, "cudaGetSymbolAddress");
-    unsigned long long* keys = static_cast<unsigned long long*>(base);
+    uint64_t* keys = static_cast<uint64_t*>(base);
     int* flag = reinterpret_cast<int*>(keys + kMaxCells);
 
     // argument check on the device (the arrays are device memory)
     if ((e = cudaMemsetAsync(flag, 0, sizeof(int), st)) != cudaSuccess)
         return bfvm::cuda_err(nullptr, e, "cudaMemsetAsync");
-    k_na_validate<<<(unsigned)bfvm::ceil_div(n_cells, 256), 256, 0, st>>>(
-        n_cells, n_sub, pos, vol, S, U, rho_star, nx * dx_um, ny * dx_um, nz * dx_um, flag);
+    bfvm::launch_validate_cells(st, n_cells, n_sub, pos, vol, S, U, rho_star, nx * dx_um,
+                                ny * dx_um, nz * dx_um, flag);
     int bad = 0;
     if ((e = cudaMemcpyAsync(&bad, flag, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
         return bfvm::cuda_err(nullptr, e, "cudaMemcpyAsync");
@@ -219,18 +137,10 @@ extern "C" bfvm_status bfvm_apply_sources_noalloc(double* rho, int32_t nx, int32
     if (bad & 4) return set_err(nullptr, BFVM_EINVAL, "secretion/uptake rates must be finite and >= 0");
     if (bad & 8) return set_err(nullptr, BFVM_EINVAL, "rho_star must be finite");
 
-    int64_t n_pad = kNaSortBlock;
+    int64_t n_pad = bfvm::kCellSortBlock;
     while (n_pad < n_cells) n_pad *= 2;
-    k_na_keys<<<(unsigned)bfvm::ceil_div(n_pad, 256), 256, 0, st>>>(n_cells, n_pad, pos, dx_um,
-                                                                     nx, ny, nz, keys);
-    const unsigned blocks = (unsigned)(n_pad / kNaSortBlock);
-    k_na_bitonic_shared<<<blocks, 512, 0, st>>>(keys, 2, kNaSortBlock);
-    for (int64_t size = 2 * kNaSortBlock; size <= n_pad; size *= 2) {
-        for (int64_t stride = size / 2; stride >= kNaSortBlock; stride /= 2)
-            k_na_bitonic_global<<<(unsigned)bfvm::ceil_div(n_pad / 2, 256), 256, 0, st>>>(
-                keys, n_pad, size, stride);
-        k_na_bitonic_shared<<<blocks, 512, 0, st>>>(keys, size, size);
-    }
+    bfvm::launch_cell_keys(st, n_cells, n_pad, pos, dx_um, nx, ny, nz, keys);
+    bfvm::launch_sort_keys(st, keys, n_pad);
     k_na_apply<<<(unsigned)bfvm::ceil_div(n_cells, 128), 128, 0, st>>>(
         n_cells, keys, n_sub, n_vox, dt_min, dx_um * dx_um * dx_um, vol, S, U, rho_star, rho);
     if ((e = cudaGetLastError()) != cudaSuccess) return bfvm::cuda_err(nullptr, e, "launch");

@@ -21,7 +21,7 @@ namespace bfvm {
 
 namespace {
 
-constexpr uint64_t kIdxBits = 31;
+constexpr uint64_t kIdxBits = kCellIdxBits;
 constexpr uint64_t kIdxMask = (1ull << kIdxBits) - 1;
 
 __global__ void k_validate_cells(int64_t n, int n_sub, const double* pos,
@@ -83,7 +83,7 @@ __global__ void k_bitonic_global(uint64_t* a, int64_t n, int64_t size, int64_t s
     }
 }
 
-constexpr int kSortBlock = 2048;
+constexpr int kSortBlock = kCellSortBlock;
 
 // Within each block of 2048 keys: for sizes from size_lo to size_hi, strides
 // down to 1 (size_lo == size_hi: only the strides < 2048 of that size).
@@ -254,24 +254,46 @@ int64_t scan_ws_size(int64_t n)
 
 bfvm_status sort_keys(Ctx* c, uint64_t* keys, int64_t n_pad)
 {
-    // n_pad is a power of two >= kSortBlock
-    unsigned blocks = (unsigned)(n_pad / kSortBlock);
-    k_bitonic_shared<<<blocks, 512, 0, c->stream>>>(keys, 2, kSortBlock);
-    c->launches += 1;
-    for (int64_t size = 2 * kSortBlock; size <= n_pad; size *= 2) {
-        for (int64_t stride = size / 2; stride >= kSortBlock; stride /= 2) {
-            k_bitonic_global<<<(unsigned)ceil_div(n_pad / 2, 256), 256, 0, c->stream>>>(
-                keys, n_pad, size, stride);
-            c->launches += 1;
-        }
-        k_bitonic_shared<<<blocks, 512, 0, c->stream>>>(keys, size, size);
-        c->launches += 1;
-    }
+    c->launches += launch_sort_keys(c->stream, keys, n_pad);
     BFVM_CUDA(c, cudaGetLastError());
     return BFVM_OK;
 }
 
 }  // namespace
+
+// The binning and ordering kernels above, launched on a plain stream: used
+// by bin_cells below and by bfvm_apply_sources_noalloc (noalloc.cu).
+void launch_validate_cells(cudaStream_t st, int64_t n, int n_sub, const double* pos,
+                           const double* vol, const double* S, const double* U,
+                           const double* rs, double lx, double ly, double lz, int* flag)
+{
+    k_validate_cells<<<(unsigned)ceil_div(n, 256), 256, 0, st>>>(n, n_sub, pos, vol, S, U, rs,
+                                                                   lx, ly, lz, flag);
+}
+
+void launch_cell_keys(cudaStream_t st, int64_t n, int64_t n_pad, const double* pos, double dx,
+                      int nx, int ny, int nz, uint64_t* keys)
+{
+    k_keys<<<(unsigned)ceil_div(n_pad, 256), 256, 0, st>>>(n, n_pad, pos, dx, nx, ny, nz, keys);
+}
+
+int64_t launch_sort_keys(cudaStream_t st, uint64_t* keys, int64_t n_pad)
+{
+    // n_pad is a power of two >= kSortBlock
+    const unsigned blocks = (unsigned)(n_pad / kSortBlock);
+    int64_t launches = 1;
+    k_bitonic_shared<<<blocks, 512, 0, st>>>(keys, 2, kSortBlock);
+    for (int64_t size = 2 * kSortBlock; size <= n_pad; size *= 2) {
+        for (int64_t stride = size / 2; stride >= kSortBlock; stride /= 2) {
+            k_bitonic_global<<<(unsigned)ceil_div(n_pad / 2, 256), 256, 0, st>>>(keys, n_pad, size,
+                                                                                stride);
+            ++launches;
+        }
+        k_bitonic_shared<<<blocks, 512, 0, st>>>(keys, size, size);
+        ++launches;
+    }
+    return launches;
+}
 
 void free_sources(Ctx* c)
 {
@@ -300,8 +322,8 @@ bfvm_status bin_cells(Ctx* c, const double* pos, const double* vol, const double
     const int n_sub = c->n_sub;
     int* flag = validate_sync ? c->d_err : c->d_err + 2;
     if (validate_sync) BFVM_CUDA(c, cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
-    k_validate_cells<<<(unsigned)ceil_div(n, 256), 256, 0, c->stream>>>(
-        n, n_sub, pos, vol, Sr, Ur, rs, c->nx * c->dx, c->ny * c->dx, c->nz * c->dx, flag);
+    launch_validate_cells(c->stream, n, n_sub, pos, vol, Sr, Ur, rs, c->nx * c->dx,
+                          c->ny * c->dx, c->nz * c->dx, flag);
     c->launches += 1;
     if (validate_sync) {
         int f = 0;
@@ -312,8 +334,7 @@ bfvm_status bin_cells(Ctx* c, const double* pos, const double* vol, const double
         if (f & 4) return set_err(c, BFVM_EINVAL, "secretion/uptake rates must be finite and >= 0");
         if (f & 8) return set_err(c, BFVM_EINVAL, "rho_star must be finite");
     }
-    k_keys<<<(unsigned)ceil_div(S.n_pad, 256), 256, 0, c->stream>>>(
-        n, S.n_pad, pos, c->dx, c->nx, c->ny, c->nz, S.keys);
+    launch_cell_keys(c->stream, n, S.n_pad, pos, c->dx, c->nx, c->ny, c->nz, S.keys);
     c->launches += 1;
     bfvm_status st = sort_keys(c, S.keys, S.n_pad);
     if (st != BFVM_OK) return st;

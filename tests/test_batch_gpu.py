@@ -66,10 +66,12 @@ def test_batch_across_periods_and_graphs(bf):
 
 
 @pytest.mark.slow
-def test_batch_256_full_size_sampled_members(bf):
+@pytest.mark.parametrize("precision,tol", [(64, 1e-12), (32, 1e-5)])
+def test_batch_256_full_size_sampled_members(bf, precision, tol):
     """The 256-member workload in the launch configuration the benchmark
-    times, 200 steps; eight members are checked against the oracle."""
-    probs = inputs.batch_256(seed=0)
+    times, 200 steps, in FP64 and in FP32; eight members (and the smallest)
+    are checked against the FP64 oracle, at 1e-12 and 1e-5."""
+    probs = inputs.batch_256(seed=0, precision=precision)
     sims = [bf.Sim.from_problem(p) for p in probs]
     batch = bf.Batch(sims)
     batch.step(probs[0].steps)
@@ -79,9 +81,9 @@ def test_batch_256_full_size_sampled_members(bf):
     sizes = np.array([p.updates_per_step for p in probs])
     pick = sorted(set(pick) | {int(np.argmin(sizes))})
     for i in pick:
-        got = sims[i].get_density().cpu().numpy()
+        got = sims[i].get_density().double().cpu().numpy()
         ref = oracle.run(probs[i])
-        assert np.all(rel_inf(got, ref) <= 1e-12), (i, rel_inf(got, ref))
+        assert np.all(rel_inf(got, ref) <= tol), (i, rel_inf(got, ref))
     batch.close()
     for s in sims:
         s.close()
