@@ -37,6 +37,15 @@ def loss_diff(fa, fb, target):
     return float(((fa - fb) * (fa + fb - 2.0 * target)).sum())
 
 
+def rate_step(p, i):
+    """FD step of cell i's rates: 1e-6 relative to the cell's rate scale
+    max(S_i, U_i).  S = 0 has no scale of its own; a step of 1e-6 absolute
+    there is below the FD's rounding floor (the quotient's error grows as
+    1/h and reaches ~2e-4 relative at h = 1e-6 for these gradients, in the
+    oracle as on the GPU), so S takes the same step as U."""
+    return 1e-6 * max(abs(p.S[i, 0]), abs(p.U[i, 0]))
+
+
 def fd_gradient(field, p, attr, index, target, f0, h):
     """Finite-difference d(loss)/d(p.attr[index]) with step h from the GPU
     forward `field`: central where the parameter may go below by h, else
@@ -120,8 +129,7 @@ def test_adjoint_central_differences(bf):
         assert out[key].cpu().numpy()[0] == pytest.approx(est, rel=1e-4, abs=1e-7), key
     for i in (0, 7, 123):
         for key, attr in (("dS", "S"), ("dU", "U")):
-            h = 1e-6 * max(abs(getattr(p, attr)[i, 0]), 1.0)
-            est = fd_gradient(field, p, attr, (i, 0), target, f0, h)
+            est = fd_gradient(field, p, attr, (i, 0), target, f0, rate_step(p, i))
             got = out[key].cpu().numpy()[i, 0]
             assert got == pytest.approx(est, rel=1e-4, abs=1e-7), (key, i, got, est)
 
@@ -192,7 +200,8 @@ def test_adjoint_workload_at_full_size(bf):
     dD, dlambda, dS and dU match the CPU FP64 adjoint at 1e-10 (infinity-norm
     relative); dD, dlambda and sampled per-cell dU and dS match central
     differences of the GPU forward with h = 1e-6 relative (S = 0 here, so dS
-    takes the one-sided second-order difference)."""
+    takes the one-sided second-order difference with the cell's rate scale
+    as its reference, see rate_step)."""
     import torch
     p, q = inputs.adjoint_problem()
     assert (p.nx, p.ny, p.nz, p.n_sub, p.n_cells, p.steps) == (100, 100, 100, 1, 20_000, 200)
@@ -226,8 +235,7 @@ def test_adjoint_workload_at_full_size(bf):
                    set(rng.choice(p.n_cells, size=3, replace=False).tolist()))
     for i in cells:
         for key, attr in (("dU", "U"), ("dS", "S")):
-            h = 1e-6 * max(abs(getattr(p, attr)[i, 0]), 1.0)
-            est = fd_gradient(field, p, attr, (i, 0), target, f0, h)
+            est = fd_gradient(field, p, attr, (i, 0), target, f0, rate_step(p, i))
             g = out[key].cpu().numpy()
             report.append((f"{key}[{i}]", float(g[i, 0]), est, float(np.abs(g).max())))
     for name, got, est, scale in report:
