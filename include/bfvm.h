@@ -334,6 +334,60 @@ bfvm_status bfvm_batch_shape(const bfvm_batch* batch, int32_t axis, int32_t* alg
 bfvm_status bfvm_batch_set_shape(bfvm_batch* batch, int32_t axis, int32_t algo, int32_t warps);
 
 /*
+ * One grid decomposed along z into slabs, one context per slab (an
+ * extension: the paper names an MPI+X decomposition of the domain as its
+ * way to larger problems, "Introduction and Motivation" and "Future Work").
+ * The slabs together compute exactly the step of the whole grid (up to
+ * rounding): the x and y lines lie inside a slab; each z line is solved by
+ * the Thomas algorithm of the whole line, split into the slabs' segments
+ * through the affine form of its two recurrences, with one exchange of one
+ * value per z line and substrate after the forward and after the backward
+ * pass.
+ *
+ * Create slab `slab` of n_slabs: the grid is nx x ny x z_starts[n_slabs],
+ * slab j holding the global layers [z_starts[j], z_starts[j+1]) (z_starts[0]
+ * = 0, every slab at least one layer).  The other arguments are those of
+ * bfvm_create; the context is FP64 in the plain Thomas form.  Its field is
+ * the slab's part of the grid, [n_sub][nz_j][ny][nx] with nz_j its layer
+ * count, set and read with bfvm_set_density / bfvm_get_density.  Its cells
+ * are given in grid coordinates (positions in [0, n_a dx] of the whole
+ * grid); every cell's voxel layer must lie in the slab (BFVM_EINVAL
+ * otherwise).  A slab context rejects bfvm_step, recording for the adjoint,
+ * Dirichlet nodes, options 1, 2, 8 and 10 and batches (BFVM_ESTATE).
+ */
+bfvm_status bfvm_create_slab(bfvm_ctx** out, int32_t nx, int32_t ny, int32_t n_slabs,
+                             const int32_t* z_starts, int32_t slab, double dx_um,
+                             double dt_min, int32_t n_sub, const double* D,
+                             const double* lambda, const int32_t* bc_kind,
+                             const double* bc_value, void* cuda_stream);
+
+/*
+ * One step of a slab, in three calls with two gathers between them.  The
+ * first two write one FP64 value per z line and substrate to the caller's
+ * device buffer send[n_sub][ny][nx]; the caller gathers the send buffers of
+ * all slabs, in slab order, into one device array gathered[n_slabs][n_sub]
+ * [ny][nx] (e.g. an all-gather across ranks, after the context's stream has
+ * finished the call) and passes it to the next call.  Both buffers stay the
+ * caller's; the calls read or write them on the context's stream.
+ *   bfvm_slab_forward   the x and y sweeps with their Dirichlet handling,
+ *                       then the z forward elimination of the slab's
+ *                       segment from a zero incoming value; send = its last
+ *                       values
+ *   bfvm_slab_backward  the segment's incoming forward value from the
+ *                       gathered values of the slabs below, then its back
+ *                       substitution from a zero incoming value; send = its
+ *                       first values
+ *   bfvm_slab_finish    the incoming value from the gathered values of the
+ *                       slabs above, the z solution, the grid's Dirichlet
+ *                       shell within the slab and the slab's cell sources
+ * All three are asynchronous.  BFVM_ESTATE on a context that is not a slab,
+ * BFVM_EINVAL for NULL buffers.
+ */
+bfvm_status bfvm_slab_forward(bfvm_ctx* ctx, double* send);
+bfvm_status bfvm_slab_backward(bfvm_ctx* ctx, const double* gathered, double* send);
+bfvm_status bfvm_slab_finish(bfvm_ctx* ctx, const double* gathered);
+
+/*
  * Measured FP64 fused multiply-add rate of the current device (the paper
  * has no counterpart: it is the denominator of the FP64-pipe roofline of
  * the FP64 sweeps, which spend two FMAs per element and axis).  One CTA of

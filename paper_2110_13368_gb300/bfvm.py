@@ -42,7 +42,8 @@ EXPORTED = ["bfvm_create", "bfvm_destroy", "bfvm_set_density", "bfvm_get_density
             "bfvm_batch_create", "bfvm_batch_step", "bfvm_batch_sync", "bfvm_batch_destroy",
             "bfvm_batch_last_error", "bfvm_batch_info", "bfvm_batch_shape",
             "bfvm_batch_set_shape", "bfvm_apply_sources_noalloc", "bfvm_set_dirichlet_nodes",
-            "bfvm_update_cells", "bfvm_fp64_fma_rate"]
+            "bfvm_update_cells", "bfvm_fp64_fma_rate", "bfvm_create_slab",
+            "bfvm_slab_forward", "bfvm_slab_backward", "bfvm_slab_finish"]
 
 
 class BfvmError(RuntimeError):
@@ -112,6 +113,16 @@ def load_library(path: Optional[str] = None):
         lib.bfvm_apply_sources_noalloc.restype = ctypes.c_int
         lib.bfvm_fp64_fma_rate.argtypes = [_i32, _i32, _i64, _vp, _dp, _dp]
         lib.bfvm_fp64_fma_rate.restype = ctypes.c_int
+        lib.bfvm_create_slab.argtypes = [ctypes.POINTER(_vp), _i32, _i32, _i32,
+                                         ctypes.POINTER(_i32), _i32, ctypes.c_double,
+                                         ctypes.c_double, _i32, _dp, _dp, ctypes.POINTER(_i32),
+                                         _dp, _vp]
+        lib.bfvm_slab_forward.argtypes = [_vp, _vp]
+        lib.bfvm_slab_backward.argtypes = [_vp, _vp, _vp]
+        lib.bfvm_slab_finish.argtypes = [_vp, _vp]
+        for name in ("bfvm_create_slab", "bfvm_slab_forward", "bfvm_slab_backward",
+                     "bfvm_slab_finish"):
+            getattr(lib, name).restype = ctypes.c_int
         for name in ("bfvm_create", "bfvm_set_density", "bfvm_get_density", "bfvm_set_cells",
                      "bfvm_step", "bfvm_sync", "bfvm_record", "bfvm_backward", "bfvm_get_info",
                      "bfvm_set_option", "bfvm_kernel_times", "bfvm_batch_create", "bfvm_batch_step",
@@ -342,6 +353,51 @@ def bfvm_batch_shape(b, axis):
 
 def bfvm_batch_set_shape(b, axis, algo, warps):
     _check(load_library().bfvm_batch_set_shape(b, int(axis), int(algo), int(warps)), b, batch=True)
+
+
+def bfvm_create_slab(nx, ny, z_starts, slab, dx_um, dt_min, D, lam, bc_kind, bc_value,
+                     stream=None):
+    """Context of z-slab `slab` of a grid decomposed along z (slab j holds
+    the global layers [z_starts[j], z_starts[j+1]))."""
+    lib = load_library()
+    n_sub = len(D)
+    zs = np.ascontiguousarray(np.asarray(z_starts, dtype=np.int32))
+    D = _f64(D, n_sub)
+    lam = _f64(lam, n_sub)
+    kind = np.ascontiguousarray(np.asarray(bc_kind, dtype=np.int32))
+    val = _f64(bc_value, n_sub)
+    h = _vp()
+    st = lib.bfvm_create_slab(ctypes.byref(h), int(nx), int(ny), int(zs.size - 1),
+                              zs.ctypes.data_as(ctypes.POINTER(_i32)), int(slab), float(dx_um),
+                              float(dt_min), n_sub, D.ctypes.data_as(_dp), lam.ctypes.data_as(_dp),
+                              kind.ctypes.data_as(ctypes.POINTER(_i32)), val.ctypes.data_as(_dp),
+                              _stream_handle(stream))
+    _check(st, None)
+    return h
+
+
+def _dev_f64(t, name):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float64 \
+            or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous float64 CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def bfvm_slab_forward(h, send):
+    """x, y sweeps and the z forward of the slab; send: (n_sub, ny, nx)."""
+    _check(load_library().bfvm_slab_forward(h, _dev_f64(send, "send")), h)
+
+
+def bfvm_slab_backward(h, gathered, send):
+    """gathered: (n_slabs, n_sub, ny, nx) of every slab's forward values."""
+    _check(load_library().bfvm_slab_backward(h, _dev_f64(gathered, "gathered"),
+                                             _dev_f64(send, "send")), h)
+
+
+def bfvm_slab_finish(h, gathered):
+    """gathered: (n_slabs, n_sub, ny, nx) of every slab's backward values."""
+    _check(load_library().bfvm_slab_finish(h, _dev_f64(gathered, "gathered")), h)
 
 
 def bfvm_fp64_fma_rate(warps_per_sm, chains, iters, stream=None):

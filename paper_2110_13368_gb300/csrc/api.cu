@@ -296,6 +296,8 @@ void bfvm_destroy(bfvm_ctx* h)
     if (c->d_bc_kind) cudaFree(c->d_bc_kind);
     if (c->d_bc_value) cudaFree(c->d_bc_value);
     if (c->d_err) cudaFree(c->d_err);
+    if (c->slab_tab) cudaFree(c->slab_tab);
+    if (c->d_z_starts) cudaFree(c->d_z_starts);
     delete h;
 }
 
@@ -398,6 +400,9 @@ bfvm_status bfvm_step(bfvm_ctx* h, int32_t n_steps)
     if (!h) return BFVM_EINVAL;
     Ctx* c = &h->impl;
     if (n_steps < 0) return set_err(c, BFVM_EINVAL, "n_steps must be >= 0");
+    if (c->slab >= 0)
+        return set_err(c, BFVM_ESTATE, "a z-slab steps with bfvm_slab_forward / "
+                                       "bfvm_slab_backward / bfvm_slab_finish");
     if (n_steps == 0) return BFVM_OK;
     const int m = period_of(c);
     bfvm_status st = BFVM_OK;
@@ -455,6 +460,8 @@ bfvm_status bfvm_record(bfvm_ctx* h, int32_t checkpoint_every)
         return set_err(c, BFVM_EINVAL, "the adjoint needs an FP64 context");
     if (checkpoint_every > 0 && c->dims != 3)
         return set_err(c, BFVM_ESTATE, "the adjoint covers the 3-D step only");
+    if (checkpoint_every > 0 && c->slab >= 0)
+        return set_err(c, BFVM_ESTATE, "the adjoint covers whole-grid contexts only");
     if (checkpoint_every > 0 && c->n_nodes > 0)
         return set_err(c, BFVM_ESTATE, "the adjoint does not cover Dirichlet nodes");
     if (checkpoint_every > 0) {
@@ -565,6 +572,8 @@ bfvm_status bfvm_set_dirichlet_nodes(bfvm_ctx* h, int64_t n_nodes, const int64_t
     Ctx* c = &h->impl;
     if (n_nodes < 0) return set_err(c, BFVM_EINVAL, "n_nodes must be >= 0");
     if (n_nodes > 0 && (!voxel || !substrate || !value)) return set_err(c, BFVM_EINVAL, "NULL node array");
+    if (n_nodes > 0 && c->slab >= 0)
+        return set_err(c, BFVM_ESTATE, "Dirichlet nodes are defined for whole-grid contexts");
     if (n_nodes > 0 && c->dims != 3)
         return set_err(c, BFVM_EINVAL, "Dirichlet nodes are defined for the 3-D step");
     if (n_nodes > 0 && c->record_every != 0)
@@ -651,6 +660,8 @@ bfvm_status bfvm_set_option(bfvm_ctx* h, int32_t key, int64_t value)
 {
     if (!h) return BFVM_EINVAL;
     Ctx* c = &h->impl;
+    if (c->slab >= 0 && (key == 1 || key == 2 || key == 8 || key == 10))
+        return set_err(c, BFVM_ESTATE, "a z-slab runs the plain 3-D form with its own z sweep");
     switch (key) {
         case 1:
             if (value != 0 && value != 1) return set_err(c, BFVM_EINVAL, "variant must be 0 or 1");

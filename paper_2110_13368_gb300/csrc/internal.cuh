@@ -147,6 +147,20 @@ struct Ctx {
     int fused_step = 1;           // one launch for x, y, z: 0 never, 1 when not fewer pairs, 2 always
     int dims = 3;                 // 2: the 2-D variant (nz == 1; x and y sweeps,
                                   // lambda dt / 2 each, four-edge Dirichlet shell)
+    // z-slab of a grid decomposed along z over several contexts
+    // (bfvm_create_slab, slab.cu): this context holds the global z range
+    // [z_origin, z_origin + nz) of nz_global layers.  z_face_lo / z_face_hi:
+    // the local z = 0 / z = nz - 1 plane is a face of the whole grid (and so
+    // a Dirichlet shell plane).  An ordinary context is the one slab.
+    int slab = -1;                // index of this slab; -1: an ordinary context
+    int n_slabs = 1;
+    int z_origin = 0, nz_global = 0;
+    bool z_face_lo = true, z_face_hi = true;
+    // z faces that are boundary planes: bit 0 the local z = 0 plane, bit 1
+    // z = nz - 1; none in the 2-D variant (its single layer is not a face)
+    int zfaces() const { return dims == 2 ? 0 : ((z_face_lo ? 1 : 0) | (z_face_hi ? 2 : 0)); }
+    int* d_z_starts = nullptr;    // [n_slabs + 1] first global layer of each slab
+    double* slab_tab = nullptr;   // z tables of this slab (slab.cu)
     // Dirichlet nodes inside the domain (bfvm_set_dirichlet_nodes): one per
     // (voxel, substrate), the caller's later node kept where two coincide
     void* staging = nullptr;         // device buffer for unscaled copies to the host
@@ -308,11 +322,16 @@ bfvm_status sync_source_counts(Ctx* c);
 // 1 position outside [0, n_a dx], 2 volume, 4 rates, 8 rho*.
 constexpr uint64_t kCellIdxBits = 31;
 constexpr int kCellSortBlock = 2048;   // keys per shared-memory sort block
+// z_origin / nz_global: the grid is the z-slab [z_origin, z_origin + nz)
+// of a grid of nz_global layers (0 / nz for a whole grid); a cell belongs to
+// the slab when its global voxel layer min(floor(p_z / dx), nz_global - 1)
+// lies in it (else the check ORs 1), and its key holds the local voxel.
 void launch_validate_cells(cudaStream_t st, int64_t n, int n_sub, const double* pos,
                            const double* vol, const double* S, const double* U,
-                           const double* rs, double lx, double ly, double lz, int* flag);
+                           const double* rs, double dx, int nx, int ny, int nz,
+                           int z_origin, int nz_global, int* flag);
 void launch_cell_keys(cudaStream_t st, int64_t n, int64_t n_pad, const double* pos, double dx,
-                      int nx, int ny, int nz, uint64_t* keys);
+                      int nx, int ny, int nz, int z_origin, int nz_global, uint64_t* keys);
 // n_pad: a power of two >= kCellSortBlock; returns the number of launches
 int64_t launch_sort_keys(cudaStream_t st, uint64_t* keys, int64_t n_pad);
 

@@ -125,8 +125,8 @@ extern "C" bfvm_status bfvm_apply_sources_noalloc(double* rho, int32_t nx, int32
     // argument check on the device (the arrays are device memory)
     if ((e = cudaMemsetAsync(flag, 0, sizeof(int), st)) != cudaSuccess)
         return bfvm::cuda_err(nullptr, e, "cudaMemsetAsync");
-    bfvm::launch_validate_cells(st, n_cells, n_sub, pos, vol, S, U, rho_star, nx * dx_um,
-                                ny * dx_um, nz * dx_um, flag);
+    bfvm::launch_validate_cells(st, n_cells, n_sub, pos, vol, S, U, rho_star, dx_um, nx, ny, nz,
+                                0, nz, flag);
     int bad = 0;
     if ((e = cudaMemcpyAsync(&bad, flag, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
         return bfvm::cuda_err(nullptr, e, "cudaMemcpyAsync");
@@ -139,7 +139,7 @@ extern "C" bfvm_status bfvm_apply_sources_noalloc(double* rho, int32_t nx, int32
 
     int64_t n_pad = bfvm::kCellSortBlock;
     while (n_pad < n_cells) n_pad *= 2;
-    bfvm::launch_cell_keys(st, n_cells, n_pad, pos, dx_um, nx, ny, nz, keys);
+    bfvm::launch_cell_keys(st, n_cells, n_pad, pos, dx_um, nx, ny, nz, 0, nz, keys);
     bfvm::launch_sort_keys(st, keys, n_pad);
     k_na_apply<<<(unsigned)bfvm::ceil_div(n_cells, 128), 128, 0, st>>>(
         n_cells, keys, n_sub, n_vox, dt_min, dx_um * dx_um * dx_um, vol, S, U, rho_star, rho);

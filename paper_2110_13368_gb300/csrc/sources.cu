@@ -24,17 +24,26 @@ namespace {
 constexpr uint64_t kIdxBits = kCellIdxBits;
 constexpr uint64_t kIdxMask = (1ull << kIdxBits) - 1;
 
+// The grid is the z-slab [z_origin, z_origin + nz) of nz_global layers
+// (0 / nz for a whole grid): positions are global, each coordinate in
+// [0, n_a dx] of the whole grid, and the cell's layer must lie in the slab.
 __global__ void k_validate_cells(int64_t n, int n_sub, const double* pos,
                                  const double* vol, const double* S,
-                                 const double* U, const double* rs, double lx,
-                                 double ly, double lz, int* flag)
+                                 const double* U, const double* rs, double dx, int nx,
+                                 int ny, int nz, int z_origin, int nz_global, int* flag)
 {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
     int bad = 0;
     double px = pos[3 * i], py = pos[3 * i + 1], pz = pos[3 * i + 2];
-    if (!(px >= 0.0 && px <= lx) || !(py >= 0.0 && py <= ly) || !(pz >= 0.0 && pz <= lz))
+    if (!(px >= 0.0 && px <= nx * dx) || !(py >= 0.0 && py <= ny * dx) ||
+        !(pz >= 0.0 && pz <= nz_global * dx))
         bad |= 1;
+    else {
+        int64_t q = (int64_t)floor(pz / dx);
+        if (q > nz_global - 1) q = nz_global - 1;
+        if (q < z_origin || q >= z_origin + nz) bad |= 1;
+    }
     double v = vol[i];
     if (!(v > 0.0) || !isfinite(v)) bad |= 2;
     for (int s = 0; s < n_sub; ++s) {
@@ -46,7 +55,7 @@ __global__ void k_validate_cells(int64_t n, int n_sub, const double* pos,
 }
 
 __global__ void k_keys(int64_t n, int64_t n_pad, const double* pos, double dx,
-                       int nx, int ny, int nz, uint64_t* keys)
+                       int nx, int ny, int nz, int z_origin, int nz_global, uint64_t* keys)
 {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n_pad) return;
@@ -54,7 +63,7 @@ __global__ void k_keys(int64_t n, int64_t n_pad, const double* pos, double dx,
         keys[i] = ~0ull;
         return;
     }
-    int ext[3] = {nx, ny, nz};
+    int ext[3] = {nx, ny, nz_global};
     int64_t v[3];
     for (int a = 0; a < 3; ++a) {
         double q = floor(pos[3 * i + a] / dx);
@@ -63,6 +72,11 @@ __global__ void k_keys(int64_t n, int64_t n_pad, const double* pos, double dx,
         if (qi < 0) qi = 0;
         v[a] = qi;
     }
+    // the slab's own layer (clamped: a cell outside the slab is reported by
+    // the check and binned to the nearest layer meanwhile)
+    v[2] -= z_origin;
+    if (v[2] < 0) v[2] = 0;
+    if (v[2] > nz - 1) v[2] = nz - 1;
     uint64_t vox = (uint64_t)((v[2] * ny + v[1]) * (int64_t)nx + v[0]);
     keys[i] = (vox << kIdxBits) | (uint64_t)i;
 }
@@ -265,16 +279,19 @@ bfvm_status sort_keys(Ctx* c, uint64_t* keys, int64_t n_pad)
 // by bin_cells below and by bfvm_apply_sources_noalloc (noalloc.cu).
 void launch_validate_cells(cudaStream_t st, int64_t n, int n_sub, const double* pos,
                            const double* vol, const double* S, const double* U,
-                           const double* rs, double lx, double ly, double lz, int* flag)
+                           const double* rs, double dx, int nx, int ny, int nz,
+                           int z_origin, int nz_global, int* flag)
 {
     k_validate_cells<<<(unsigned)ceil_div(n, 256), 256, 0, st>>>(n, n_sub, pos, vol, S, U, rs,
-                                                                   lx, ly, lz, flag);
+                                                                   dx, nx, ny, nz, z_origin,
+                                                                   nz_global, flag);
 }
 
 void launch_cell_keys(cudaStream_t st, int64_t n, int64_t n_pad, const double* pos, double dx,
-                      int nx, int ny, int nz, uint64_t* keys)
+                      int nx, int ny, int nz, int z_origin, int nz_global, uint64_t* keys)
 {
-    k_keys<<<(unsigned)ceil_div(n_pad, 256), 256, 0, st>>>(n, n_pad, pos, dx, nx, ny, nz, keys);
+    k_keys<<<(unsigned)ceil_div(n_pad, 256), 256, 0, st>>>(n, n_pad, pos, dx, nx, ny, nz,
+                                                           z_origin, nz_global, keys);
 }
 
 int64_t launch_sort_keys(cudaStream_t st, uint64_t* keys, int64_t n_pad)
@@ -322,19 +339,24 @@ bfvm_status bin_cells(Ctx* c, const double* pos, const double* vol, const double
     const int n_sub = c->n_sub;
     int* flag = validate_sync ? c->d_err : c->d_err + 2;
     if (validate_sync) BFVM_CUDA(c, cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
-    launch_validate_cells(c->stream, n, n_sub, pos, vol, Sr, Ur, rs, c->nx * c->dx,
-                          c->ny * c->dx, c->nz * c->dx, flag);
+    const int nzg = c->slab >= 0 ? c->nz_global : c->nz;
+    launch_validate_cells(c->stream, n, n_sub, pos, vol, Sr, Ur, rs, c->dx, c->nx, c->ny, c->nz,
+                          c->z_origin, nzg, flag);
     c->launches += 1;
     if (validate_sync) {
         int f = 0;
         BFVM_CUDA(c, cudaMemcpyAsync(&f, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
         BFVM_CUDA(c, cudaStreamSynchronize(c->stream));
-        if (f & 1) return set_err(c, BFVM_EINVAL, "cell position outside [0, n*dx] on some axis");
+        if (f & 1)
+            return set_err(c, BFVM_EINVAL, c->slab >= 0 ? "cell position outside [0, n*dx] on "
+                                                          "some axis, or outside this slab"
+                                                        : "cell position outside [0, n*dx] on some axis");
         if (f & 2) return set_err(c, BFVM_EINVAL, "cell volume must be finite and > 0");
         if (f & 4) return set_err(c, BFVM_EINVAL, "secretion/uptake rates must be finite and >= 0");
         if (f & 8) return set_err(c, BFVM_EINVAL, "rho_star must be finite");
     }
-    launch_cell_keys(c->stream, n, S.n_pad, pos, c->dx, c->nx, c->ny, c->nz, S.keys);
+    launch_cell_keys(c->stream, n, S.n_pad, pos, c->dx, c->nx, c->ny, c->nz, c->z_origin, nzg,
+                     S.keys);
     c->launches += 1;
     bfvm_status st = sort_keys(c, S.keys, S.n_pad);
     if (st != BFVM_OK) return st;

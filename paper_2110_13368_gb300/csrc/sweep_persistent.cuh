@@ -666,11 +666,13 @@ template <typename T>
 __global__ void k_shell_fill(T* __restrict__ field, int nx, int ny, int nz, int n_sub,
                              int64_t pitch, const int32_t* __restrict__ kind,
                              const double* __restrict__ value, int64_t L,
-                             const double* __restrict__ sc, int dims)
+                             const double* __restrict__ sc, int zfaces)
 {
     // faces enumerated as: z planes (2 nx ny), y rows of the other planes
     // (2 nx nz), x columns (2 ny nz); overlaps are written twice with the
-    // same value.  In the 2-D variant the z planes are not boundaries.
+    // same value.  A z plane is written only where zfaces marks it as a
+    // boundary (bit 0: z = 0, bit 1: z = nz - 1): neither in the 2-D variant,
+    // only the grid's own end planes on a z-slab of a decomposed grid.
     const int64_t fz = 2 * (int64_t)nx * ny, fy = 2 * (int64_t)nx * nz, fx = 2 * (int64_t)ny * nz;
     const int64_t per = fz + fy + fx;
     int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -678,10 +680,11 @@ __global__ void k_shell_fill(T* __restrict__ field, int nx, int ny, int nz, int 
     const int s = (int)(e / per);
     if (kind[s] != BFVM_BC_DIRICHLET) return;
     int64_t t = e % per;
-    if (dims == 2 && t < fz) return;
     int x, y, z;
     if (t < fz) {
-        x = (int)(t % nx); y = (int)((t / nx) % ny); z = (t / ((int64_t)nx * ny)) ? nz - 1 : 0;
+        const bool hi = (t / ((int64_t)nx * ny)) != 0;
+        if (!(zfaces & (hi ? 2 : 1))) return;
+        x = (int)(t % nx); y = (int)((t / nx) % ny); z = hi ? nz - 1 : 0;
     } else if ((t -= fz) < fy) {
         x = (int)(t % nx); z = (int)((t / nx) % nz); y = (t / ((int64_t)nx * nz)) ? ny - 1 : 0;
     } else {

@@ -73,14 +73,14 @@ __device__ __forceinline__ SplitLine split_line(const SweepArgs<T>& A, int64_t l
         L.s = (int)(t / A.nz);
         L.base = (((int64_t)L.s * A.nz + oz) * A.ny + oy) * A.pitch;
         L.stride = 1;
-        other_shell = (oy == 0 || oy == A.ny - 1 || (A.dims == 3 && (oz == 0 || oz == A.nz - 1)));
+        other_shell = (oy == 0 || oy == A.ny - 1 || (((A.zfaces & 1) && oz == 0) || ((A.zfaces & 2) && oz == A.nz - 1)));
     } else if (AXIS == 1) {
         const int ox = (int)(t % A.nx); t /= A.nx;
         const int oz = (int)(t % A.nz);
         L.s = (int)(t / A.nz);
         L.base = (((int64_t)L.s * A.nz + oz) * A.ny) * A.pitch + ox;
         L.stride = A.pitch;
-        other_shell = (ox == 0 || ox == A.nx - 1 || (A.dims == 3 && (oz == 0 || oz == A.nz - 1)));
+        other_shell = (ox == 0 || ox == A.nx - 1 || (((A.zfaces & 1) && oz == 0) || ((A.zfaces & 2) && oz == A.nz - 1)));
     } else {
         const int ox = (int)(t % A.nx); t /= A.nx;
         const int oy = (int)(t % A.ny);

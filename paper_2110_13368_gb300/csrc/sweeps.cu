@@ -89,6 +89,7 @@ struct SweepArgs {
     const int32_t* bc_kind;
     const double* bc_value;
     int dims;              // 3, or 2: the single z layer of a 2-D grid is not a boundary
+    int zfaces;            // z planes on the grid's boundary: bit 0 z = 0, bit 1 z = nz - 1
 };
 
 // MODE 0: plain Thomas (3 flops per element: FMA + MUL forward, FMA back).
@@ -133,7 +134,7 @@ __device__ __forceinline__ void sweep_one_line(const SweepArgs<T>& A, int64_t li
         ox = -1;
         base = (((int64_t)s * A.nz + oz) * A.ny + oy) * A.pitch;
         stride = 1;
-        other_shell = (oy == 0 || oy == A.ny - 1 || (A.dims == 3 && (oz == 0 || oz == A.nz - 1)));
+        other_shell = (oy == 0 || oy == A.ny - 1 || (((A.zfaces & 1) && oz == 0) || ((A.zfaces & 2) && oz == A.nz - 1)));
     } else if (AXIS == 1) {
         int64_t t = line;
         ox = (int)(t % A.nx); t /= A.nx;
@@ -141,7 +142,7 @@ __device__ __forceinline__ void sweep_one_line(const SweepArgs<T>& A, int64_t li
         oy = -1;
         base = (((int64_t)s * A.nz + oz) * A.ny) * A.pitch + ox;
         stride = A.pitch;
-        other_shell = (ox == 0 || ox == A.nx - 1 || (A.dims == 3 && (oz == 0 || oz == A.nz - 1)));
+        other_shell = (ox == 0 || ox == A.nx - 1 || (((A.zfaces & 1) && oz == 0) || ((A.zfaces & 2) && oz == A.nz - 1)));
     } else {
         int64_t t = line;
         ox = (int)(t % A.nx); t /= A.nx;
@@ -390,6 +391,7 @@ SweepArgs<T> make_args(Ctx* c, int axis, int p, const T* r, const T* cr,
     A.bc_kind = c->d_bc_kind;
     A.bc_value = c->d_bc_value;
     A.dims = c->dims;
+    A.zfaces = c->zfaces();
     return A;
 }
 
@@ -680,6 +682,17 @@ bfvm_status launch_xyz(Ctx* c, int p, const T* r, const T* cr, const T* cv)
 
 }  // namespace
 
+// The x and y sweeps of one step in the plain FP64 form, one launch per axis
+// (a z-slab of a decomposed grid: its z sweep is the slabs' own, slab.cu).
+bfvm_status launch_xy_plain64(Ctx* c)
+{
+    bfvm_status st = launch_axis<double, 0, 0>(c, make_args<double>(c, 0, 0, c->coef.r, c->coef.cr,
+                                                                     c->coef.c));
+    if (st != BFVM_OK) return st;
+    return launch_axis<double, 1, 0>(c, make_args<double>(c, 1, 0, c->coef.r, c->coef.cr,
+                                                          c->coef.c));
+}
+
 // Plain FP64 sweep along one axis from `in` to `out` (pitched layout), with
 // Dirichlet mode dir_mode (see k_sweep).  Used by the adjoint.
 bfvm_status launch_sweep_plain64(Ctx* c, int axis, const double* in, double* out,
@@ -717,16 +730,20 @@ bfvm_status build_line_tables(Ctx* c)
         first[0] = 0;
         for (int s = 0; s < c->n_sub; ++s) {
             bool dir = c->bc_kind[s] == BFVM_BC_DIRICHLET;
-            // 2-D variant: z is not a boundary coordinate (the slow other
-            // coordinate of the x and y lines), and there is no z sweep
-            const bool b_dir = dir && !(c->dims == 2 && axis < 2);
-            int ca = dir ? ea - 2 : ea, cb = b_dir ? eb - 2 : eb;
+            // z, the slow other coordinate of the x and y lines, has boundary
+            // planes only where zfaces says so: none in the 2-D variant (which
+            // has no z sweep either), and only the grid's own end planes on a
+            // z-slab of a decomposed grid
+            const int zf = c->zfaces();
+            const int b_lo = (dir && (axis == 2 || (zf & 1))) ? 1 : 0;
+            const int b_hi = (dir && (axis == 2 || (zf & 2))) ? 1 : 0;
+            int ca = dir ? ea - 2 : ea, cb = eb - b_lo - b_hi;
             if (ca < 0) ca = 0;
             if (cb < 0) cb = 0;
             if (c->dims == 2 && axis == 2) ca = cb = 0;
             c->lines_lo_a[axis][s] = dir ? 1 : 0;
             c->lines_cnt_a[axis][s] = ca > 0 ? ca : 1;
-            c->lines_lo_b[axis][s] = b_dir ? 1 : 0;
+            c->lines_lo_b[axis][s] = b_lo;
             first[s + 1] = first[s] + (int64_t)ca * cb;
         }
         BFVM_CUDA(c, c->ensure_line_tables(axis, first));
@@ -805,11 +822,11 @@ bfvm_status launch_shell_fill(Ctx* c, int p_scale)
     if (c->precision == 64)
         persistent::k_shell_fill<double><<<grid, 256, 0, c->stream>>>(
             reinterpret_cast<double*>(c->field), c->nx, c->ny, c->nz, c->n_sub, c->pitch,
-            c->d_bc_kind, c->d_bc_value, c->coef.L, sc, c->dims);
+            c->d_bc_kind, c->d_bc_value, c->coef.L, sc, c->zfaces());
     else
         persistent::k_shell_fill<float><<<grid, 256, 0, c->stream>>>(
             reinterpret_cast<float*>(c->field), c->nx, c->ny, c->nz, c->n_sub, c->pitch,
-            c->d_bc_kind, c->d_bc_value, c->coef.L, nullptr, c->dims);
+            c->d_bc_kind, c->d_bc_value, c->coef.L, nullptr, c->zfaces());
     c->launches += 1;
     BFVM_CUDA(c, cudaGetLastError());
     return BFVM_OK;
