@@ -334,6 +334,22 @@ bfvm_status bfvm_batch_shape(const bfvm_batch* batch, int32_t axis, int32_t* alg
 bfvm_status bfvm_batch_set_shape(bfvm_batch* batch, int32_t axis, int32_t algo, int32_t warps);
 
 /*
+ * Options of a batch (each returns BFVM_EINVAL for an unknown key or value):
+ *   key 1  1: each step of the batch as one persistent launch whose warp
+ *          pairs take (axis, member substrate, 32-line block) tasks of all
+ *          members in order, a task starting once the previous axis of its
+ *          member's substrate is complete, followed in the same launch by
+ *          the members' Dirichlet shells and cell sources (the default where
+ *          its column buffers fit in shared memory; BFVM_EINVAL otherwise);
+ *          0: one launch per sweep phase with the tuned line-block shapes
+ *   key 2  test of the bounded device waits of key 1's launch: v > 0 makes
+ *          every dependency wait unreachable and give up after v polls, so
+ *          bfvm_batch_sync reports BFVM_ETIMEOUT (results of such steps are
+ *          not valid); 0 (the default) is normal operation
+ */
+bfvm_status bfvm_batch_set_option(bfvm_batch* batch, int32_t key, int64_t value);
+
+/*
  * One grid decomposed along z into slabs, one context per slab (an
  * extension: the paper names an MPI+X decomposition of the domain as its
  * way to larger problems, "Introduction and Motivation" and "Future Work").

@@ -42,7 +42,7 @@ EXPORTED = ["bfvm_create", "bfvm_destroy", "bfvm_set_density", "bfvm_get_density
             "bfvm_batch_create", "bfvm_batch_step", "bfvm_batch_sync", "bfvm_batch_destroy",
             "bfvm_batch_last_error", "bfvm_batch_info", "bfvm_batch_shape",
             "bfvm_batch_set_shape", "bfvm_apply_sources_noalloc", "bfvm_set_dirichlet_nodes",
-            "bfvm_update_cells", "bfvm_fp64_fma_rate", "bfvm_create_slab",
+            "bfvm_update_cells", "bfvm_fp64_fma_rate", "bfvm_create_slab", "bfvm_batch_set_option",
             "bfvm_slab_forward", "bfvm_slab_backward", "bfvm_slab_finish"]
 
 
@@ -108,6 +108,8 @@ def load_library(path: Optional[str] = None):
         lib.bfvm_batch_shape.restype = ctypes.c_int
         lib.bfvm_batch_set_shape.argtypes = [_vp, _i32, _i32, _i32]
         lib.bfvm_batch_set_shape.restype = ctypes.c_int
+        lib.bfvm_batch_set_option.argtypes = [_vp, _i32, _i64]
+        lib.bfvm_batch_set_option.restype = ctypes.c_int
         lib.bfvm_apply_sources_noalloc.argtypes = ([_vp] + [_i32] * 4 + [ctypes.c_double] * 2
                                                    + [_i64] + [_vp] * 5 + [_vp])
         lib.bfvm_apply_sources_noalloc.restype = ctypes.c_int
@@ -355,6 +357,14 @@ def bfvm_batch_set_shape(b, axis, algo, warps):
     _check(load_library().bfvm_batch_set_shape(b, int(axis), int(algo), int(warps)), b, batch=True)
 
 
+BATCH_OPT_ONE_LAUNCH = 1
+BATCH_OPT_WAIT_TEST = 2
+
+
+def bfvm_batch_set_option(b, key, value):
+    _check(load_library().bfvm_batch_set_option(b, int(key), int(value)), b, batch=True)
+
+
 def bfvm_create_slab(nx, ny, z_starts, slab, dx_um, dt_min, D, lam, bc_kind, bc_value,
                      stream=None):
     """Context of z-slab `slab` of a grid decomposed along z (slab j holds
@@ -478,6 +488,9 @@ class Batch:
 
     def shape(self, axis):
         return bfvm_batch_shape(self.handle, axis)
+
+    def set_option(self, key, value):
+        bfvm_batch_set_option(self.handle, key, value)
 
     def set_shape(self, axis, algo, warps):
         bfvm_batch_set_shape(self.handle, axis, algo, warps)

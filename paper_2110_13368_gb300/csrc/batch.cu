@@ -63,7 +63,7 @@ bfvm_status launch_block(BatchImpl* b, int len)
     }
     cudaError_t e = cudaGraphLaunch(b->graph, b->stream);
     if (e != cudaSuccess) return bcuda(b, e, "cudaGraphLaunch");
-    int per_step = 3 + (b->n_entries > 0 ? 1 : 0);
+    const int per_step = (b->one_launch && b->one_launch_ok) ? 1 : 3 + (b->n_entries > 0 ? 1 : 0);
     b->launches += (int64_t)len * per_step;
     return BFVM_OK;
 }
@@ -150,6 +150,40 @@ bfvm_status bfvm_batch_sync(bfvm_batch* h)
     cudaError_t e = cudaStreamSynchronize(b->stream);
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) return bcuda(b, e, "batch sync");
+    if (b->d_err) {
+        int flag = 0;
+        e = cudaMemcpy(&flag, b->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return bcuda(b, e, "batch sync");
+        if (flag) {
+            cudaMemset(b->d_err, 0, sizeof(int));
+            return berr(b, BFVM_ETIMEOUT,
+                        "a device wait of the batched step gave up (result not valid)");
+        }
+    }
+    return BFVM_OK;
+}
+
+bfvm_status bfvm_batch_set_option(bfvm_batch* h, int32_t key, int64_t value)
+{
+    if (!h) return BFVM_EINVAL;
+    BatchImpl* b = &h->impl;
+    switch (key) {
+        case 1:
+            if (value != 0 && value != 1) return berr(b, BFVM_EINVAL, "one-launch mode must be 0 or 1");
+            if (value == 1 && !b->one_launch_ok)
+                return berr(b, BFVM_EINVAL, "the one-launch step does not fit this batch");
+            b->one_launch = value == 1;
+            break;
+        case 2:
+            if (value < 0 || value > 1000000) return berr(b, BFVM_EINVAL, "poll limit must be 0..1e6");
+            b->wait_test_polls = (int)value;
+            break;
+        default:
+            return berr(b, BFVM_EINVAL, "unknown batch option key");
+    }
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+    b->graph_len = 0;
     return BFVM_OK;
 }
 

@@ -385,6 +385,25 @@ struct BatchImpl {
     int pcr_e = 1;                // elements per lane of the PCR kernel (ceil(max nx / 32))
     double* d_pcr = nullptr;      // PCR stage tables of all members (FP64)
     float* d_pcr32 = nullptr;     // their FP32 hi/lo splits
+    // One persistent launch per step (sweep_batch_step.cuh): warp pairs take
+    // (axis, member-substrate group, 32-line block) tasks of all members.
+    // one_launch: use it (where it fits); tables built at create.
+    bool one_launch = false;      // the one-launch step is in use
+    bool one_launch_ok = false;   // its tables exist (it fits this batch)
+    int n_groups = 0;             // NS: member-substrate groups
+    int n_btasks = 0;             // tasks of one step
+    int64_t n_epi = 0;            // epilogue chunks of one step
+    int b_slots = 0;              // column buffer slots (G x longest line in groups)
+    int b_pairs = 0;              // warp pairs per CTA
+    size_t b_smem = 0;            // dynamic shared memory per CTA
+    void* d_members = nullptr;    // [period][members] member tables, one set per rescale state
+    void* d_groups = nullptr;     // [3][NS] groups of the task list
+    int64_t* d_epi_first = nullptr;   // [NS + 1] first epilogue chunk of each group
+    int* d_gmem = nullptr;        // [NS] member of each group
+    int* d_btask_first = nullptr; // [3 NS + 1]
+    unsigned* d_bsched = nullptr; // claim, exit, done[3 NS], eclaim, shell_done[NS]
+    int* d_err = nullptr;         // set when a bounded wait of the launch gave up
+    int wait_test_polls = 0;      // > 0: waits cannot end (tests of the bounded waits)
 };
 
 bfvm_status batch_build(BatchImpl* b);

@@ -352,6 +352,7 @@ __global__ void k_sources(T* __restrict__ field, int64_t n_entries, const int64_
 #include "sweep_persistent.cuh"
 #include "sweep_pair.cuh"
 #include "sweep_step.cuh"
+#include "sweep_batch_step.cuh"
 #include "sweep_split.cuh"
 
 namespace bfvm {
@@ -1217,6 +1218,192 @@ __global__ void __launch_bounds__(256) k_batch_pcr_x(const BatchDesc<T>* __restr
 template <typename T>
 bfvm_status batch_tune_t(BatchImpl* b, const std::vector<BatchDesc<T>>& desc);
 
+// Tables of the one-launch batched step (sweep_batch_step.cuh): the groups
+// (member, substrate) of the task list with their line sets, the task and
+// epilogue-chunk offsets, one member table per rescale state, and the
+// scheduling counters.  Leaves one_launch_ok false (the per-phase launches
+// then run) where the kernel does not fit: a member without line tables,
+// column buffers too long for shared memory, too many tasks.
+template <typename T>
+bfvm_status batch_build_one_launch(BatchImpl* b)
+{
+    using namespace persistent;
+    constexpr int G = Groups<T>::G;
+    const int M = (int)b->members.size();
+    std::vector<BGroup> grp;
+    std::vector<int> gmem;
+    int max_n = 1;
+    for (int m = 0; m < M; ++m) {
+        const Ctx* c = b->members[m];
+        if (c->n_sub > 64) return BFVM_OK;
+        for (int a = 0; a < 3; ++a)
+            if (!c->line_tables_ready[a]) return BFVM_OK;
+        for (int s = 0; s < c->n_sub; ++s) gmem.push_back(m);
+        max_n = std::max(max_n, std::max(c->nx, std::max(c->ny, c->nz)));
+    }
+    const int NS = (int)gmem.size();
+    grp.resize((size_t)3 * NS);
+    std::vector<int> tf((size_t)3 * NS + 1, 0);
+    std::vector<int64_t> epi(NS + 1, 0);
+    int64_t t = 0;
+    for (int a = 0; a < 3; ++a) {
+        int g = 0;
+        for (int m = 0; m < M; ++m) {
+            const Ctx* c = b->members[m];
+            const int ext[3] = {c->nx, c->ny, c->nz};
+            for (int s = 0; s < c->n_sub; ++s, ++g) {
+                BGroup q;
+                q.m = m;
+                q.s = s;
+                q.lo_a = c->lines_lo_a[a][s];
+                q.cnt_a = c->lines_cnt_a[a][s];
+                q.lo_b = c->lines_lo_b[a][s];
+                q.n = ext[a];
+                q.dir = c->bc_kind[s] == BFVM_BC_DIRICHLET ? 1 : 0;
+                q.pad = 0;
+                q.n_lines = c->lines_first[a][s + 1] - c->lines_first[a][s];
+                q.v = c->bc_value[s];
+                grp[(size_t)a * NS + g] = q;
+                tf[(size_t)a * NS + g] = (int)t;
+                t += ceil_div(q.n_lines, 32);
+                if (t > ((int64_t)1 << 30)) return BFVM_OK;
+            }
+        }
+    }
+    tf[(size_t)3 * NS] = (int)t;
+    {
+        int g = 0;
+        for (int m = 0; m < M; ++m) {
+            const Ctx* c = b->members[m];
+            const int64_t n_seg = c->src.cap > 0 ? c->src.n_seg : 0;
+            for (int s = 0; s < c->n_sub; ++s, ++g)
+                epi[g + 1] = epi[g] +
+                             (c->bc_kind[s] == BFVM_BC_DIRICHLET ? epi_shell_chunks(c->nx, c->ny, c->nz) : 0) +
+                             epi_src_chunks(n_seg);
+        }
+    }
+    if (epi[NS] > ((int64_t)1 << 30)) return BFVM_OK;
+    const int ns = (int)ceil_div(max_n, G) * G;
+    const BatchSmem sm = batch_smem<T>(NS, ns);
+    const size_t optin = b->members[0]->smem_optin;
+    if (optin < sm.tab + sm.pair + 64) return BFVM_OK;
+    int pairs = (int)((optin - sm.tab - 64) / sm.pair);
+    if (pairs > Groups<T>::MAX_PAIRS) pairs = Groups<T>::MAX_PAIRS;
+    // member tables of every rescale state of the batch
+    const int P = b->period;
+    std::vector<BMember<T>> mem((size_t)P * M);
+    for (int p = 0; p < P; ++p) {
+        const bool renorm = b->rescaled && p == P - 1;
+        int g0 = 0;
+        for (int m = 0; m < M; ++m) {
+            Ctx* c = b->members[m];
+            const T* r;
+            const T* cr;
+            const T* cv;
+            if (sizeof(T) == 8) {
+                r = reinterpret_cast<const T*>(c->coef.r);
+                cr = reinterpret_cast<const T*>(c->coef.cr);
+                cv = reinterpret_cast<const T*>(c->coef.c);
+            } else {
+                r = reinterpret_cast<const T*>(c->coef.r32);
+                cr = reinterpret_cast<const T*>(c->coef.cr32);
+                cv = reinterpret_cast<const T*>(c->coef.c32);
+            }
+            BMember<T>& d = mem[(size_t)p * M + m];
+            d = BMember<T>{};
+            for (int a = 0; a < 3; ++a) d.A[a] = make_args<T>(c, a, b->rescaled ? p : 0, r, cr, cv);
+            EpiArgs<T>& E = d.E;
+            E.field = reinterpret_cast<T*>(c->field);
+            E.nx = c->nx;
+            E.ny = c->ny;
+            E.nz = c->nz;
+            E.pitch = c->pitch;
+            E.L = c->coef.L;
+            E.sc = (!b->rescaled || renorm) ? nullptr : d.A[0].sc_p1;
+            E.n_seg = c->src.cap > 0 ? c->src.n_seg : 0;
+            E.d_nseg = nullptr;
+            E.off = c->src.off;
+            E.alpha = c->src.alpha;
+            E.beta = c->src.beta;
+            E.vox = c->src.vox;
+            E.sub = c->src.sub;
+            d.n_sub = c->n_sub;
+            d.g0 = g0;
+            g0 += c->n_sub;
+        }
+    }
+    cudaError_t e;
+    const size_t n_sched = 2 + (size_t)3 * NS + 1 + (size_t)NS;
+    if ((e = cudaMalloc(&b->d_members, sizeof(BMember<T>) * mem.size())) != cudaSuccess ||
+        (e = cudaMalloc(&b->d_groups, sizeof(BGroup) * grp.size())) != cudaSuccess ||
+        (e = cudaMalloc(&b->d_epi_first, sizeof(int64_t) * epi.size())) != cudaSuccess ||
+        (e = cudaMalloc(&b->d_gmem, sizeof(int) * gmem.size())) != cudaSuccess ||
+        (e = cudaMalloc(&b->d_btask_first, sizeof(int) * tf.size())) != cudaSuccess ||
+        (e = cudaMalloc(&b->d_bsched, sizeof(unsigned) * n_sched)) != cudaSuccess ||
+        (e = cudaMalloc(&b->d_err, sizeof(int))) != cudaSuccess)
+        return BFVM_ENOMEM;
+    // synchronous copies: built once at create, outside any capture
+    if ((e = cudaMemcpy(b->d_members, mem.data(), sizeof(BMember<T>) * mem.size(),
+                        cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(b->d_groups, grp.data(), sizeof(BGroup) * grp.size(),
+                        cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(b->d_epi_first, epi.data(), sizeof(int64_t) * epi.size(),
+                        cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(b->d_gmem, gmem.data(), sizeof(int) * gmem.size(),
+                        cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(b->d_btask_first, tf.data(), sizeof(int) * tf.size(),
+                        cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemset(b->d_bsched, 0, sizeof(unsigned) * n_sched)) != cudaSuccess ||
+        (e = cudaMemset(b->d_err, 0, sizeof(int))) != cudaSuccess)
+        return BFVM_ECUDA;
+    b->n_groups = NS;
+    b->n_btasks = (int)t;
+    b->n_epi = epi[NS];
+    b->b_slots = ns;
+    b->b_pairs = pairs;
+    b->b_smem = sm.tab + sm.pair * pairs;
+    b->one_launch_ok = true;
+    b->one_launch = true;
+    return BFVM_OK;
+}
+
+// One step of the batch as one launch in rescale state p (sweep_batch_step.cuh).
+template <typename T, int MXY, int MZ>
+bfvm_status batch_step_one_launch(BatchImpl* b, int p)
+{
+    using namespace persistent;
+    if (b->n_btasks == 0 && b->n_epi == 0) return BFVM_OK;
+    const int NS = b->n_groups;
+    StepSched Q;
+    Q.claim = b->d_bsched;
+    Q.exit_count = b->d_bsched + 1;
+    Q.done = b->d_bsched + 2;
+    Q.task_first = b->d_btask_first;
+    Q.err = b->d_err;
+    Q.n_sub = NS;
+    Q.n_tasks = b->n_btasks;
+    Q.max_polls = b->wait_test_polls > 0 ? (unsigned)b->wait_test_polls : kMaxPolls;
+    Q.extra_need = b->wait_test_polls > 0 ? 1u : 0u;
+    Q.eclaim = b->d_bsched + 2 + 3 * NS;
+    Q.shell_done = Q.eclaim + 1;
+    Q.n_epi_chunks = (int)b->n_epi;
+    const int pairs = b->b_pairs;
+    int64_t grid = ceil_div(std::max<int64_t>(b->n_btasks, 1), pairs);
+    grid = std::max<int64_t>(grid, ceil_div(b->n_epi, 8 * pairs));
+    const int sms = b->members[0]->sm_count;
+    if (grid > sms) grid = sms;
+    auto kern = k_batch_step_pair<T, MXY, MZ>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->b_smem) !=
+        cudaSuccess)
+        return BFVM_ECUDA;
+    const size_t M = b->members.size();
+    const BMember<T>* D = reinterpret_cast<const BMember<T>*>(b->d_members) + (size_t)p * M;
+    kern<<<(unsigned)grid, 64 * pairs, b->b_smem, b->stream>>>(
+        D, reinterpret_cast<const BGroup*>(b->d_groups), b->d_epi_first, b->d_gmem, Q, b->b_slots);
+    b->launches += 1;
+    return cudaGetLastError() == cudaSuccess ? BFVM_OK : BFVM_ECUDA;
+}
+
 template <typename T>
 bfvm_status batch_build_t(BatchImpl* b)
 {
@@ -1318,7 +1505,9 @@ bfvm_status batch_build_t(BatchImpl* b)
     if ((e = cudaMemcpy(b->d_entry_prefix, prefix.data(), sizeof(int64_t) * (M + 1),
                         cudaMemcpyHostToDevice)) != cudaSuccess)
         return BFVM_ECUDA;
-    return batch_tune_t<T>(b, desc);
+    bfvm_status st = batch_tune_t<T>(b, desc);
+    if (st != BFVM_OK) return st;
+    return batch_build_one_launch<T>(b);
 }
 
 // Largest Thomas CTA (warps of one 32-line block each) whose line buffers
@@ -1473,6 +1662,7 @@ template <typename T, int MODE_Z>
 bfvm_status batch_step_t(BatchImpl* b, int p)
 {
     constexpr int M = MODE_Z == 0 ? 0 : 1;
+    if (b->one_launch && b->one_launch_ok) return batch_step_one_launch<T, M, MODE_Z>(b, p);
     bfvm_status st;
     if ((st = batch_axis<T, 0, M>(b, p)) != BFVM_OK) return st;
     if ((st = batch_axis<T, 1, M>(b, p)) != BFVM_OK) return st;
@@ -1533,6 +1723,15 @@ void batch_free(BatchImpl* b)
     for (int a = 0; a < 3; ++a)
         if (b->d_tasks[a]) cudaFree(b->d_tasks[a]);
     if (b->d_entry_prefix) cudaFree(b->d_entry_prefix);
+    void* one[] = {b->d_members, b->d_groups, b->d_epi_first, b->d_gmem, b->d_btask_first,
+                   b->d_bsched, b->d_err};
+    for (void* q : one)
+        if (q) cudaFree(q);
+    b->d_members = b->d_groups = nullptr;
+    b->d_epi_first = nullptr;
+    b->d_gmem = b->d_btask_first = b->d_err = nullptr;
+    b->d_bsched = nullptr;
+    b->one_launch_ok = b->one_launch = false;
     if (b->graph) cudaGraphExecDestroy(b->graph);
     b->d_desc = nullptr;
     b->d_entry_prefix = nullptr;

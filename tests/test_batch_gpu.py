@@ -127,6 +127,7 @@ def test_batch_line_block_shapes_match_oracle(bf, precision, variant, tol, x_alg
         for s in sims:
             s.set_option(bf.OPT_VARIANT, variant)
     batch = bf.Batch(sims)
+    batch.set_option(bf.BATCH_OPT_ONE_LAUNCH, 0)   # the tuned per-phase launches
     batch.set_shape(0, x_algo, x_warps)
     batch.set_shape(1, 0, yz_warps)
     batch.set_shape(2, 0, yz_warps)
@@ -173,3 +174,69 @@ def test_batch_autotuner_measures_and_leaves_fields(bf):
     b2.close()
     for s in sims + big:
         s.close()
+
+
+@pytest.mark.parametrize("precision,variant,tol", [(64, 1, 1e-12), (64, 0, 1e-12), (32, None, 1e-5)])
+def test_one_launch_batch_matches_oracle_and_per_phase_launches(bf, precision, variant, tol):
+    """The one-launch batched step (every member's x, y, z tasks, shells and
+    sources in one persistent launch) against each member's oracle run and
+    against the per-phase launches of the same batch, in the rescaled and
+    plain FP64 forms and in FP32; members of uneven shapes, a Dirichlet
+    member, lines of 1 to 128 voxels; steps crossing the rescale period."""
+    probs = small_batch(n_inst=6, steps=13, seed=11) + pcr_batch(steps=13)
+    results = []
+    for one in (1, 0):
+        sims = [bf.Sim.from_problem(p, precision=precision) for p in probs]
+        if variant is not None:
+            for s in sims:
+                s.set_option(bf.OPT_VARIANT, variant)
+        if precision == 64 and variant == 1:
+            for s in sims:
+                s.set_option(bf.OPT_PERIOD, 4)
+        batch = bf.Batch(sims)
+        batch.set_option(bf.BATCH_OPT_ONE_LAUNCH, one)
+        launches0 = batch.info()["launches"]
+        for n in (5, 3, 5):
+            batch.step(n)
+        batch.sync()
+        per_step = (batch.info()["launches"] - launches0) / 13
+        if one:
+            assert per_step == 1.0, per_step
+        results.append([s.get_density().double().cpu().numpy() for s in sims])
+        batch.close()
+        for s in sims:
+            s.close()
+    for p, a, b in zip(probs, *results):
+        ref = oracle.run(p)
+        assert np.all(rel_inf(a, ref) <= tol), (p.name, rel_inf(a, ref))
+        assert np.all(rel_inf(a, b) <= tol), (p.name, rel_inf(a, b))
+
+
+def test_one_launch_batch_wait_gives_up_with_status(bf):
+    """Batch option 2 makes every dependency wait of the one-launch step
+    unreachable: the waits give up after the given polls, bfvm_batch_sync
+    reports BFVM_ETIMEOUT, and after the option is cleared steps from a fresh
+    field are correct again."""
+    import torch
+    probs = small_batch(n_inst=4, steps=2, seed=13)
+    sims = [bf.Sim.from_problem(p) for p in probs]
+    batch = bf.Batch(sims)
+    batch.set_option(bf.BATCH_OPT_WAIT_TEST, 200)
+    batch.step(1)
+    with pytest.raises(bf.BfvmError) as ei:
+        batch.sync()
+    assert ei.value.status == 5
+    batch.set_option(bf.BATCH_OPT_WAIT_TEST, 0)
+    batch.close()
+    for p, s in zip(probs, sims):
+        s.set_density(torch.as_tensor(p.rho0, dtype=s.dtype, device="cuda"))
+    batch = bf.Batch(sims)
+    batch.step(2)
+    batch.sync()
+    for p, s in zip(probs, sims):
+        got = s.get_density().cpu().numpy()
+        assert np.all(rel_inf(got, oracle.run(p)) <= 1e-12), p.name
+    batch.close()
+    for s in sims:
+        s.close()
+
