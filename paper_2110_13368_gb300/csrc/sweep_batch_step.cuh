@@ -16,9 +16,10 @@
 // the reads of task k + 1's arguments (k = the pair's task count) before it
 // eliminates task k and stores them after; B reads the slot of the task it
 // back-substitutes.  Three slots rotate, so F never writes the slot B is
-// reading.  The coefficient rows stay in global memory (every lane of a task
-// reads the same row: one L1 broadcast per element); a group's line set is
-// one entry of the group table.
+// reading.  The task's coefficient rows are staged the same way: F copies
+// them (cp.async, with the task's first column copies) into one of three
+// rotating shared slots, where both warps read them as broadcasts.  A
+// group's line set is one entry of the group table.
 //
 // Epilogue: the Dirichlet shell and the cell sources of every group, in
 // chunks claimed after the sweep tasks, each waiting on the last swept axis
@@ -131,23 +132,6 @@ __device__ __forceinline__ LinePre issue_line_b(const SweepArgs<T>& A, const BGr
     return P;
 }
 
-// Coefficient tables of a member's sweep (global memory, [s][L])
-template <typename T, int MODE>
-__device__ __forceinline__ CoefTabs<T> member_tabs(const SweepArgs<T>& A)
-{
-    CoefTabs<T> K;
-    if (MODE >= 1) {
-        K.a = reinterpret_cast<const T*>(A.fa);
-        K.b = reinterpret_cast<const T*>(A.fb);
-    } else {
-        K.a = A.r;
-        K.b = A.cr;
-    }
-    K.a_lo = (MODE == 0 && sizeof(T) == 4) ? A.r_lo : K.a;
-    K.b_lo = (MODE == 0 && sizeof(T) == 4) ? A.cr_lo : K.b;
-    return K;
-}
-
 // What a pair's two warps share in the batched kernel.
 template <typename T>
 struct BPairShared {
@@ -157,10 +141,81 @@ struct BPairShared {
     int* hs;
     T* handover;
     double* hinv;          // [32] MODE 2: inverse of the other axes' scales of B's lines
-    volatile int* ho;      // task handed over, next task, paired (0/1), pair-barrier meetings
+    volatile int* ho;      // task handed over, next task, paired (0/1), pair-barrier
+                           // meetings, and the handed task's axis, group, block
     T* W;
+    unsigned char* cslot;  // [3] coefficient rows of the pair's tasks k mod 3
+    size_t cslot_bytes;
     int ns, lane, bar_id;
 };
+
+// Coefficient rows of one task staged in shared memory: the forward and
+// backward coefficients (fa / fb of the rescaled form, r / cr of the plain
+// form), their FP32 low parts, and (renormalising z sweep) the inverse
+// output scales, each indexed by the element k of the line.
+template <typename T>
+__host__ __device__ constexpr int coef_rows()
+{
+    return sizeof(T) == 4 ? 4 : 2;
+}
+
+template <typename T>
+__host__ __device__ inline size_t cslot_size(int n_slots)
+{
+    return round16((size_t)coef_rows<T>() * n_slots * sizeof(T) + (size_t)n_slots * sizeof(double));
+}
+
+template <typename T, int AXIS, int MODE>
+__device__ __forceinline__ CoefRow<T> slot_coef_row(const SweepArgs<T>& A, const unsigned char* cs,
+                                                    int ns, int s)
+{
+    const T* t = reinterpret_cast<const T*>(cs);
+    CoefRow<T> C;
+    C.a = t;
+    C.b = t + ns;
+    C.a_lo = coef_rows<T>() == 4 ? t + 2 * ns : t;
+    C.b_lo = coef_rows<T>() == 4 ? t + 3 * ns : t + ns;
+    C.o = reinterpret_cast<const double*>(t + coef_rows<T>() * ns);
+    C.c = (T)0;
+    C.c_lo = (T)0;
+    if (MODE == 0) {
+        C.c = A.cvec[s * 3 + AXIS];
+        if (sizeof(T) == 4) C.c_lo = A.cvec_lo[s * 3 + AXIS];
+    }
+    return C;
+}
+
+// F: copy (cp.async, in the commit group of the task's first column copies)
+// the coefficient rows of substrate s of a task on axis `axis` into slot cs
+template <typename T, int MXY, int MZ>
+__device__ __forceinline__ void stage_coefs(const SweepArgs<T>& A, int axis, int s,
+                                            unsigned char* cs, int ns, int lane)
+{
+    T* t = reinterpret_cast<T*>(cs);
+    const int mode = axis == 2 ? MZ : MXY;
+    const int64_t row = (int64_t)s * A.L + A.axis_off;
+    const T* a;
+    const T* b;
+    if (mode >= 1) {
+        a = reinterpret_cast<const T*>(A.fa) + row;
+        b = reinterpret_cast<const T*>(A.fb) + row;
+    } else {
+        a = A.r + row;
+        b = A.cr + row;
+    }
+    for (int i = lane; i < A.n; i += 32) {
+        cp_async_elem(t + i, a + i);
+        cp_async_elem(t + ns + i, b + i);
+        if (coef_rows<T>() == 4) {
+            cp_async_elem(t + 2 * ns + i, A.r_lo + row + i);
+            cp_async_elem(t + 3 * ns + i, A.cr_lo + row + i);
+        }
+        if (mode == 2) {
+            double* o = reinterpret_cast<double*>(t + coef_rows<T>() * ns);
+            cp_async_elem(o + i, A.isc_p1 + row + i);
+        }
+    }
+}
 
 struct BFState {
     int t, tn, k;
@@ -186,6 +241,39 @@ struct ArgsCopy {
         if (lane < args_words<T>()) reinterpret_cast<uint64_t*>(dst)[lane] = w;
     }
 };
+
+// F: copies and forward elimination of a task with coefficient row C (see
+// f_task of the single-context step)
+template <typename T, int AXIS, int MODE>
+__device__ __forceinline__ T f_task_b(const SweepArgs<T>& A, const Line& L, const CoefRow<T>& C,
+                                      T* W, int ns, int lane, int bar_id, int64_t* rbF, int q,
+                                      bool solo, int iters)
+{
+    constexpr int G = Groups<T>::G;
+    PairSweeper<T, AXIS, MODE> sw{A, W, A.field, A.field, axis_stride(A, AXIS), A.n, ns, lane, bar_id};
+    __syncwarp();
+    rbF[lane] = L.base;
+    __syncwarp();
+    int64_t rv[G];
+    sw.load_rows(rbF, rv);
+    T prev;
+    if (solo) {
+        const int gcount = (A.n + G - 1) / G;
+        for (int g = 0; g < gcount; ++g) {
+            if (q) sw.template copy_group<1>(L, rbF, g);
+            else sw.template copy_group<0>(L, rbF, g);
+        }
+        cp_async_commit();
+        cp_async_wait<0>();
+        __syncwarp();
+        prev = q ? sw.template f_solo<1>(L, C) : sw.template f_solo<0>(L, C);
+    } else {
+        prev = q ? sw.template f_block<1>(L, C, rbF, rv, iters)
+                 : sw.template f_block<0>(L, C, rbF, rv, iters);
+        cp_async_wait<0>();
+    }
+    return prev;
+}
 
 template <typename T>
 __device__ __forceinline__ int line_groups(int n)
@@ -227,9 +315,10 @@ __device__ __forceinline__ void f_axis_b(BFState& f, const BMember<T>* Dm, const
             gn = grp[(int64_t)rn.a * NS + rn.s];
             cp.load(Dm, gmem[rn.s], rn.a, P.lane);
         }
-        const CoefTabs<T> K = member_tabs<T, MODE>(A);
-        const T prev = f_task<T, AXIS, MODE>(A, L, A.field, K, P.W, P.ns, P.lane, P.bar_id, P.rbF,
-                                             f.k & 1, f.solo, f.iters);
+        const CoefRow<T> C =
+            slot_coef_row<T, AXIS, MODE>(A, P.cslot + (f.k % 3) * P.cslot_bytes, P.ns, L.s);
+        const T prev = f_task_b<T, AXIS, MODE>(A, L, C, P.W, P.ns, P.lane, P.bar_id, P.rbF,
+                                               f.k & 1, f.solo, f.iters);
         bool paired = false;
         if (has_next) {
             if (dep < 0) {
@@ -252,6 +341,9 @@ __device__ __forceinline__ void f_axis_b(BFState& f, const BMember<T>* Dm, const
             P.ho[1] = f.tn;
             P.ho[2] = paired ? 1 : 0;
             P.ho[3] = iters;
+            P.ho[4] = r.a;
+            P.ho[5] = r.s;
+            P.ho[6] = r.j;
         }
         if (has_next) cp.store(&P.slot[(f.k + 1) % 3], P.lane);
         pair_sync(P.bar_id);                            // hand-over of task f.t
@@ -273,9 +365,10 @@ __device__ __forceinline__ void f_axis_b(BFState& f, const BMember<T>* Dm, const
         f.tn = t2 < (unsigned)NT ? (int)t2 : NT;
         f.r = rn;
         ++f.k;
-        // the next task's lines, from its slot (stored above; the barrier
-        // ordered the stores of every lane)
+        // the next task's lines and coefficient rows, from its argument slot
+        // (stored above; the barrier ordered the stores of every lane)
         const SweepArgs<T>& An = P.slot[f.k % 3];
+        stage_coefs<T, MXY, MZ>(An, rn.a, gn.s, P.cslot + (f.k % 3) * P.cslot_bytes, P.ns, P.lane);
         if (rn.a == 0) f.pre = issue_line_b<T, 0, MXY>(An, gn, rn.j, P.lane);
         else if (rn.a == 1) f.pre = issue_line_b<T, 1, MXY>(An, gn, rn.j, P.lane);
         else f.pre = issue_line_b<T, 2, MZ>(An, gn, rn.j, P.lane);
@@ -288,6 +381,7 @@ struct BBState {
     bool paired;
     int k;
     int iters;
+    TaskRef r;    // decoded t (handed over by F)
     T x;
 };
 
@@ -299,7 +393,7 @@ __device__ __forceinline__ void b_axis_b(BBState<T>& b, const int* tf, const Ste
     constexpr int G = Groups<T>::G;
     const int NT = Q.n_tasks;
     while (b.t < NT) {
-        const TaskRef r = decode_task_b(tf, Q.n_sub, b.t);
+        const TaskRef r = b.r;
         if (r.a != AXIS) return;
         const bool more = b.t_next < NT;
         const bool paired = more && b.paired;
@@ -317,7 +411,8 @@ __device__ __forceinline__ void b_axis_b(BBState<T>& b, const int* tf, const Ste
             L.dir = false;
             L.end0 = L.end1 = 0.0;
             L.inv_other = (MODE == 2) ? P.hinv[lane] : 1.0;
-            const CoefRow<T> C = step_coef_row<T, AXIS, MODE>(A, member_tabs<T, MODE>(A), L.s);
+            const CoefRow<T> C =
+                slot_coef_row<T, AXIS, MODE>(A, P.cslot + (b.k % 3) * P.cslot_bytes, P.ns, L.s);
             int64_t rv[G];
             sw.load_rows(P.rbB, rv);
             if (b.k & 1) sw.template b_block<1>(L, C, b.x, P.rbB, rv, paired, b.iters, rel);
@@ -333,6 +428,9 @@ __device__ __forceinline__ void b_axis_b(BBState<T>& b, const int* tf, const Ste
         b.t_next = P.ho[1];
         b.paired = P.ho[2] != 0;
         b.iters = P.ho[3];
+        b.r.a = P.ho[4];
+        b.r.s = P.ho[5];
+        b.r.j = P.ho[6];
         b.x = P.handover[P.lane];
         ++b.k;
     }
@@ -426,19 +524,26 @@ __device__ __forceinline__ void step_epilogue_b(const StepSched& Q, const BMembe
 // Dynamic shared memory of the batched kernel: task_first [3 NS + 1] and
 // the group -> member map [NS] (ints), then per pair: the column buffer
 // (n_slots x 32), 4 x 32 row / line bases, 32 chain values, 32 inverse
-// scales, 4 hand-over words, 32 substrates, 3 argument slots.
+// scales, 8 hand-over words, 32 substrates, 3 argument slots and 3
+// coefficient slots.
 struct BatchSmem {
     size_t tab, pair;
 };
+
+template <typename T>
+__host__ __device__ inline size_t pair_head_bytes(int n_slots)
+{
+    return round16((size_t)n_slots * 32 * sizeof(T) + 4 * 32 * sizeof(int64_t) + 32 * sizeof(T) +
+                   32 * sizeof(double) + 8 * sizeof(int) + 32 * sizeof(int));
+}
 
 template <typename T>
 __host__ __device__ inline BatchSmem batch_smem(int ns_groups, int n_slots)
 {
     BatchSmem m;
     m.tab = round16(((size_t)3 * ns_groups + 1 + ns_groups) * sizeof(int));
-    m.pair = round16((size_t)n_slots * 32 * sizeof(T) + 4 * 32 * sizeof(int64_t) +
-                     32 * sizeof(T) + 32 * sizeof(double) + 4 * sizeof(int) + 32 * sizeof(int)) +
-             round16(3 * sizeof(SweepArgs<T>));
+    m.pair = pair_head_bytes<T>(n_slots) + round16(3 * sizeof(SweepArgs<T>)) +
+             3 * cslot_size<T>(n_slots);
     return m;
 }
 
@@ -474,10 +579,9 @@ __global__ void __launch_bounds__(64 * Groups<T>::MAX_PAIRS, 1)
     T* handover = reinterpret_cast<T*>(rbF + 128);
     double* hinv = reinterpret_cast<double*>(handover + 32);
     volatile int* ho = reinterpret_cast<volatile int*>(hinv + 32);
-    int* hs = const_cast<int*>(ho) + 4;
-    SweepArgs<T>* slot = reinterpret_cast<SweepArgs<T>*>(
-        my + round16((size_t)n_slots * 32 * sizeof(T) + 4 * 32 * sizeof(int64_t) +
-                     32 * sizeof(T) + 32 * sizeof(double) + 4 * sizeof(int) + 32 * sizeof(int)));
+    int* hs = const_cast<int*>(ho) + 8;
+    SweepArgs<T>* slot = reinterpret_cast<SweepArgs<T>*>(my + pair_head_bytes<T>(n_slots));
+    unsigned char* cslot = my + pair_head_bytes<T>(n_slots) + round16(3 * sizeof(SweepArgs<T>));
 
     BPairShared<T> P;
     P.slot = slot;
@@ -488,6 +592,8 @@ __global__ void __launch_bounds__(64 * Groups<T>::MAX_PAIRS, 1)
     P.hinv = hinv;
     P.ho = ho;
     P.W = W;
+    P.cslot = cslot;
+    P.cslot_bytes = cslot_size<T>(n_slots);
     P.ns = n_slots;
     P.lane = lane;
     P.bar_id = 1 + pair;
@@ -507,6 +613,7 @@ __global__ void __launch_bounds__(64 * Groups<T>::MAX_PAIRS, 1)
             cp.store(&slot[0], lane);
             __syncwarp();
             task_wait(Q, tf, f.r, lane);
+            stage_coefs<T, MXY, MZ>(slot[0], f.r.a, g0.s, cslot, n_slots, lane);
             if (f.r.a == 0) f.pre = issue_line_b<T, 0, MXY>(slot[0], g0, f.r.j, lane);
             else if (f.r.a == 1) f.pre = issue_line_b<T, 1, MXY>(slot[0], g0, f.r.j, lane);
             else f.pre = issue_line_b<T, 2, MZ>(slot[0], g0, f.r.j, lane);
@@ -516,6 +623,7 @@ __global__ void __launch_bounds__(64 * Groups<T>::MAX_PAIRS, 1)
                 ho[1] = NT;
                 ho[2] = 0;
                 ho[3] = 0;
+                ho[4] = 3;   // no axis: B's loops end at once
             }
             pair_sync(P.bar_id);                        // nothing for B
         }
@@ -529,6 +637,9 @@ __global__ void __launch_bounds__(64 * Groups<T>::MAX_PAIRS, 1)
         b.t_next = ho[1];
         b.paired = ho[2] != 0;
         b.iters = ho[3];
+        b.r.a = ho[4];
+        b.r.s = ho[5];
+        b.r.j = ho[6];
         b.x = handover[lane];
         b.k = 0;
         b_axis_b<T, 0, MXY>(b, tf, Q, P);
