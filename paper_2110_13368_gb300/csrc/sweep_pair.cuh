@@ -26,11 +26,11 @@
 namespace bfvm {
 namespace persistent {
 
-template <typename T, int AXIS, int MODE>
+template <typename T, int AXIS, int MODE, int LAG = Groups<T>::PAIR_LAG>
 struct PairSweeper {
     static constexpr int G = Groups<T>::G;
     static constexpr int ROWS = Groups<T>::ROWS;
-    static constexpr int LG = Groups<T>::PAIR_LAG;   // copy-ahead distance of F, in groups
+    static constexpr int LG = LAG;   // copy-ahead distance of F, in groups
 
     const SweepArgs<T>& A;
     T* W;
