@@ -633,13 +633,27 @@ __global__ void __launch_bounds__(64 * Groups<T>::MAX_PAIRS, 1)
     if (!is_b) {
         BFState f;
         {
+            // the first task and the next one: from the first claimed chunk,
+            // or (a chunk of one task) from a second claim
+            constexpr unsigned C = (unsigned)BatchChunk<T>::C;
             unsigned c0 = 0;
-            if (lane == 0) c0 = atomicAdd(Q.claim, (unsigned)BatchChunk<T>::C);
+            if (lane == 0) c0 = atomicAdd(Q.claim, C);
             c0 = __shfl_sync(0xffffffffu, c0, 0);
             f.t = c0 < (unsigned)NT ? (int)c0 : NT;
-            f.tn = c0 + 1u < (unsigned)NT ? (int)c0 + 1 : NT;
-            f.cnext = (int)min((unsigned)NT, c0 + 2u);
-            f.cend = (int)min((unsigned)NT, c0 + (unsigned)BatchChunk<T>::C);
+            f.cnext = (int)min((unsigned)NT, c0 + 1u);
+            f.cend = (int)min((unsigned)NT, c0 + C);
+            if (f.cnext < f.cend) {
+                f.tn = f.cnext++;
+            } else if (f.t < NT) {
+                unsigned c1 = 0;
+                if (lane == 0) c1 = atomicAdd(Q.claim, C);
+                c1 = __shfl_sync(0xffffffffu, c1, 0);
+                f.tn = c1 < (unsigned)NT ? (int)c1 : NT;
+                f.cnext = (int)min((unsigned)NT, c1 + 1u);
+                f.cend = (int)min((unsigned)NT, c1 + C);
+            } else {
+                f.tn = NT;
+            }
         }
         f.k = 0;
         f.solo = true;

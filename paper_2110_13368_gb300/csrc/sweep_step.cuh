@@ -420,17 +420,26 @@ __device__ __forceinline__ int64_t shell_count(const EpiArgs<T>& E)
 }
 
 template <typename T>
-__device__ __forceinline__ void shell_voxel(const EpiArgs<T>& E, int s, double v, int64_t t)
+__device__ __forceinline__ void shell_voxel(const EpiArgs<T>& E, int s, double v, int64_t t64)
 {
-    const int64_t fz = 2 * (int64_t)E.nx * E.ny, fy = 2 * (int64_t)E.nx * E.nz;
+    // 32-bit index arithmetic (64-bit division is far slower): the kernels
+    // that run this epilogue hold a whole line of every axis in one shared
+    // column buffer, so no extent exceeds a few thousand voxels and the shell
+    // has far fewer than 2^31 voxels
+    const int nx = E.nx, ny = E.ny, nz = E.nz;
+    const int fz = 2 * nx * ny, fy = 2 * nx * nz;
+    int t = (int)t64;
     int x, y, z;
     if (t < fz) {
-        x = (int)(t % E.nx); y = (int)((t / E.nx) % E.ny); z = (t / ((int64_t)E.nx * E.ny)) ? E.nz - 1 : 0;
+        const int q = t / nx;
+        x = t - q * nx; y = q % ny; z = (q / ny) ? nz - 1 : 0;
     } else if ((t -= fz) < fy) {
-        x = (int)(t % E.nx); z = (int)((t / E.nx) % E.nz); y = (t / ((int64_t)E.nx * E.nz)) ? E.ny - 1 : 0;
+        const int q = t / nx;
+        x = t - q * nx; z = q % nz; y = (q / nz) ? ny - 1 : 0;
     } else {
         t -= fy;
-        y = (int)(t % E.ny); z = (int)((t / E.ny) % E.nz); x = (t / ((int64_t)E.ny * E.nz)) ? E.nx - 1 : 0;
+        const int q = t / ny;
+        y = t - q * ny; z = q % nz; x = (q / nz) ? nx - 1 : 0;
     }
     if (E.sc) {
         const double* q = E.sc + (int64_t)s * E.L;
