@@ -50,26 +50,31 @@ __global__ void k_pitched_to_dense(const double* __restrict__ src, double* __res
     dst[e] = src[r * pitch + x];
 }
 
-// out = in with the Dirichlet shell set to `value` (set = true) or zeroed
-__global__ void k_shell(const double* __restrict__ in, double* __restrict__ out, int nx,
-                        int ny, int nz, int n_sub, int64_t pitch,
-                        const int32_t* __restrict__ kind, const double* __restrict__ value,
-                        bool set)
+// out = in with the Dirichlet shell set to `value` (set = true) or zeroed;
+// out2 (may be null) receives the same values.  One thread per voxel of the
+// pitched field; n_sub nz ny nx < 2^32 (32-bit index arithmetic).
+__global__ void k_shell(const double* __restrict__ in, double* __restrict__ out,
+                        double* __restrict__ out2, int nx, int ny, int nz, int n_sub,
+                        int64_t pitch, const int32_t* __restrict__ kind,
+                        const double* __restrict__ value, bool set)
 {
-    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    int64_t n = (int64_t)n_sub * nz * ny * nx;
+    const uint32_t n = (uint32_t)n_sub * nz * ny * nx;
+    const uint32_t e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= n) return;
-    int x = (int)(e % nx);
-    int64_t t = e / nx;
-    int y = (int)(t % ny); t /= ny;
-    int z = (int)(t % nz);
-    int s = (int)(t / nz);
-    int64_t o = (((int64_t)s * nz + z) * ny + y) * pitch + x;
+    const uint32_t r = e / (uint32_t)nx;       // row (s, z, y)
+    const int x = (int)(e - r * (uint32_t)nx);
+    const uint32_t q = r / (uint32_t)ny;
+    const int y = (int)(r - q * (uint32_t)ny);
+    const uint32_t s_ = q / (uint32_t)nz;
+    const int z = (int)(q - s_ * (uint32_t)nz);
+    const int s = (int)s_;
+    const int64_t o = (int64_t)r * pitch + x;
     double v = in[o];
     if (kind[s] == BFVM_BC_DIRICHLET &&
         (x == 0 || x == nx - 1 || y == 0 || y == ny - 1 || z == 0 || z == nz - 1))
         v = set ? value[s] : 0.0;
     out[o] = v;
+    if (out2) out2[o] = v;
 }
 
 // forward composed maps, in place: rho <- alpha rho + beta
@@ -121,77 +126,91 @@ __global__ void k_sources_adjoint(double* __restrict__ g, const double* __restri
     g[o] = gr;
 }
 
-// Per-block partial sums of <g, v> and <g, L_axis v> over substrate s.
-__global__ void k_param_dots(const double* __restrict__ g, const double* __restrict__ v,
-                             int axis, int s, int nx, int ny, int nz, int64_t pitch,
-                             double* __restrict__ partial)
+// The parameter terms of one adjoint step for substrate s, all three axes
+// in one pass: for axis a, <g_a, v_a> and <g_a, L_a v_a>, with g_a the
+// adjoint after the solve of axis a (gz, gy, gx) and v_a that axis' raw
+// forward solve output (vx, vy, vz), L_a the zero-flux line Laplacian along
+// a.  Per-block partial sums in a fixed order; the last block to finish (a
+// completion counter) adds the partials in block order and applies, for
+// axes z, y, x in turn, dlambda[s] -= dt/3 * <g, v> and dD[s] -= dt/dx^2 *
+// <g, L v>, then resets the counter.  The result is the same bits on every
+// run.
+__global__ void k_param_dots(const double* __restrict__ gx, const double* __restrict__ gy,
+                             const double* __restrict__ gz, const double* __restrict__ vx,
+                             const double* __restrict__ vy, const double* __restrict__ vz, int s,
+                             int nx, int ny, int nz, int64_t pitch, double* __restrict__ partial,
+                             unsigned* __restrict__ counter, double dt, double dx, double* dD,
+                             double* dl)
 {
-    __shared__ double sh0[kRedThreads];
-    __shared__ double sh1[kRedThreads];
-    int64_t n = (int64_t)nz * ny * nx;
-    int64_t stride_a = axis == 0 ? 1 : (axis == 1 ? pitch : pitch * ny);
-    int n_a = axis == 0 ? nx : (axis == 1 ? ny : nz);
-    const double* gs = g + (int64_t)s * nz * ny * pitch;
-    const double* vs = v + (int64_t)s * nz * ny * pitch;
-    double acc0 = 0.0, acc1 = 0.0;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        int x = (int)(e % nx);
-        int64_t t = e / nx;
-        int y = (int)(t % ny);
-        int z = (int)(t / ny);
-        int i = axis == 0 ? x : (axis == 1 ? y : z);
-        int64_t o = ((int64_t)z * ny + y) * pitch + x;
-        double vi = vs[o];
-        double lv = 0.0;
-        if (n_a > 1) {
-            if (i > 0) lv += vi - vs[o - stride_a];
-            if (i < n_a - 1) lv += vi - vs[o + stride_a];
+    __shared__ double sh[6][kRedThreads];
+    __shared__ bool last;
+    const int64_t n = (int64_t)nz * ny * nx;
+    const int64_t so = (int64_t)s * nz * ny * pitch;
+    const int64_t stride[3] = {1, pitch, pitch * ny};
+    const double* G[3] = {gx + so, gy + so, gz + so};
+    const double* Vv[3] = {vx + so, vy + so, vz + so};
+    double acc[6] = {0, 0, 0, 0, 0, 0};
+    // 32-bit index arithmetic: nz ny nx < 2^32 voxels per substrate
+    for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < (uint32_t)n;
+         e += gridDim.x * blockDim.x) {
+        const uint32_t r = e / (uint32_t)nx;   // row (z, y)
+        const int x = (int)(e - r * (uint32_t)nx);
+        const uint32_t zq = r / (uint32_t)ny;
+        const int y = (int)(r - zq * (uint32_t)ny);
+        const int z = (int)zq;
+        const int64_t o = (int64_t)r * pitch + x;
+        const int idx[3] = {x, y, z};
+        const int ext[3] = {nx, ny, nz};
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const double vi = Vv[a][o];
+            double lv = 0.0;
+            if (ext[a] > 1) {
+                if (idx[a] > 0) lv += vi - Vv[a][o - stride[a]];
+                if (idx[a] < ext[a] - 1) lv += vi - Vv[a][o + stride[a]];
+            }
+            const double gi = G[a][o];
+            acc[2 * a] += gi * vi;
+            acc[2 * a + 1] += gi * lv;
         }
-        double gi = gs[o];
-        acc0 += gi * vi;
-        acc1 += gi * lv;
     }
-    sh0[threadIdx.x] = acc0;
-    sh1[threadIdx.x] = acc1;
+#pragma unroll
+    for (int q = 0; q < 6; ++q) sh[q][threadIdx.x] = acc[q];
     __syncthreads();
     for (int w = kRedThreads / 2; w > 0; w /= 2) {
-        if (threadIdx.x < w) {
-            sh0[threadIdx.x] += sh0[threadIdx.x + w];
-            sh1[threadIdx.x] += sh1[threadIdx.x + w];
-        }
+        if (threadIdx.x < w)
+#pragma unroll
+            for (int q = 0; q < 6; ++q) sh[q][threadIdx.x] += sh[q][threadIdx.x + w];
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        partial[2 * blockIdx.x] = sh0[0];
-        partial[2 * blockIdx.x + 1] = sh1[0];
+#pragma unroll
+        for (int q = 0; q < 6; ++q) partial[6 * blockIdx.x + q] = sh[q][0];
+        __threadfence();
+        last = atomicAdd(counter, 1u) == gridDim.x - 1;
     }
-}
-
-// dlambda[s] -= dt/3 * sum0, dD[s] -= dt/dx^2 * sum1 (one block, fixed order)
-__global__ void k_param_finish(const double* __restrict__ partial, int nblk, int s,
-                               double dt, double dx, double* dD, double* dl)
-{
-    __shared__ double sh0[kRedThreads];
-    __shared__ double sh1[kRedThreads];
-    double a0 = 0.0, a1 = 0.0;
-    for (int b = threadIdx.x; b < nblk; b += blockDim.x) {
-        a0 += partial[2 * b];
-        a1 += partial[2 * b + 1];
-    }
-    sh0[threadIdx.x] = a0;
-    sh1[threadIdx.x] = a1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    double b6[6] = {0, 0, 0, 0, 0, 0};
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
+#pragma unroll
+        for (int q = 0; q < 6; ++q) b6[q] += __ldcg(partial + 6 * b + q);
+#pragma unroll
+    for (int q = 0; q < 6; ++q) sh[q][threadIdx.x] = b6[q];
     __syncthreads();
     for (int w = kRedThreads / 2; w > 0; w /= 2) {
-        if (threadIdx.x < w) {
-            sh0[threadIdx.x] += sh0[threadIdx.x + w];
-            sh1[threadIdx.x] += sh1[threadIdx.x + w];
-        }
+        if (threadIdx.x < w)
+#pragma unroll
+            for (int q = 0; q < 6; ++q) sh[q][threadIdx.x] += sh[q][threadIdx.x + w];
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        dl[s] -= (dt / 3.0) * sh0[0];
-        dD[s] -= (dt / (dx * dx)) * sh1[0];
+        for (int a = 2; a >= 0; --a) {
+            dl[s] -= (dt / 3.0) * sh[2 * a][0];
+            dD[s] -= (dt / (dx * dx)) * sh[2 * a + 1][0];
+        }
+        *counter = 0u;
     }
 }
 
@@ -209,6 +228,8 @@ bfvm_status run_backward(Ctx* c, const double* g_final, double* dD, double* dl,
     const SourceTable& S = c->src;
     const int n_sub = c->n_sub;
     cudaStream_t st = c->stream;
+    if (n_dense >= ((int64_t)1 << 32))
+        return set_err(c, BFVM_EINVAL, "the adjoint covers grids of fewer than 2^32 voxel-substrates");
     const unsigned gd = (unsigned)ceil_div(n_dense, 256);
 
     // device buffers
@@ -229,7 +250,16 @@ bfvm_status run_backward(Ctx* c, const double* g_final, double* dD, double* dl,
     if ((rc = alloc(nf, &cur)) != BFVM_OK) { release(); return rc; }
     if ((rc = alloc(nf * 4 * (int64_t)k, &seg)) != BFVM_OK) { release(); return rc; }
     if ((rc = alloc(S.n_cells * n_sub, &pre)) != BFVM_OK) { release(); return rc; }
-    if ((rc = alloc(2 * kRedBlocks, &partial)) != BFVM_OK) { release(); return rc; }
+    if ((rc = alloc(6 * kRedBlocks + 1, &partial)) != BFVM_OK) { release(); return rc; }
+    // the dots' completion counter lives after the partials
+    unsigned* counter = reinterpret_cast<unsigned*>(partial + 6 * kRedBlocks);
+    // the adjoint after the z and the y solve of a step (the x solve writes g)
+    double *gz = nullptr, *gy = nullptr;
+    if ((rc = alloc(nf, &gz)) != BFVM_OK) { release(); return rc; }
+    if ((rc = alloc(nf, &gy)) != BFVM_OK) { release(); return rc; }
+    cudaMemsetAsync(counter, 0, sizeof(unsigned), st);
+    bool any_dir = false;
+    for (int s = 0; s < n_sub; ++s) any_dir = any_dir || c->bc_kind[s] == BFVM_BC_DIRICHLET;
     cudaMemsetAsync(g, 0, sizeof(double) * nf, st);
     cudaMemsetAsync(cur, 0, sizeof(double) * nf, st);
     cudaMemsetAsync(dD, 0, sizeof(double) * n_sub, st);
@@ -242,54 +272,109 @@ bfvm_status run_backward(Ctx* c, const double* g_final, double* dD, double* dl,
     c->launches += 1;
 
     auto V = [&](int t, int which) { return seg + ((int64_t)t * 4 + which) * nf; };
+    // One segment of len steps from its checkpoint (already in `cur`): the
+    // replay that keeps each step's raw solve outputs and pre-source field,
+    // then the adjoint steps in reverse.  Every launch reads and writes the
+    // same buffers for every segment, so a segment is captured once as a
+    // CUDA graph (per length) and replayed for all of them.
+    auto segment = [&](int len) -> bfvm_status {
+        bfvm_status r = BFVM_OK;
+        for (int j = 0; j < len; ++j) {
+            if ((r = launch_sweep_plain64(c, 0, cur, V(j, 0), 1)) != BFVM_OK) return r;
+            if ((r = launch_sweep_plain64(c, 1, V(j, 0), V(j, 1), 1)) != BFVM_OK) return r;
+            if ((r = launch_sweep_plain64(c, 2, V(j, 1), V(j, 2), 1)) != BFVM_OK) return r;
+            // the field before the sources: P(v3) (kept for the sources'
+            // adjoint when a Dirichlet shell makes it differ from v3), and the
+            // next step's input
+            k_shell<<<gd, 256, 0, c->stream>>>(V(j, 2), any_dir ? V(j, 3) : cur,
+                                               any_dir ? cur : nullptr, c->nx, c->ny, c->nz,
+                                               n_sub, c->pitch, c->d_bc_kind, c->d_bc_value, true);
+            c->launches += 1;
+            if (S.n_entries > 0) {
+                k_apply_maps<<<(unsigned)ceil_div(S.n_entries, 256), 256, 0, c->stream>>>(
+                    cur, S.n_entries, S.off, S.alpha, S.beta);
+                c->launches += 1;
+            }
+        }
+        for (int j = len - 1; j >= 0; --j) {
+            if (S.n_entries > 0) {
+                k_sources_adjoint<<<(unsigned)ceil_div(S.n_seg * n_sub, 128), 128, 0, c->stream>>>(
+                    g, any_dir ? V(j, 3) : V(j, 2), S.n_seg, n_sub, S.seg_start, S.off,
+                    S.cell_sorted, S.ca, S.cb, S.cw, S.crs, pre, dS, dU);
+                c->launches += 1;
+            }
+            if ((r = launch_sweep_plain64(c, 2, g, gz, 2)) != BFVM_OK) return r;
+            if ((r = launch_sweep_plain64(c, 1, gz, gy, 2)) != BFVM_OK) return r;
+            if ((r = launch_sweep_plain64(c, 0, gy, g, 2)) != BFVM_OK) return r;
+            for (int s = 0; s < n_sub; ++s) {
+                k_param_dots<<<kRedBlocks, kRedThreads, 0, c->stream>>>(
+                    g, gy, gz, V(j, 0), V(j, 1), V(j, 2), s, c->nx, c->ny, c->nz, c->pitch,
+                    partial, counter, c->dt, c->dx, dD, dl);
+                c->launches += 1;
+            }
+            if (any_dir) {   // P' g: the shell's adjoint is zero
+                k_shell<<<gd, 256, 0, c->stream>>>(g, g, nullptr, c->nx, c->ny, c->nz, n_sub,
+                                                   c->pitch, c->d_bc_kind, c->d_bc_value, false);
+                c->launches += 1;
+            }
+        }
+        return r;
+    };
+    // graphs of the segment lengths in use (the first segment processed,
+    // the last of the run, may be shorter); launched one by one when the
+    // kernels are being timed
+    const bool graphs = c->use_graphs && !c->time_kernels;
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    int glen[2] = {0, 0};
+    int64_t gkern[2] = {0, 0};   // kernels in each graph
+    auto run_segment = [&](int len) -> bfvm_status {
+        if (!graphs) return segment(len);
+        int slot = (glen[0] == len || glen[0] == 0) ? 0 : 1;
+        if (!gexec[slot]) {
+            cudaStream_t cs = nullptr;
+            cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+            if (e != cudaSuccess) return cuda_err(c, e, "cudaStreamCreate");
+            cudaStream_t saved = c->stream;
+            const int64_t saved_launches = c->launches;
+            c->stream = cs;
+            bfvm_status r = BFVM_OK;
+            e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+            if (e != cudaSuccess) r = cuda_err(c, e, "cudaStreamBeginCapture");
+            if (r == BFVM_OK) {
+                r = segment(len);
+                cudaGraph_t gr = nullptr;
+                cudaError_t e2 = cudaStreamEndCapture(cs, &gr);
+                if (r == BFVM_OK && e2 != cudaSuccess) r = cuda_err(c, e2, "cudaStreamEndCapture");
+                if (r == BFVM_OK) {
+                    e2 = cudaGraphInstantiate(&gexec[slot], gr, 0);
+                    if (e2 != cudaSuccess) r = cuda_err(c, e2, "cudaGraphInstantiate");
+                }
+                if (gr) cudaGraphDestroy(gr);
+            }
+            c->stream = saved;
+            cudaStreamDestroy(cs);
+            gkern[slot] = c->launches - saved_launches;
+            c->launches = saved_launches;
+            if (r != BFVM_OK) return r;
+            glen[slot] = len;
+        }
+        cudaError_t e = cudaGraphLaunch(gexec[slot], st);
+        if (e != cudaSuccess) return cuda_err(c, e, "cudaGraphLaunch");
+        c->launches += gkern[slot];
+        return BFVM_OK;
+    };
     for (int q = n_ckpt - 1; q >= 0; --q) {
         int t0 = q * k;
         int t1 = t0 + k < n_steps ? t0 + k : n_steps;
         k_dense_to_pitched<<<gd, 256, 0, st>>>(static_cast<const double*>(c->checkpoints[q]),
                                                cur, c->nx, rows, c->pitch);
         c->launches += 1;
-        for (int t = t0; t < t1; ++t) {
-            int j = t - t0;
-            if ((rc = launch_sweep_plain64(c, 0, cur, V(j, 0), 1)) != BFVM_OK) break;
-            if ((rc = launch_sweep_plain64(c, 1, V(j, 0), V(j, 1), 1)) != BFVM_OK) break;
-            if ((rc = launch_sweep_plain64(c, 2, V(j, 1), V(j, 2), 1)) != BFVM_OK) break;
-            k_shell<<<gd, 256, 0, st>>>(V(j, 2), V(j, 3), c->nx, c->ny, c->nz, n_sub, c->pitch,
-                                        c->d_bc_kind, c->d_bc_value, true);
-            k_shell<<<gd, 256, 0, st>>>(V(j, 2), cur, c->nx, c->ny, c->nz, n_sub, c->pitch,
-                                        c->d_bc_kind, c->d_bc_value, true);
-            c->launches += 2;
-            if (S.n_entries > 0) {
-                k_apply_maps<<<(unsigned)ceil_div(S.n_entries, 256), 256, 0, st>>>(
-                    cur, S.n_entries, S.off, S.alpha, S.beta);
-                c->launches += 1;
-            }
-        }
-        if (rc != BFVM_OK) { release(); return rc; }
-        for (int t = t1 - 1; t >= t0; --t) {
-            int j = t - t0;
-            if (S.n_entries > 0) {
-                k_sources_adjoint<<<(unsigned)ceil_div(S.n_seg * n_sub, 128), 128, 0, st>>>(
-                    g, V(j, 3), S.n_seg, n_sub, S.seg_start, S.off, S.cell_sorted, S.ca, S.cb,
-                    S.cw, S.crs, pre, dS, dU);
-                c->launches += 1;
-            }
-            for (int a = 2; a >= 0; --a) {
-                if ((rc = launch_sweep_plain64(c, a, g, g, 2)) != BFVM_OK) break;
-                for (int s = 0; s < n_sub; ++s) {
-                    k_param_dots<<<kRedBlocks, kRedThreads, 0, st>>>(
-                        g, V(j, a), a, s, c->nx, c->ny, c->nz, c->pitch, partial);
-                    k_param_finish<<<1, kRedThreads, 0, st>>>(partial, kRedBlocks, s, c->dt,
-                                                              c->dx, dD, dl);
-                    c->launches += 2;
-                }
-            }
-            if (rc != BFVM_OK) break;
-            k_shell<<<gd, 256, 0, st>>>(g, g, c->nx, c->ny, c->nz, n_sub, c->pitch,
-                                        c->d_bc_kind, c->d_bc_value, false);
-            c->launches += 1;
-        }
-        if (rc != BFVM_OK) { release(); return rc; }
+        if ((rc = run_segment(t1 - t0)) != BFVM_OK) break;
     }
+    cudaStreamSynchronize(st);   // before the graphs go
+    for (cudaGraphExec_t ge : gexec)
+        if (ge) cudaGraphExecDestroy(ge);
+    if (rc != BFVM_OK) { release(); return rc; }
     if (g0) {
         k_pitched_to_dense<<<gd, 256, 0, st>>>(g, g0, c->nx, rows, c->pitch);
         c->launches += 1;

@@ -444,15 +444,20 @@ bfvm_status launch_axis(Ctx* c, const SweepArgs<T>& A)
                    ((((size_t)A.n_sub + 1) * 8 + 15) & ~(size_t)15);
     int max_warps = sizeof(T) == 8 ? 4 : 8;
     int warps = 0;
-    if (DIR == 0 && A.n_sub <= 64 && c->smem_optin > fixed)
+    // the shared-memory sweeps run the step's Dirichlet handling; the
+    // adjoint's solves (DIR 1, 2) differ from it only on Dirichlet
+    // substrates, so without those they take the same kernels
+    bool any_dir = false;
+    for (int s = 0; s < c->n_sub; ++s) any_dir = any_dir || c->bc_kind[s] == BFVM_BC_DIRICHLET;
+    if ((DIR == 0 || !any_dir) && A.n_sub <= 64 && c->smem_optin > fixed)
         warps = (int)((c->smem_optin - fixed) / per_warp);
     if (warps > max_warps) warps = max_warps;
     KernelTimer timer(c, AXIS);
     // plain-form sweeps: the split solve where one thread or one 32-line
     // block per line cannot fill the GPU (the 2-D variant) or the step's
     // lines are too long for the shared-memory kernels; the adjoint's solves
-    // (DIR 1, 2) only when forced: on the 100^3 adjoint workload the
-    // one-thread-per-line sweep was faster (backward 60.7 ms against 69.5)
+    // (DIR 1, 2) only when forced (on the 100^3 adjoint workload it gained
+    // nothing over one thread per line)
     if (MODE == 0 &&
         (c->split == 2 || (c->split == 1 && DIR == 0 && (c->dims == 2 || warps < 1))))
         return launch_split<T, AXIS, DIR>(c, A);
