@@ -55,6 +55,11 @@ def parse():
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the FP32 / batched / adjoint form measurements")
     ap.add_argument("--form-steps", type=int, default=10)
+    ap.add_argument("--form", default=None,
+                    choices=["fp32", "batched", "batched_fp32", "adjoint", "two_d", "nodes",
+                             "slabs"],
+                    help="time one form of the step on its own (for profiling runs): "
+                         "--warmup untimed and --steps timed steps, one JSON line")
     return ap.parse_args()
 
 
@@ -690,10 +695,103 @@ def run_ours(args):
     return 0
 
 
+def run_form(args):
+    """One form of the step on its own: W untimed and K timed steps (CUDA
+    events, 512 MB L2 flush before each), its rate in voxel-substrate
+    updates per second.  For profiling runs; the default run measures every
+    form beside the headline."""
+    import numpy as np
+    import torch
+    from paper_2110_13368_gb300 import bfvm, inputs, slabs
+    from paper_2110_13368_gb300 import build as pbuild
+    pbuild.build()
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    form = args.form
+    closers = []
+    if form == "fp32":
+        p = inputs.tumour_200(steps=1000, precision=32)
+        sim = bfvm.Sim.from_problem(p)
+        closers.append(sim)
+        n_upd, step = p.updates_per_step, (lambda: sim.step(1))
+        launches = lambda: sim.info()["launches"]
+    elif form in ("batched", "batched_fp32"):
+        probs = inputs.batch_256(seed=0, precision=64 if form == "batched" else 32)
+        sims = [bfvm.Sim.from_problem(q) for q in probs]
+        batch = bfvm.Batch(sims)
+        closers += [batch] + sims
+        n_upd, step = sum(q.updates_per_step for q in probs), (lambda: batch.step(1))
+        launches = lambda: batch.info()["launches"]
+    elif form == "adjoint":
+        # one timed unit = a recorded forward of the workload and its backward
+        p, q = inputs.adjoint_problem()
+        sim = bfvm.Sim.from_problem(p)
+        closers.append(sim)
+        rho0 = torch.as_tensor(p.rho0, device=dev)
+        target = torch.ones_like(rho0)
+
+        def step():
+            sim.set_density(rho0)
+            sim.record(20)
+            sim.step(p.steps)
+            sim.backward(2.0 * (sim.get_density() - target))
+        n_upd = p.updates_per_step * p.steps
+        launches = lambda: sim.info()["launches"]
+    elif form == "two_d":
+        p = inputs.make_problem(1000, 1000, 1, n_sub=2, D=[1e5, 1e3], lam=[0.1, 0.01],
+                                bc_kind=[1, 0], bc_value=[38.0, 0.0], field_mode="zero",
+                                n_cells=20_000, U=[10.0, 0.0], S=[0.0, 10.0],
+                                rho_star=[1.0, 1.0], steps=10, seed=0, dims=2)
+        sim = bfvm.Sim.from_problem(p)
+        closers.append(sim)
+        n_upd, step = p.updates_per_step, (lambda: sim.step(1))
+        launches = lambda: sim.info()["launches"]
+    elif form == "nodes":
+        pt = inputs.tumour_200(steps=10)
+        rng = np.random.default_rng(5)
+        vox, sub, val = [], [], []
+        for _ in range(40):
+            x, y = rng.integers(10, 190, size=2)
+            v, sb, vl = inputs.vessel_nodes(pt.nx, pt.ny, pt.nz, substrate=0, value=38.0,
+                                            x=int(x), y=int(y))
+            vox.append(v); sub.append(sb); val.append(vl)
+        p = pt.with_(nodes=(np.concatenate(vox), np.concatenate(sub), np.concatenate(val)))
+        sim = bfvm.Sim.from_problem(p)
+        closers.append(sim)
+        n_upd, step = p.updates_per_step, (lambda: sim.step(1))
+        launches = lambda: sim.info()["launches"]
+    else:   # slabs: the 200^3 x 2 tumour grid as two z-slabs on this one GPU
+        p = inputs.tumour_200(steps=10)
+        z = slabs.partition(p.nz, 2)
+        parts = [slabs.Slab.from_problem(p, z, j) for j in range(2)]
+        closers += parts
+        n_upd, step = p.updates_per_step, (lambda: slabs.step_together(parts, 1))
+        launches = lambda: sum(bfvm.bfvm_get_info(s.handle)["launches"] for s in parts)
+    for _ in range(max(args.warmup, 1)):
+        flush.fill_(1.0)
+        step()
+    torch.cuda.synchronize()
+    l0 = launches()
+    ms = timed_steps(step, args.steps, stream, flush)
+    l1 = launches()
+    for o in closers:
+        o.close()
+    print(json.dumps({"form": form, "metric": "voxel-substrate updates/s",
+                      "value": n_upd * args.steps / (ms / 1e3),
+                      "ms_per_step": ms / args.steps, "steps": args.steps,
+                      "launches_per_step": (l1 - l0) / args.steps,
+                      "l2": "512 MB buffer written before every timed step"}), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.form is not None:
+        return run_form(args)
     return run_ours(args)
 
 
