@@ -26,6 +26,18 @@
 namespace bfvm {
 namespace persistent {
 
+// 16-byte vector of the element type
+template <typename T>
+struct Vec16;
+template <>
+struct Vec16<double> {
+    using type = double2;
+};
+template <>
+struct Vec16<float> {
+    using type = float4;
+};
+
 template <typename T, int AXIS, int MODE, int LAG = Groups<T>::PAIR_LAG>
 struct PairSweeper {
     static constexpr int G = Groups<T>::G;
@@ -48,14 +60,76 @@ struct PairSweeper {
     __device__ __forceinline__ int slot(int k) const { return Q ? (ns - 1 - k) : k; }
     template <int Q>
     __device__ __forceinline__ static constexpr int res(int kmod) { return Q ? (G - 1 - kmod) : kmod; }
-    __device__ __forceinline__ T* at(int s, int l, int m) const
+    __device__ __forceinline__ T* at(int s, int l) const { return W + s * 32 + l; }
+
+    // x lines (AXIS 0) are contiguous in memory, so each lane copies,
+    // eliminates and writes its own line.  The G elements of group g of a
+    // lane lie together in the 32 G slots that elements [gG, gG+G) occupy in
+    // the y/z layout (so the slot schedule is the same for every axis), as
+    // 16-byte chunks whose order within the lane is swizzled so that the
+    // 16-byte accesses of a quarter-warp fall on distinct banks.  Copies are
+    // 16-byte cp.async, shared reads and writes 16-byte vectors, and B
+    // writes its outputs with 32-byte (FP64) or 16-byte (FP32) stores.  Rows
+    // start on 32-byte boundaries (the pitch is a multiple of 4 elements),
+    // and a chunk that starts inside a line ends inside its row.
+    static constexpr int CW = 16 / (int)sizeof(T);   // elements per chunk
+    static constexpr int NCH = G / CW;               // chunks per lane and group
+    using V16 = typename Vec16<T>::type;
+    __device__ __forceinline__ int xswz() const { return (lane / (8 / NCH)) % NCH; }
+    template <int Q>
+    __device__ __forceinline__ T* xgrp(int g) const
     {
-        return W + s * 32 + (AXIS == 0 ? (l ^ (m * ROWS)) : l);
+        return W + (Q ? (ns / G - 1 - g) : g) * (G * 32) + lane * G;
+    }
+    template <int Q>
+    __device__ __forceinline__ T* xel(int k) const
+    {
+        const int u = k % G;
+        return xgrp<Q>(k / G) + CW * ((u / CW) ^ xswz()) + u % CW;
     }
     template <int Q>
     __device__ __forceinline__ T* own(int k, int u) const
     {
-        return at(slot<Q>(k), lane, res<Q>(u));
+        if (AXIS == 0) return xel<Q>(k);
+        return at(slot<Q>(k), lane);
+    }
+    // chunks c of group g (x lines): 16-byte reads and writes
+    __device__ __forceinline__ void x_read(const T* grp, T (&v)[G]) const
+    {
+#pragma unroll
+        for (int c = 0; c < NCH; ++c) {
+            const V16 q = *reinterpret_cast<const V16*>(grp + CW * (c ^ xswz()));
+            const T* e = reinterpret_cast<const T*>(&q);
+#pragma unroll
+            for (int i = 0; i < CW; ++i) v[c * CW + i] = e[i];
+        }
+    }
+    __device__ __forceinline__ void x_write_chunk(T* grp, int c, const T* v) const
+    {
+        V16 q;
+        T* e = reinterpret_cast<T*>(&q);
+#pragma unroll
+        for (int i = 0; i < CW; ++i) e[i] = v[i];
+        *reinterpret_cast<V16*>(grp + CW * (c ^ xswz())) = q;
+    }
+    // B's outputs of a whole group of an x line: two 32-byte (FP64) or two
+    // 16-byte (FP32) stores
+    __device__ __forceinline__ void x_store_group(T* dst, const T (&o)[G]) const
+    {
+        if (sizeof(T) == 8) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+                asm volatile("st.global.v4.f64 [%0], {%1, %2, %3, %4};" ::"l"(dst + 4 * h),
+                             "d"((double)o[4 * h]), "d"((double)o[4 * h + 1]),
+                             "d"((double)o[4 * h + 2]), "d"((double)o[4 * h + 3])
+                             : "memory");
+        } else {
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+                *reinterpret_cast<float4*>(dst + 4 * h) =
+                    make_float4((float)o[4 * h], (float)o[4 * h + 1], (float)o[4 * h + 2],
+                                (float)o[4 * h + 3]);
+        }
     }
 
     // F: copy elements [gG, gG+G) of a block into the slots of parity Q
@@ -64,16 +138,12 @@ struct PairSweeper {
     {
         if (g * G >= n) return;
         if (AXIS == 0) {
-            const int e = g * G + (lane % G);
-            if (e < n) {
-                const int s = slot<Q>(e);
-                const int m = res<Q>(lane % G);
+            if (!ln.valid) return;
+            const T* src = fin + ln.base + g * G;
+            T* d = xgrp<Q>(g);
 #pragma unroll
-                for (int t = 0; t < G; ++t) {
-                    const int r = t * ROWS + lane / G;
-                    cp_async_elem(at(s, r, m), fin + rb[r] + e);
-                }
-            }
+            for (int c = 0; c < NCH; ++c)
+                if (g * G + c * CW < n) cp_async_16(d + CW * (c ^ xswz()), src + c * CW);
         } else {
             const T* src = fin + ln.base + (int64_t)g * G * stride;
 #pragma unroll
@@ -88,16 +158,46 @@ struct PairSweeper {
     // compensated multiply-add (comp_axpy).  Rescaled form: one FMA each.
     __device__ __forceinline__ T fwd_op(const CoefRow<T>& C, T prev, T d, int k) const
     {
-        if (MODE != 0) return fma(C.a[k], prev, d);
-        if (sizeof(T) == 8) return fma(C.c, prev, d) * C.a[k];
+        return fwd_val(C, prev, d, C.a[k], (MODE == 0 && sizeof(T) == 4) ? C.a_lo[k] : (T)0);
+    }
+    // the same step with the element's coefficients already in registers
+    __device__ __forceinline__ T fwd_val(const CoefRow<T>& C, T prev, T d, T a, T a_lo) const
+    {
+        if (MODE != 0) return fma(a, prev, d);
+        if (sizeof(T) == 8) return fma(C.c, prev, d) * a;
         const float t = comp_axpy((float)C.c, (float)C.c_lo, (float)prev, (float)d);
-        return (T)__fmaf_rn(t, (float)C.a[k], __fmul_rn(t, (float)C.a_lo[k]));
+        return (T)__fmaf_rn(t, (float)a, __fmul_rn(t, (float)a_lo));
     }
     __device__ __forceinline__ T bwd_op(const CoefRow<T>& C, T x, T w, int k) const
     {
+        return bwd_val(x, w, C.b[k], (MODE == 0 && sizeof(T) == 4) ? C.b_lo[k] : (T)0);
+    }
+    __device__ __forceinline__ T bwd_val(T x, T w, T b, T b_lo) const
+    {
         if (MODE == 0 && sizeof(T) == 4)
-            return (T)comp_axpy((float)C.b[k], (float)C.b_lo[k], (float)x, (float)w);
-        return fma(C.b[k], x, w);
+            return (T)comp_axpy((float)b, (float)b_lo, (float)x, (float)w);
+        return fma(b, x, w);
+    }
+
+    // B's inputs of one interior group, read ahead into registers: the
+    // group's intermediates (written by F in the previous phase) and its
+    // backward coefficients
+    struct BIn {
+        T w[G], b[G], bl[G];
+    };
+    template <int Q>
+    __device__ __forceinline__ void bwd_load(const CoefRow<T>& C, int h, BIn& in) const
+    {
+        constexpr bool LO = MODE == 0 && sizeof(T) == 4;
+        const int k0 = h * G;
+        if (AXIS == 0) x_read(xgrp<Q>(h), in.w);
+        const T* p = W + slot<Q>(k0) * 32;
+#pragma unroll
+        for (int u = 0; u < G; ++u) {
+            if (AXIS != 0) in.w[u] = p[off<Q>(u)];
+            in.b[u] = C.b[k0 + u];
+            in.bl[u] = LO ? C.b_lo[k0 + u] : (T)0;
+        }
     }
 
     // F: forward elimination of group g (parity Q); prev carries the chain
@@ -105,10 +205,15 @@ struct PairSweeper {
     __device__ __forceinline__ void fwd_group(const Line& L, const CoefRow<T>& C, T& prev,
                                               int g) const
     {
-        T d[G];
+        // FP64: coefficients read with the elements, ahead of the chain
+        constexpr bool HOIST = sizeof(T) == 8;
+        T d[G], ca[G];
 #pragma unroll
         for (int u = 0; u < G; ++u)
-            if (g * G + u < n) d[u] = *own<Q>(g * G + u, u);
+            if (g * G + u < n) {
+                d[u] = *own<Q>(g * G + u, u);
+                if (HOIST) ca[u] = C.a[g * G + u];
+            }
 #pragma unroll
         for (int u = 0; u < G; ++u) {
             const int k = g * G + u;
@@ -116,8 +221,9 @@ struct PairSweeper {
                 T dk = d[u];
                 if (L.dir && k == 0) dk = (T)L.end0;
                 if (L.dir && k == n - 1) dk = (T)L.end1;
-                if (MODE == 0) prev = fwd_op(C, prev, dk, k);
-                else prev = (k == 0) ? dk : fwd_op(C, prev, dk, k);
+                const T nk = HOIST ? fwd_val(C, prev, dk, ca[u], (T)0) : fwd_op(C, prev, dk, k);
+                if (MODE == 0) prev = nk;
+                else prev = (k == 0) ? dk : nk;
                 if (k < n - 1) *own<Q>(k, u) = prev;
             }
         }
@@ -127,7 +233,7 @@ struct PairSweeper {
     template <int Q>
     __device__ __forceinline__ int off(int u) const
     {
-        return (Q ? -u : u) * 32 + (AXIS == 0 ? (lane ^ (res<Q>(u) * ROWS)) : lane);
+        return (Q ? -u : u) * 32 + lane;
     }
 
     // Interior groups: all G elements exist, none is the line's last and
@@ -137,12 +243,11 @@ struct PairSweeper {
     __device__ __forceinline__ void copy_fast(const Line& ln, const int64_t (&rv)[G], int g) const
     {
         if (AXIS == 0) {
-            const int e = g * G + (lane % G);
-            const int s = slot<Q>(e);
-            const int m = res<Q>(lane % G);
+            if (!ln.valid) return;
+            const T* src = fin + ln.base + g * G;
+            T* d = xgrp<Q>(g);
 #pragma unroll
-            for (int t = 0; t < G; ++t)
-                cp_async_elem(at(s, t * ROWS + lane / G, m), fin + rv[t] + e);
+            for (int c = 0; c < NCH; ++c) cp_async_16(d + CW * (c ^ xswz()), src + c * CW);
         } else {
             T* p = W + slot<Q>(g * G) * 32;
             const T* src = fin + ln.base + (int64_t)g * G * stride;
@@ -151,45 +256,48 @@ struct PairSweeper {
         }
     }
 
+    // The group's coefficients are read into registers with its elements,
+    // before the chain: read inside it, each read would wait for the store
+    // of the previous element (the two may alias, as far as the compiler
+    // knows), and the shared-memory latency would sit on the chain.
     template <int Q>
     __device__ __forceinline__ void fwd_fast(const CoefRow<T>& C, T& prev, int g) const
     {
-        T* p = W + slot<Q>(g * G) * 32;
-        T d[G];
-#pragma unroll
-        for (int u = 0; u < G; ++u) d[u] = p[off<Q>(u)];
+        constexpr bool LO = MODE == 0 && sizeof(T) == 4;
+        T* p = AXIS == 0 ? xgrp<Q>(g) : W + slot<Q>(g * G) * 32;
+        T d[G], ca[G], cl[G];
+        if (AXIS == 0) x_read(p, d);
 #pragma unroll
         for (int u = 0; u < G; ++u) {
-            prev = fwd_op(C, prev, d[u], g * G + u);
-            p[off<Q>(u)] = prev;
+            if (AXIS != 0) d[u] = p[off<Q>(u)];
+            ca[u] = C.a[g * G + u];
+            cl[u] = LO ? C.a_lo[g * G + u] : (T)0;
+        }
+#pragma unroll
+        for (int u = 0; u < G; ++u) {
+            prev = fwd_val(C, prev, d[u], ca[u], cl[u]);
+            if (AXIS == 0) {
+                d[u] = prev;
+                if (u % CW == CW - 1) x_write_chunk(p, u / CW, d + (u - (CW - 1)));
+            } else {
+                p[off<Q>(u)] = prev;
+            }
         }
     }
 
     template <int Q>
     __device__ __forceinline__ void bwd_fast(const Line& L, const CoefRow<T>& C, T& x, int h,
-                                             const int64_t (&rv)[G]) const
+                                             const int64_t (&rv)[G], const BIn& in) const
     {
         const int k0 = h * G;
-        T* p = W + slot<Q>(k0) * 32;
-        T w[G], o[G];
-#pragma unroll
-        for (int u = 0; u < G; ++u) w[u] = p[off<Q>(u)];
+        T o[G];
 #pragma unroll
         for (int u = G - 1; u >= 0; --u) {
-            x = bwd_op(C, x, w[u], k0 + u);
+            x = bwd_val(x, in.w[u], in.b[u], in.bl[u]);
             o[u] = (MODE == 2) ? (T)(((double)x * C.o[k0 + u]) * L.inv_other) : x;
         }
         if (AXIS == 0) {
-#pragma unroll
-            for (int u = 0; u < G; ++u) p[off<Q>(u)] = o[u];
-            __syncwarp();
-            const int k = k0 + (lane % G);
-            const int s = slot<Q>(k);
-            const int m = res<Q>(lane % G);
-#pragma unroll
-            for (int t = 0; t < G; ++t)
-                if (rv[t] >= 0) fout[rv[t] + k] = *at(s, t * ROWS + lane / G, m);
-            __syncwarp();
+            if (L.valid) x_store_group(fout + L.base + k0, o);
         } else if (L.valid) {
             T* dst = fout + L.base + (int64_t)k0 * stride;
 #pragma unroll
@@ -197,12 +305,12 @@ struct PairSweeper {
         }
     }
 
-    // Row bases of the transposed x-sweep accesses of this lane: rows
-    // t*ROWS + lane/G of the block (from the warp's row table)
+    // Row bases of transposed accesses: none in this layout (kept so that
+    // the callers' row tables stay the same for every axis)
     __device__ __forceinline__ void load_rows(const int64_t* rb, int64_t (&rv)[G]) const
     {
 #pragma unroll
-        for (int t = 0; t < G; ++t) rv[t] = (AXIS == 0) ? rb[t * ROWS + lane / G] : 0;
+        for (int t = 0; t < G; ++t) rv[t] = 0;   // no transposed accesses (any axis)
     }
 
     // F: forward elimination of a whole block on its own (the pair's first)
@@ -274,11 +382,23 @@ struct PairSweeper {
         if (!paired) iters = gcount;
         else if (iters < 0) iters = gcount + LG;
         bool released = false;
+        // FP64: the next interior group's inputs are read before the pair
+        // barrier, so that B's FMA chain resumes right after it (in FP32 the
+        // registers this takes cost more than the latency it hides)
+        constexpr bool READ_AHEAD = false;
+        BIn in;
+        bool have = false;
         for (int jg = 0; jg < iters; ++jg) {
             const int h = h_top - jg;
             if (h >= 0) {
-                if (h < b_hi) bwd_fast<Q>(L, C, x, h, rv);
-                else bwd_group<Q>(L, C, x, h, rb);
+                if (h < b_hi) {
+                    if (!have) bwd_load<Q>(C, h, in);
+                    bwd_fast<Q>(L, C, x, h, rv, in);
+                } else {
+                    bwd_group<Q>(L, C, x, h, rb);
+                }
+                have = READ_AHEAD && h >= 1 && h - 1 < b_hi;
+                if (have) bwd_load<Q>(C, h - 1, in);
             } else if (!released) {
                 rel();
                 released = true;
@@ -306,21 +426,12 @@ struct PairSweeper {
             }
         }
         if (AXIS == 0) {
+            if (L.valid) {
+                T* dst = fout + L.base + h * G;
 #pragma unroll
-            for (int u = 0; u < G; ++u)
-                if (h * G + u < n) *own<Q>(h * G + u, u) = o[u];
-            __syncwarp();
-            const int k = h * G + (lane % G);
-            if (k < n) {
-                const int s = slot<Q>(k);
-                const int m = res<Q>(lane % G);
-#pragma unroll
-                for (int t = 0; t < G; ++t) {
-                    const int r = t * ROWS + lane / G;
-                    if (rb[r] >= 0) fout[rb[r] + k] = *at(s, r, m);
-                }
+                for (int u = 0; u < G; ++u)
+                    if (h * G + u < n) dst[u] = o[u];
             }
-            __syncwarp();
         } else if (L.valid) {
             T* dst = fout + L.base + (int64_t)h * G * stride;
 #pragma unroll

@@ -37,6 +37,12 @@ __device__ __forceinline__ void cp_async_elem(float* dst, const float* src)
     unsigned s = (unsigned)__cvta_generic_to_shared(dst);
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(src) : "memory");
 }
+// 16 bytes, both addresses 16-byte aligned; not cached in L1
+__device__ __forceinline__ void cp_async_16(void* dst, const void* src)
+{
+    unsigned s = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(src) : "memory");
+}
 __device__ __forceinline__ void cp_async_commit()
 {
     asm volatile("cp.async.commit_group;\n" ::: "memory");
