@@ -269,7 +269,7 @@ __device__ __forceinline__ T f_task_b(const SweepArgs<T>& A, const Line& L, cons
                                       bool solo, int iters)
 {
     constexpr int G = Groups<T>::G;
-    PairSweeper<T, AXIS, MODE, BatchLag<T>::LG> sw{A, W, A.field, A.field, axis_stride(A, AXIS),
+    PairSweeper<T, AXIS, MODE, BatchLag<T>::LG, false> sw{A, W, A.field, A.field, axis_stride(A, AXIS),
                                                    A.n, ns, lane, bar_id};
     __syncwarp();
     rbF[lane] = L.base;
@@ -432,7 +432,7 @@ __device__ __forceinline__ void b_axis_b(BBState<T>& b, const int* tf, const Ste
         const SweepArgs<T>& A = P.slot[b.k % 3];
         auto rel = [&]() { task_done(Q, r, lane); };
         {
-            PairSweeper<T, AXIS, MODE, BatchLag<T>::LG> sw{A, P.W, A.field, A.field,
+            PairSweeper<T, AXIS, MODE, BatchLag<T>::LG, false> sw{A, P.W, A.field, A.field,
                                                            axis_stride(A, AXIS), A.n, P.ns,
                                                            lane, P.bar_id};
             Line L;

@@ -38,7 +38,9 @@ struct Vec16<float> {
     using type = float4;
 };
 
-template <typename T, int AXIS, int MODE, int LAG = Groups<T>::PAIR_LAG>
+// BBAR: B meets F at the pair barrier between reading a group and solving
+// it (true), or after solving it (false; see b_block)
+template <typename T, int AXIS, int MODE, int LAG = Groups<T>::PAIR_LAG, bool BBAR = true>
 struct PairSweeper {
     static constexpr int G = Groups<T>::G;
     static constexpr int ROWS = Groups<T>::ROWS;
@@ -370,6 +372,15 @@ struct PairSweeper {
     // `rel` runs once after the last group's stores have been issued: in the
     // first iteration that has no group left (F is still eliminating its
     // last groups then), else after the loop.
+    //
+    // With BBAR, B reads a group's inputs into registers before it meets F
+    // at the pair barrier and runs the group's chain after it: the group's
+    // slots are free once read (B's outputs go to global memory), and F
+    // arrives at the barrier at the end of its own chain, so B's chain fills
+    // the FP64 pipe while F issues its copies and reads its next group
+    // (200^3 FP64 step 301 -> 292 us).  The batched step, whose tasks pair
+    // lines of unequal length, measured faster with the chain before the
+    // barrier (5.1e10 against 4.8e10 updates/s), and takes BBAR = false.
     template <int Q, typename Rel = NoRelease>
     __device__ __forceinline__ void b_block(const Line& L, const CoefRow<T>& C, T& x,
                                             const int64_t* rb, const int64_t (&rv)[G],
@@ -382,46 +393,59 @@ struct PairSweeper {
         if (!paired) iters = gcount;
         else if (iters < 0) iters = gcount + LG;
         bool released = false;
-        // FP64: the next interior group's inputs are read before the pair
-        // barrier, so that B's FMA chain resumes right after it (in FP32 the
-        // registers this takes cost more than the latency it hides)
-        constexpr bool READ_AHEAD = false;
         BIn in;
-        bool have = false;
         for (int jg = 0; jg < iters; ++jg) {
             const int h = h_top - jg;
             if (h >= 0) {
-                if (h < b_hi) {
-                    if (!have) bwd_load<Q>(C, h, in);
-                    bwd_fast<Q>(L, C, x, h, rv, in);
-                } else {
-                    bwd_group<Q>(L, C, x, h, rb);
-                }
-                have = READ_AHEAD && h >= 1 && h - 1 < b_hi;
-                if (have) bwd_load<Q>(C, h - 1, in);
+                if (h < b_hi) bwd_load<Q>(C, h, in);
+                else bwd_load_edge<Q>(C, h, in);
+                if (!BBAR) bwd_solve<Q>(L, C, x, h, b_hi, rv, in);
             } else if (!released) {
                 rel();
                 released = true;
             }
             if (paired) pair_bar();                      // group h released to F
+            if (BBAR && h >= 0) bwd_solve<Q>(L, C, x, h, b_hi, rv, in);
         }
         if (!released) rel();
     }
 
-    // B: back substitution of group h (parity Q) and its output
+    template <int Q>
+    __device__ __forceinline__ void bwd_solve(const Line& L, const CoefRow<T>& C, T& x, int h,
+                                              int b_hi, const int64_t (&rv)[G],
+                                              const BIn& in) const
+    {
+        if (h < b_hi) bwd_fast<Q>(L, C, x, h, rv, in);
+        else bwd_group<Q>(L, C, x, h, in);
+    }
+
+    // B: inputs of the line's last group (elements below n - 1 only)
+    template <int Q>
+    __device__ __forceinline__ void bwd_load_edge(const CoefRow<T>& C, int h, BIn& in) const
+    {
+        constexpr bool LO = MODE == 0 && sizeof(T) == 4;
+#pragma unroll
+        for (int u = 0; u < G; ++u) {
+            const int k = h * G + u;
+            if (k < n - 1) {
+                in.w[u] = *own<Q>(k, u);
+                in.b[u] = C.b[k];
+                in.bl[u] = LO ? C.b_lo[k] : (T)0;
+            }
+        }
+    }
+
+    // B: back substitution of the line's last group (parity Q) and its output
     template <int Q>
     __device__ __forceinline__ void bwd_group(const Line& L, const CoefRow<T>& C, T& x, int h,
-                                              const int64_t* rb) const
+                                              const BIn& in) const
     {
-        T w[G], o[G];
-#pragma unroll
-        for (int u = 0; u < G; ++u)
-            if (h * G + u < n - 1) w[u] = *own<Q>(h * G + u, u);
+        T o[G];
 #pragma unroll
         for (int u = G - 1; u >= 0; --u) {
             const int k = h * G + u;
             if (k < n) {
-                if (k < n - 1) x = bwd_op(C, x, w[u], k);
+                if (k < n - 1) x = bwd_val(x, in.w[u], in.b[u], in.bl[u]);
                 o[u] = (MODE == 2) ? (T)(((double)x * C.o[k]) * L.inv_other) : x;
             }
         }
@@ -445,7 +469,7 @@ struct PairSweeper {
 // [MODE 2 output scales] [line-set prefix] [per pair: column buffer,
 // 2 x 32 row bases of each warp (4 x 32), 32 chain hand-over values].
 template <typename T, int AXIS, int MODE>
-__global__ void __launch_bounds__(64 * Groups<T>::MAX_PAIRS, 1) k_sweep_pair(SweepArgs<T> A, LineSet S,
+__global__ void __launch_bounds__(64 * Groups<T>::AXIS_PAIRS, 1) k_sweep_pair(SweepArgs<T> A, LineSet S,
                                                        int64_t n_blocks, int n_slots)
 {
     constexpr int G = Groups<T>::G;

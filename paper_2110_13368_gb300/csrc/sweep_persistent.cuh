@@ -41,6 +41,9 @@
 namespace bfvm {
 namespace persistent {
 
+#ifndef BFVM_LAG64
+#define BFVM_LAG64 3
+#endif
 // Group of G consecutive elements per loop iteration: 8 for both types (one
 // 32-byte sector of FP32, two of FP64), so that per-group costs (waits,
 // commits, pointer updates, boundary groups) are amortised over 8 elements.
@@ -52,13 +55,16 @@ struct Groups {
     // copy-ahead distance of a warp pair's F warp (sweep_pair.cuh); measured
     // on the 200^3 step: FP64 3 groups (2: 1.5 % slower, 1: 40 % slower),
     // FP32 4 (8: 4 % slower)
-    static constexpr int PAIR_LAG = sizeof(T) == 8 ? 3 : 4;
+    static constexpr int PAIR_LAG = sizeof(T) == 8 ? BFVM_LAG64 : 4;
     // most warp pairs per CTA of the pair kernels (per-axis and one-launch):
     // FP64 is bound by the FP64 pipe with two pairs' warps per SMSP; the FP32
     // sweeps are latency-bound and take more warps.  Measured on the 200^3
     // FP32 step: 4 pairs 0.224 ms, 5 pairs 0.210 ms, 6 pairs 0.166 ms,
     // 8 pairs 0.192 ms.
     static constexpr int MAX_PAIRS = sizeof(T) == 8 ? 4 : 6;
+    // most warp pairs per CTA of the per-axis pair kernel (k_sweep_pair);
+    // FP32 at 8 pairs measured 12 % slower than at 6 (200^3 step)
+    static constexpr int AXIS_PAIRS = MAX_PAIRS;
 };
 
 // Lines of one axis that need a solve, substrate by substrate: for a

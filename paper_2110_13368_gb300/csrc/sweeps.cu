@@ -481,7 +481,7 @@ bfvm_status launch_axis(Ctx* c, const SweepArgs<T>& A)
         const size_t per_pair = (size_t)32 * ns * sizeof(T) + 4 * 32 * sizeof(int64_t) +
                                 32 * sizeof(T);
         int pairs = (int)((c->smem_optin - fixed) / per_pair);
-        if (pairs > persistent::Groups<T>::MAX_PAIRS) pairs = persistent::Groups<T>::MAX_PAIRS;
+        if (pairs > persistent::Groups<T>::AXIS_PAIRS) pairs = persistent::Groups<T>::AXIS_PAIRS;
         if (c->sweep_kernel == 0 && pairs >= 1) {
             size_t smem = fixed + per_pair * pairs;
             auto kern = persistent::k_sweep_pair<T, AXIS, MODE>;
@@ -555,7 +555,7 @@ bfvm_status launch_step_fused(Ctx* c, int p, bool renorm, const T* r, const T* c
     // the per-axis launches stage one axis' coefficients only; where that
     // leaves room for more pairs, they are the faster choice
     const size_t fixed_axis = (size_t)c->n_sub * NC * ns * sizeof(T) + 1024;
-    const int pairs_axis = (int)std::min<size_t>(persistent::Groups<T>::MAX_PAIRS,
+    const int pairs_axis = (int)std::min<size_t>(persistent::Groups<T>::AXIS_PAIRS,
                                                  (c->smem_optin - fixed_axis) / M.pair);
     if (c->fused_step != 2) {
         if (pairs < pairs_axis) return BFVM_ESTATE;
