@@ -41,9 +41,6 @@
 namespace bfvm {
 namespace persistent {
 
-#ifndef BFVM_LAG64
-#define BFVM_LAG64 3
-#endif
 // Group of G consecutive elements per loop iteration: 8 for both types (one
 // 32-byte sector of FP32, two of FP64), so that per-group costs (waits,
 // commits, pointer updates, boundary groups) are amortised over 8 elements.
@@ -53,9 +50,9 @@ struct Groups {
     static constexpr int ROWS = 32 / G;             // rows per transposed instruction
     static constexpr int LAG_GROUPS = sizeof(T) == 8 ? 3 : 4;
     // copy-ahead distance of a warp pair's F warp (sweep_pair.cuh); measured
-    // on the 200^3 step: FP64 3 groups (2: 1.5 % slower, 1: 40 % slower),
+    // on the 200^3 step: FP64 3 groups (289.5 us; 2: 310 us, 4: 292.5 us),
     // FP32 4 (8: 4 % slower)
-    static constexpr int PAIR_LAG = sizeof(T) == 8 ? BFVM_LAG64 : 4;
+    static constexpr int PAIR_LAG = sizeof(T) == 8 ? 3 : 4;
     // most warp pairs per CTA of the pair kernels (per-axis and one-launch):
     // FP64 is bound by the FP64 pipe with two pairs' warps per SMSP; the FP32
     // sweeps are latency-bound and take more warps.  Measured on the 200^3

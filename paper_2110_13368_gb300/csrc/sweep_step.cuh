@@ -497,44 +497,22 @@ __device__ __forceinline__ void step_epilogue(const StepSched& Q, const EpiArgs<
         }
         const bool dir = bck[s] == BFVM_BC_DIRICHLET;
         const bool mask_ok = s < 32;
-        if (!(mask_ok && ((got >> s) & 1ull))) {
-            const int i = dep_index(tf, n_sub, 3, s);   // last swept axis of substrate s
-            if (i >= 0) wait_count(Q, Q.done + i, (unsigned)(tf[i + 1] - tf[i]) + Q.extra_need, lane);
-            if (mask_ok) got |= 1ull << s;
-        }
-        if (dir && k < sh_chunks) {
-            const int64_t lo = (int64_t)k * kEpiChunk;
-            const int64_t hi = min(per, lo + kEpiChunk);
-            for (int64_t t0 = lo + lane; t0 < hi; t0 += 32 * kEpiUnroll) {
+        const bool shell = dir && k < sh_chunks;
+        // a source chunk reads its entries (field offsets, the composed
+        // maps, the scale of each voxel) before it waits for the sweeps:
+        // none of them depends on the step, so only the field's gather and
+        // update are left for after the wait (a warp that claims a chunk of
+        // the last swept substrate waits for its last z tasks)
+        constexpr int R = kEpiChunk / 32;
+        int64_t o[R];
+        double a[R], b[R];
+        if (!shell) {
+            const int kk = dir ? k - sh_chunks : k;
+            const int64_t lo = (int64_t)kk * kEpiChunk;
+            const int64_t hi = min(n_seg, lo + kEpiChunk);
 #pragma unroll
-                for (int u = 0; u < kEpiUnroll; ++u) {
-                    const int64_t t = t0 + 32 * u;
-                    if (t < hi) shell_voxel(E, s, bcv[s], t);
-                }
-            }
-            fence_acq_rel_gpu();
-            __syncwarp();
-            if (lane == 0) atomicAdd(Q.shell_done + s, 1u);
-            continue;
-        }
-        if (dir) {
-            k -= sh_chunks;
-            if (!(mask_ok && ((got >> (32 + s)) & 1ull))) {
-                wait_count(Q, Q.shell_done + s, (unsigned)sh_chunks + Q.extra_need, lane);
-                if (mask_ok) got |= 1ull << (32 + s);
-            }
-        }
-        const int64_t lo = (int64_t)k * kEpiChunk;
-        const int64_t hi = min(n_seg, lo + kEpiChunk);
-        for (int64_t g0 = lo + lane; g0 < hi; g0 += 32 * kEpiUnroll) {
-            // all reads of kEpiUnroll entries first (entries are distinct
-            // voxel-substrate pairs, so no two touch one field element)
-            int64_t o[kEpiUnroll];
-            double a[kEpiUnroll], b[kEpiUnroll];
-            T f[kEpiUnroll];
-#pragma unroll
-            for (int u = 0; u < kEpiUnroll; ++u) {
-                const int64_t g = g0 + 32 * u;
+            for (int u = 0; u < R; ++u) {
+                const int64_t g = lo + lane + 32 * u;
                 o[u] = -1;
                 if (g < hi) {
                     const int64_t e = g * n_sub + s;
@@ -551,13 +529,40 @@ __device__ __forceinline__ void step_epilogue(const StepSched& Q, const EpiArgs<
                     }
                 }
             }
-#pragma unroll
-            for (int u = 0; u < kEpiUnroll; ++u)
-                if (o[u] >= 0) f[u] = E.field[o[u]];
-#pragma unroll
-            for (int u = 0; u < kEpiUnroll; ++u)
-                if (o[u] >= 0) E.field[o[u]] = (T)fma(a[u], (double)f[u], b[u]);
         }
+        if (!(mask_ok && ((got >> s) & 1ull))) {
+            const int i = dep_index(tf, n_sub, 3, s);   // last swept axis of substrate s
+            if (i >= 0) wait_count(Q, Q.done + i, (unsigned)(tf[i + 1] - tf[i]) + Q.extra_need, lane);
+            if (mask_ok) got |= 1ull << s;
+        }
+        if (shell) {
+            const int64_t lo = (int64_t)k * kEpiChunk;
+            const int64_t hi = min(per, lo + kEpiChunk);
+            for (int64_t t0 = lo + lane; t0 < hi; t0 += 32 * kEpiUnroll) {
+#pragma unroll
+                for (int u = 0; u < kEpiUnroll; ++u) {
+                    const int64_t t = t0 + 32 * u;
+                    if (t < hi) shell_voxel(E, s, bcv[s], t);
+                }
+            }
+            fence_acq_rel_gpu();
+            __syncwarp();
+            if (lane == 0) atomicAdd(Q.shell_done + s, 1u);
+            continue;
+        }
+        if (dir && !(mask_ok && ((got >> (32 + s)) & 1ull))) {
+            wait_count(Q, Q.shell_done + s, (unsigned)sh_chunks + Q.extra_need, lane);
+            if (mask_ok) got |= 1ull << (32 + s);
+        }
+        // entries are distinct voxel-substrate pairs, so no two touch one
+        // field element: all gathers first, then the updates
+        T f[R];
+#pragma unroll
+        for (int u = 0; u < R; ++u)
+            if (o[u] >= 0) f[u] = E.field[o[u]];
+#pragma unroll
+        for (int u = 0; u < R; ++u)
+            if (o[u] >= 0) E.field[o[u]] = (T)fma(a[u], (double)f[u], b[u]);
     }
 }
 
