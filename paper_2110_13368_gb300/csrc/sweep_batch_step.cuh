@@ -495,38 +495,20 @@ __device__ __forceinline__ void step_epilogue_b(const StepSched& Q, const BMembe
         const EpiArgs<T>& E = Dm[Gg.m].E;
         const int n_sub = Dm[Gg.m].n_sub;
         const int i = dep_index(tf, NS, 3, g);   // last swept axis of the group
-        if (i >= 0) wait_count(Q, Q.done + i, (unsigned)(tf[i + 1] - tf[i]) + Q.extra_need, lane);
         const int sh_chunks = Gg.dir ? (int)epi_shell_chunks(E.nx, E.ny, E.nz) : 0;
-        if (k < sh_chunks) {
-            const int64_t per = shell_count(E);
-            const int64_t lo_t = (int64_t)k * kEpiChunk;
-            const int64_t hi_t = min(per, lo_t + kEpiChunk);
-            for (int64_t t0 = lo_t + lane; t0 < hi_t; t0 += 32 * kEpiUnroll) {
+        const bool shell = k < sh_chunks;
+        // a source chunk reads its entries before its waits (see
+        // step_epilogue of the single-context step)
+        constexpr int R = kEpiChunk / 32;
+        int64_t o[R];
+        double a[R], bb[R];
+        if (!shell) {
+            const int64_t n_seg = E.d_nseg ? *E.d_nseg : E.n_seg;
+            const int64_t lo_g = (int64_t)(k - sh_chunks) * kEpiChunk;
+            const int64_t hi_g = min(n_seg, lo_g + kEpiChunk);
 #pragma unroll
-                for (int u = 0; u < kEpiUnroll; ++u) {
-                    const int64_t t = t0 + 32 * u;
-                    if (t < hi_t) shell_voxel(E, s, Gg.v, t);
-                }
-            }
-            fence_acq_rel_gpu();
-            __syncwarp();
-            if (lane == 0) atomicAdd(Q.shell_done + g, 1u);
-            continue;
-        }
-        if (Gg.dir) {
-            k -= sh_chunks;
-            wait_count(Q, Q.shell_done + g, (unsigned)sh_chunks + Q.extra_need, lane);
-        }
-        const int64_t n_seg = E.d_nseg ? *E.d_nseg : E.n_seg;
-        const int64_t lo_g = (int64_t)k * kEpiChunk;
-        const int64_t hi_g = min(n_seg, lo_g + kEpiChunk);
-        for (int64_t g0 = lo_g + lane; g0 < hi_g; g0 += 32 * kEpiUnroll) {
-            int64_t o[kEpiUnroll];
-            double a[kEpiUnroll], bb[kEpiUnroll];
-            T f[kEpiUnroll];
-#pragma unroll
-            for (int u = 0; u < kEpiUnroll; ++u) {
-                const int64_t gg = g0 + 32 * u;
+            for (int u = 0; u < R; ++u) {
+                const int64_t gg = lo_g + lane + 32 * u;
                 o[u] = -1;
                 if (gg < hi_g) {
                     const int64_t e = gg * n_sub + s;
@@ -543,13 +525,32 @@ __device__ __forceinline__ void step_epilogue_b(const StepSched& Q, const BMembe
                     }
                 }
             }
-#pragma unroll
-            for (int u = 0; u < kEpiUnroll; ++u)
-                if (o[u] >= 0) f[u] = E.field[o[u]];
-#pragma unroll
-            for (int u = 0; u < kEpiUnroll; ++u)
-                if (o[u] >= 0) E.field[o[u]] = (T)fma(a[u], (double)f[u], bb[u]);
         }
+        if (i >= 0) wait_count(Q, Q.done + i, (unsigned)(tf[i + 1] - tf[i]) + Q.extra_need, lane);
+        if (shell) {
+            const int64_t per = shell_count(E);
+            const int64_t lo_t = (int64_t)k * kEpiChunk;
+            const int64_t hi_t = min(per, lo_t + kEpiChunk);
+            for (int64_t t0 = lo_t + lane; t0 < hi_t; t0 += 32 * kEpiUnroll) {
+#pragma unroll
+                for (int u = 0; u < kEpiUnroll; ++u) {
+                    const int64_t t = t0 + 32 * u;
+                    if (t < hi_t) shell_voxel(E, s, Gg.v, t);
+                }
+            }
+            fence_acq_rel_gpu();
+            __syncwarp();
+            if (lane == 0) atomicAdd(Q.shell_done + g, 1u);
+            continue;
+        }
+        if (Gg.dir) wait_count(Q, Q.shell_done + g, (unsigned)sh_chunks + Q.extra_need, lane);
+        T f[R];
+#pragma unroll
+        for (int u = 0; u < R; ++u)
+            if (o[u] >= 0) f[u] = E.field[o[u]];
+#pragma unroll
+        for (int u = 0; u < R; ++u)
+            if (o[u] >= 0) E.field[o[u]] = (T)fma(a[u], (double)f[u], bb[u]);
     }
 }
 
