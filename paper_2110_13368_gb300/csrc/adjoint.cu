@@ -331,14 +331,21 @@ bfvm_status run_backward(Ctx* c, const double* g_final, double* dD, double* dl,
         for (int j = 0; j < len; ++j) {
             if ((r = launch_sweep_plain64(c, 0, cur, V(j, 0), 1)) != BFVM_OK) return r;
             if ((r = launch_sweep_plain64(c, 1, V(j, 0), V(j, 1), 1)) != BFVM_OK) return r;
-            if ((r = launch_sweep_plain64(c, 2, V(j, 1), V(j, 2), 1)) != BFVM_OK) return r;
-            // the field before the sources: P(v3) (kept for the sources'
-            // adjoint when a Dirichlet shell makes it differ from v3), and the
-            // next step's input
-            k_shell<<<gd, 256, 0, c->stream>>>(V(j, 2), any_dir ? V(j, 3) : cur,
-                                               any_dir ? cur : nullptr, c->nx, c->ny, c->nz,
-                                               n_sub, c->pitch, c->d_bc_kind, c->d_bc_value, true);
-            c->launches += 1;
+            // without a Dirichlet shell the z solve also writes the next
+            // step's input (cur) itself
+            if ((r = launch_sweep_plain64(c, 2, V(j, 1), V(j, 2), 1, any_dir ? nullptr : cur)) !=
+                BFVM_OK)
+                return r;
+            if (any_dir || !c->dual_done) {
+                // the field before the sources: P(v3) (kept for the sources'
+                // adjoint when a Dirichlet shell makes it differ from v3), and
+                // the next step's input
+                k_shell<<<gd, 256, 0, c->stream>>>(V(j, 2), any_dir ? V(j, 3) : cur,
+                                                   any_dir ? cur : nullptr, c->nx, c->ny, c->nz,
+                                                   n_sub, c->pitch, c->d_bc_kind, c->d_bc_value,
+                                                   true);
+                c->launches += 1;
+            }
             if (S.n_entries > 0) {
                 k_apply_maps<<<(unsigned)ceil_div(S.n_entries, 256), 256, 0, c->stream>>>(
                     cur, S.n_entries, S.off, S.alpha, S.beta);

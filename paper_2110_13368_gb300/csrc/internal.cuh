@@ -143,6 +143,7 @@ struct Ctx {
     int use_graphs = 1;
     int grid_limit = 0;           // cap on persistent sweep CTAs (0 = one per SM)
     int sweep_kernel = 0;         // 0 warp pairs, 1 one warp per buffer
+    bool dual_done = false;       // the last plain sweep also wrote its second output
     int split = 1;                // split line solve: 0 never, 1 auto, 2 always (plain form)
     int fused_step = 1;           // one launch for x, y, z: 0 never, 1 when not fewer pairs, 2 always
     int dims = 3;                 // 2: the 2-D variant (nz == 1; x and y sweeps,
@@ -415,7 +416,8 @@ void batch_free(BatchImpl* b);
 
 namespace bfvm {
 // plain FP64 sweep along one axis, in -> out (sweeps.cu); dir_mode 0 step,
-// 1 raw replay, 2 adjoint
+// 1 raw replay, 2 adjoint.  With out2, the warp-pair kernel writes its
+// output to out2 as well where it runs, and sets c->dual_done.
 bfvm_status launch_sweep_plain64(Ctx* c, int axis, const double* in, double* out,
-                                 int dir_mode);
+                                 int dir_mode, double* out2 = nullptr);
 }  // namespace bfvm

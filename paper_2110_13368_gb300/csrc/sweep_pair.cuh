@@ -40,7 +40,10 @@ struct Vec16<float> {
 
 // BBAR: B meets F at the pair barrier between reading a group and solving
 // it (true), or after solving it (false; see b_block)
-template <typename T, int AXIS, int MODE, int LAG = Groups<T>::PAIR_LAG, bool BBAR = true>
+// DUAL: B also writes every output to A.field2 (the adjoint's replay keeps
+// the raw z solve and starts the next step from a copy of it)
+template <typename T, int AXIS, int MODE, int LAG = Groups<T>::PAIR_LAG, bool BBAR = true,
+          bool DUAL = false>
 struct PairSweeper {
     static constexpr int G = Groups<T>::G;
     static constexpr int ROWS = Groups<T>::ROWS;
@@ -299,11 +302,19 @@ struct PairSweeper {
             o[u] = (MODE == 2) ? (T)(((double)x * C.o[k0 + u]) * L.inv_other) : x;
         }
         if (AXIS == 0) {
-            if (L.valid) x_store_group(fout + L.base + k0, o);
+            if (L.valid) {
+                x_store_group(fout + L.base + k0, o);
+                if (DUAL) x_store_group(A.field2 + L.base + k0, o);
+            }
         } else if (L.valid) {
             T* dst = fout + L.base + (int64_t)k0 * stride;
 #pragma unroll
             for (int u = 0; u < G; ++u) dst[u * stride] = o[u];
+            if (DUAL) {
+                T* dst2 = A.field2 + L.base + (int64_t)k0 * stride;
+#pragma unroll
+                for (int u = 0; u < G; ++u) dst2[u * stride] = o[u];
+            }
         }
     }
 
@@ -455,12 +466,24 @@ struct PairSweeper {
 #pragma unroll
                 for (int u = 0; u < G; ++u)
                     if (h * G + u < n) dst[u] = o[u];
+                if (DUAL) {
+                    T* dst2 = A.field2 + L.base + h * G;
+#pragma unroll
+                    for (int u = 0; u < G; ++u)
+                        if (h * G + u < n) dst2[u] = o[u];
+                }
             }
         } else if (L.valid) {
             T* dst = fout + L.base + (int64_t)h * G * stride;
 #pragma unroll
             for (int u = 0; u < G; ++u)
                 if (h * G + u < n) dst[u * stride] = o[u];
+            if (DUAL) {
+                T* dst2 = A.field2 + L.base + (int64_t)h * G * stride;
+#pragma unroll
+                for (int u = 0; u < G; ++u)
+                    if (h * G + u < n) dst2[u * stride] = o[u];
+            }
         }
     }
 };
@@ -468,7 +491,7 @@ struct PairSweeper {
 // Dynamic shared memory: [coefficients of all substrates, this axis]
 // [MODE 2 output scales] [line-set prefix] [per pair: column buffer,
 // 2 x 32 row bases of each warp (4 x 32), 32 chain hand-over values].
-template <typename T, int AXIS, int MODE>
+template <typename T, int AXIS, int MODE, bool DUAL = false>
 __global__ void __launch_bounds__(64 * Groups<T>::AXIS_PAIRS, 1) k_sweep_pair(SweepArgs<T> A, LineSet S,
                                                        int64_t n_blocks, int n_slots)
 {
@@ -529,7 +552,7 @@ __global__ void __launch_bounds__(64 * Groups<T>::AXIS_PAIRS, 1) k_sweep_pair(Sw
     if (b0 >= n_blocks) return;   // both warps of the pair leave together
     const int64_t nb = (n_blocks - 1 - b0) / tp + 1;   // blocks of this pair
 
-    PairSweeper<T, AXIS, MODE> sw{A, W, A.in, A.field,
+    PairSweeper<T, AXIS, MODE, Groups<T>::PAIR_LAG, true, DUAL> sw{A, W, A.in, A.field,
                                   AXIS == 0 ? 1 : (AXIS == 1 ? A.pitch : (int64_t)A.ny * A.pitch),
                                   n, ns, lane, 1 + pair};
     auto coef_row = [&](int s) {

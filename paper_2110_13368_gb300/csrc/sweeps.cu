@@ -96,6 +96,7 @@ struct SweepArgs {
     const double* bc_value;
     int dims;              // 3, or 2: the single z layer of a 2-D grid is not a boundary
     int zfaces;            // z planes on the grid's boundary: bit 0 z = 0, bit 1 z = nz - 1
+    T* field2;             // second copy of the output (per-axis pair kernel with DUAL)
 };
 
 // MODE 0: plain Thomas (3 flops per element: FMA + MUL forward, FMA back).
@@ -491,6 +492,12 @@ bfvm_status launch_axis(Ctx* c, const SweepArgs<T>& A)
             if (per_sm < pairs) pairs = (int)(per_sm > 1 ? per_sm : 1);
             size_t smem = fixed + per_pair * pairs;
             auto kern = persistent::k_sweep_pair<T, AXIS, MODE>;
+            if constexpr (sizeof(T) == 8 && MODE == 0) {
+                if (A.field2) {   // the adjoint's replay: a second copy of the output
+                    kern = persistent::k_sweep_pair<T, AXIS, MODE, true>;
+                    c->dual_done = true;
+                }
+            }
             BFVM_CUDA(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                               (int)smem));
             int64_t grid = ceil_div(n_blocks, pairs);
@@ -713,11 +720,13 @@ bfvm_status launch_xy_plain64(Ctx* c)
 // Plain FP64 sweep along one axis from `in` to `out` (pitched layout), with
 // Dirichlet mode dir_mode (see k_sweep).  Used by the adjoint.
 bfvm_status launch_sweep_plain64(Ctx* c, int axis, const double* in, double* out,
-                                 int dir_mode)
+                                 int dir_mode, double* out2)
 {
     SweepArgs<double> A = make_args<double>(c, axis, 0, c->coef.r, c->coef.cr, c->coef.c);
     A.in = in;
     A.field = out;
+    A.field2 = out2;
+    c->dual_done = false;
     if (axis == 0) {
         if (dir_mode == 1) return launch_axis<double, 0, 0, 1>(c, A);
         if (dir_mode == 2) return launch_axis<double, 0, 0, 2>(c, A);
