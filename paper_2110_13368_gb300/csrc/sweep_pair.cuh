@@ -165,12 +165,16 @@ struct PairSweeper {
     {
         return fwd_val(C, prev, d, C.a[k], (MODE == 0 && sizeof(T) == 4) ? C.a_lo[k] : (T)0);
     }
-    // the same step with the element's coefficients already in registers
+    // the same step with the element's coefficients already in registers.
+    // EXACT (FP32, c exactly representable: c_lo = 0): fl(c prev + d) is the
+    // single rounding of one FMA, so the compensated sum is not needed
+    template <bool EXACT = false>
     __device__ __forceinline__ T fwd_val(const CoefRow<T>& C, T prev, T d, T a, T a_lo) const
     {
         if (MODE != 0) return fma(a, prev, d);
         if (sizeof(T) == 8) return fma(C.c, prev, d) * a;
-        const float t = comp_axpy((float)C.c, (float)C.c_lo, (float)prev, (float)d);
+        const float t = EXACT ? __fmaf_rn((float)C.c, (float)prev, (float)d)
+                              : comp_axpy((float)C.c, (float)C.c_lo, (float)prev, (float)d);
         return (T)__fmaf_rn(t, (float)a, __fmul_rn(t, (float)a_lo));
     }
     __device__ __forceinline__ T bwd_op(const CoefRow<T>& C, T x, T w, int k) const
@@ -278,9 +282,16 @@ struct PairSweeper {
             ca[u] = C.a[g * G + u];
             cl[u] = LO ? C.a_lo[g * G + u] : (T)0;
         }
+        if (LO && C.c_lo == (T)0) fwd_chain<Q, true>(C, prev, p, d, ca, cl);
+        else fwd_chain<Q, false>(C, prev, p, d, ca, cl);
+    }
+    template <int Q, bool EXACT>
+    __device__ __forceinline__ void fwd_chain(const CoefRow<T>& C, T& prev, T* p, T (&d)[G],
+                                              const T (&ca)[G], const T (&cl)[G]) const
+    {
 #pragma unroll
         for (int u = 0; u < G; ++u) {
-            prev = fwd_val(C, prev, d[u], ca[u], cl[u]);
+            prev = fwd_val<EXACT>(C, prev, d[u], ca[u], cl[u]);
             if (AXIS == 0) {
                 d[u] = prev;
                 if (u % CW == CW - 1) x_write_chunk(p, u / CW, d + (u - (CW - 1)));
