@@ -56,8 +56,8 @@ def parse():
                     help="skip the FP32 / batched / adjoint form measurements")
     ap.add_argument("--form-steps", type=int, default=10)
     ap.add_argument("--form", default=None,
-                    choices=["fp32", "batched", "batched_fp32", "adjoint", "two_d", "nodes",
-                             "slabs"],
+                    choices=["fp32", "batched", "batched_fp32", "batched_phases", "adjoint",
+                             "two_d", "nodes", "slabs"],
                     help="time one form of the step on its own (for profiling runs): "
                          "--warmup untimed and --steps timed steps, one JSON line")
     return ap.parse_args()
@@ -717,10 +717,13 @@ def run_form(args):
         closers.append(sim)
         n_upd, step = p.updates_per_step, (lambda: sim.step(1))
         launches = lambda: sim.info()["launches"]
-    elif form in ("batched", "batched_fp32"):
-        probs = inputs.batch_256(seed=0, precision=64 if form == "batched" else 32)
+    elif form in ("batched", "batched_fp32", "batched_phases"):
+        # batched_phases: the FP64 batch on its tuned per-phase launches
+        probs = inputs.batch_256(seed=0, precision=32 if form == "batched_fp32" else 64)
         sims = [bfvm.Sim.from_problem(q) for q in probs]
         batch = bfvm.Batch(sims)
+        if form == "batched_phases":
+            batch.set_option(bfvm.BATCH_OPT_ONE_LAUNCH, 0)
         closers += [batch] + sims
         n_upd, step = sum(q.updates_per_step for q in probs), (lambda: batch.step(1))
         launches = lambda: batch.info()["launches"]
