@@ -200,6 +200,28 @@ def dist_setup(args):
     return world, rank, local
 
 
+def host_link_rates(host_in, host_out, stream, reps=3):
+    """Best-of-reps GB/s of pinned host -> device and device -> host copies of
+    host_in's size on `stream` (CUDA events)."""
+    import torch
+    dev_buf = torch.empty(host_in.shape, dtype=host_in.dtype, device="cuda")
+    nbytes = host_in.numel() * host_in.element_size()
+    best = [0.0, 0.0]
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        for _ in range(reps):
+            for k, (dst, src) in enumerate(((dev_buf, host_in), (host_out, dev_buf))):
+                torch.cuda.synchronize()
+                e0.record(stream)
+                dst.copy_(src, non_blocking=True)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                best[k] = max(best[k], nbytes / (e0.elapsed_time(e1) / 1e3) / 1e9)
+    del dev_buf
+    return best[0], best[1]
+
+
 def max_over_ranks(value, world, device=None):
     """The job's time from each rank's own: the maximum over the ranks of
     the initialised process group (the value itself on one rank)."""
@@ -358,7 +380,7 @@ def measure_forms(args, plain_ups, dev, stream, flush):
                     "form": "plain Thomas, x and y sweeps, split line solve", "ratio_vs_plain_fp64_3d": ups2 / plain_ups,
                     "hbm_frac_32B_per_update": ups2 * 4 * 8 / 1e9 / peaks()[0]}
     # Dirichlet nodes: the 200^3 x 2 workload with 40 vessel columns of
-    # oxygen nodes (per-axis launches plus node fills)
+    # oxygen nodes (FP64: a node-fill launch plus the one-launch step)
     pt = inputs.tumour_200(steps=K)
     rng = np.random.default_rng(5)
     vox, sub, val = [], [], []
@@ -634,6 +656,15 @@ def run_ours(args):
            "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
            "steps": args.e2e_steps,
            "call": "bfvm_set_density(host) + bfvm_step(1) + bfvm_get_density(host)"}
+    # the host link's own rates (pinned buffers of the same size, copy engine)
+    # and the e2e rate they allow: both copies plus the device step
+    h2d, d2h = host_link_rates(host_in, host_out, stream)
+    link_ms = nbytes / h2d / 1e6 + nbytes / d2h / 1e6 + ms_per_step
+    e2e["host_link"] = {"h2d_gbs": h2d, "d2h_gbs": d2h,
+                        "bound_value": N / (link_ms / 1e3),
+                        "frac_of_bound": e2e["value"] / world / (N / (link_ms / 1e3)),
+                        "note": "pinned cudaMemcpyAsync of the field in each direction; "
+                                "bound = updates per (H2D + D2H + ms_per_step)"}
 
     forms = None
     if not args.no_forms and world == 1:

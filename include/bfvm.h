@@ -137,10 +137,15 @@ bfvm_status bfvm_set_cells(bfvm_ctx* ctx, int64_t n_cells, const double* pos,
  *   voxel[n]      int64, 0 <= voxel < nx ny nz
  *   substrate[n]  int32, 0 <= substrate < n_sub
  *   value[n]      FP64, finite
+ * A node on a face of its substrate's Dirichlet shell is set after the
+ * shell, so the solve of the line it ends takes the node's value there.
  * Arrays follow on_device like the other setters and are copied.  3-D
- * contexts only (BFVM_EINVAL for the 2-D variant); a context with nodes
- * runs its sweeps as one launch per axis and cannot record for the adjoint
- * or join a batch (BFVM_ESTATE).  Resets any recorded forward run.
+ * contexts only (BFVM_EINVAL for the 2-D variant).  In FP64 a step with
+ * nodes is one node-fill launch plus option 8's one launch (node values
+ * written after the x and y tasks that solve their lines and at the end of
+ * the step); FP32 runs it one launch per axis with node fills between them.
+ * A context with nodes cannot record for the adjoint or join a batch
+ * (BFVM_ESTATE).  Resets any recorded forward run.
  */
 bfvm_status bfvm_set_dirichlet_nodes(bfvm_ctx* ctx, int64_t n_nodes, const int64_t* voxel,
                                      const int32_t* substrate, const double* value,
@@ -238,8 +243,9 @@ bfvm_status bfvm_get_info(const bfvm_ctx* ctx, int64_t* info);
  *          default); small caps make every warp walk many line blocks
  *   key 7  sweep kernel: 0 warp pairs sharing each line buffer (the
  *          default), 1 one warp per line buffer
- *   key 8  with warp pairs (3-D grids, no Dirichlet nodes): the x, y and z
- *          sweeps of a step, its Dirichlet shell and its cell sources as one
+ *   key 8  with warp pairs (3-D grids; with Dirichlet nodes FP64 only):
+ *          the x, y and z sweeps of a step, its Dirichlet shell, its nodes
+ *          and its cell sources as one
  *          persistent launch whose warp pairs take (axis, substrate, 32-line
  *          block) tasks in order, a task starting once the previous axis of
  *          its substrate is complete.  1 (the default): where that launch

@@ -634,7 +634,10 @@ bfvm_status bfvm_set_dirichlet_nodes(bfvm_ctx* h, int64_t n_nodes, const int64_t
     BFVM_CUDA(c, cudaMemcpy(c->d_node_sub, sub32.data(), sizeof(int32_t) * m, cudaMemcpyHostToDevice));
     BFVM_CUDA(c, cudaMemcpy(c->d_node_val, val.data(), sizeof(double) * m, cudaMemcpyHostToDevice));
     c->n_nodes = m;
-    return BFVM_OK;
+    std::vector<int64_t> vox64(vox32.begin(), vox32.end());
+    const bfvm_status st = build_node_tables(c, vox64, sub32, val, off);
+    if (st != BFVM_OK) c->free_nodes();
+    return st;
 }
 
 bfvm_status bfvm_get_info(const bfvm_ctx* h, int64_t* info)

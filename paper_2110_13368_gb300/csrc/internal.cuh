@@ -117,6 +117,14 @@ struct SourceTable {
     int64_t* scan_ws = nullptr; // block sums of the scan
 };
 
+// A Dirichlet node as the one-launch step writes it (sweep_step.cuh): field
+// offset, raw value and coordinates (for the rescaled form's scales)
+struct NodePatch {
+    int64_t off;
+    double v;
+    int32_t x, y, z, pad;
+};
+
 struct Ctx {
     int nx = 0, ny = 0, nz = 0, n_sub = 0, precision = 64;
     int64_t pitch = 0;            // row length in elements (>= nx, multiple of 4)
@@ -171,12 +179,36 @@ struct Ctx {
     int32_t* d_node_vox = nullptr;   // x + nx (y + ny z)
     int32_t* d_node_sub = nullptr;
     double* d_node_val = nullptr;
+    // nodes on a Dirichlet shell face: per axis, the raw values at the ends of
+    // the lines they end ([line][2], NaN elsewhere; null when there are none)
+    double* d_node_ends[3] = {nullptr, nullptr, nullptr};
+    // the one-launch step with nodes: the patches of the x and y tasks
+    // ([n_tasks + 1] first patch of each task) and every node by substrate
+    // ([n_sub + 1] first node of each substrate) for the epilogue
+    int* d_node_task_first = nullptr;
+    NodePatch* d_node_patch = nullptr;
+    int* d_node_sfirst = nullptr;
+    NodePatch* d_node_epi = nullptr;
+    std::vector<int> node_chunks;     // epilogue node chunks per substrate
     void free_nodes()
     {
         if (d_node_off) cudaFree(d_node_off);
         if (d_node_vox) cudaFree(d_node_vox);
         if (d_node_sub) cudaFree(d_node_sub);
         if (d_node_val) cudaFree(d_node_val);
+        for (int a = 0; a < 3; ++a) {
+            if (d_node_ends[a]) cudaFree(d_node_ends[a]);
+            d_node_ends[a] = nullptr;
+        }
+        if (d_node_task_first) cudaFree(d_node_task_first);
+        if (d_node_patch) cudaFree(d_node_patch);
+        if (d_node_sfirst) cudaFree(d_node_sfirst);
+        if (d_node_epi) cudaFree(d_node_epi);
+        d_node_task_first = nullptr;
+        d_node_patch = nullptr;
+        d_node_sfirst = nullptr;
+        d_node_epi = nullptr;
+        node_chunks.clear();
         d_node_off = nullptr;
         d_node_vox = d_node_sub = nullptr;
         d_node_val = nullptr;
@@ -343,6 +375,12 @@ bfvm_status run_backward(Ctx* c, const double* g_final_dev, double* dD_dev,
 
 // layout conversion between the caller's dense [s][z][y][x] and the pitched
 // field (layout.cu)
+// Device tables of the Dirichlet nodes (sweeps.cu): line-end values for the
+// sweeps and the one-launch step's patch lists.  Nodes given as voxel,
+// substrate, value and pitched field offset, one per (voxel, substrate).
+bfvm_status build_node_tables(Ctx* c, const std::vector<int64_t>& vox,
+                              const std::vector<int32_t>& sub, const std::vector<double>& val,
+                              const std::vector<int64_t>& off);
 bfvm_status copy_in_dense(Ctx* c, const void* src, bool on_device);
 bfvm_status copy_out_dense(Ctx* c, void* dst, bool on_device);
 

@@ -111,21 +111,26 @@ __device__ __forceinline__ Line make_line(const SweepArgs<T>& A, const LineSet& 
         L.base = ((int64_t)s * A.nz * A.ny + oy) * A.pitch + ox;
     }
     L.dir = A.bc_kind[s] == BFVM_BC_DIRICHLET;
-    const double v = A.bc_value[s];
-    L.end0 = v;
-    L.end1 = v;
+    double v0, v1;   // the ends' values: the boundary value, or a node's there
+    end_values(A.ends, full_line<T, AXIS>(A, s, ox, oy, oz), A.bc_value[s], v0, v1);
+    L.end0 = v0;
+    L.end1 = v1;
     L.inv_other = 1.0;
     if (MODE >= 1) {
         const int64_t row = (int64_t)s * A.L;
-        double kline;
-        if (AXIS == 0)
-            kline = v * A.sc_p[row + A.off_y + oy] * A.sc_p[row + A.off_z + oz];
-        else if (AXIS == 1)
-            kline = v * A.sc_p1[row + A.off_x + ox] * A.sc_p[row + A.off_z + oz];
-        else
-            kline = v * A.sc_p1[row + A.off_x + ox] * A.sc_p1[row + A.off_y + oy];
-        L.end0 = kline * A.sc_p[row + A.axis_off];
-        L.end1 = kline * A.sc_p[row + A.axis_off + A.n - 1];
+        double sa, sb;
+        if (AXIS == 0) {
+            sa = A.sc_p[row + A.off_y + oy];
+            sb = A.sc_p[row + A.off_z + oz];
+        } else if (AXIS == 1) {
+            sa = A.sc_p1[row + A.off_x + ox];
+            sb = A.sc_p[row + A.off_z + oz];
+        } else {
+            sa = A.sc_p1[row + A.off_x + ox];
+            sb = A.sc_p1[row + A.off_y + oy];
+        }
+        L.end0 = (v0 * sa * sb) * A.sc_p[row + A.axis_off];
+        L.end1 = (v1 * sa * sb) * A.sc_p[row + A.axis_off + A.n - 1];
         if (MODE == 2 && AXIS == 2)
             L.inv_other = A.isc_p1[row + A.off_x + ox] * A.isc_p1[row + A.off_y + oy];
     }

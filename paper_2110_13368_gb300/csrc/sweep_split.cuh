@@ -59,6 +59,7 @@ struct SplitLine {
     int s;
     bool dir, all_shell;
     double v;
+    double v0, v1;   // input values of the two ends (a Dirichlet node's, if one sits there)
 };
 
 template <typename T, int AXIS>
@@ -92,6 +93,7 @@ __device__ __forceinline__ SplitLine split_line(const SweepArgs<T>& A, int64_t l
     L.dir = A.bc_kind[L.s] == BFVM_BC_DIRICHLET;
     L.all_shell = L.dir && other_shell;
     L.v = A.bc_value[L.s];
+    end_values(A.ends, line, L.v, L.v0, L.v1);
     return L;
 }
 
@@ -198,7 +200,9 @@ __global__ void __launch_bounds__(256) k_split_fwd(SweepArgs<T> A, SplitArgs Z)
         T prev = (T)0;
         for (int k = k0; k < k1; ++k) {
             T d = V.get(k);
-            if (L.all_shell || (L.dir && (k == 0 || k == n - 1))) d = (T)vin;
+            if (L.all_shell) d = (T)vin;
+            else if (L.dir && (k == 0 || k == n - 1))
+                d = (T)(DIR == 0 ? (k == 0 ? L.v0 : L.v1) : vin);
             if (sizeof(T) == 8) {
                 prev = (T)(fma((double)c, (double)prev, (double)d) * (double)A.r[row + k]);
             } else {

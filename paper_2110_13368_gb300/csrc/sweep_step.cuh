@@ -67,8 +67,16 @@ struct StepSched {
     // epilogue of the step (after every z task of a substrate): the
     // Dirichlet shell, then the cell sources, in chunks of kEpiChunk
     unsigned* eclaim;       // [1] next epilogue chunk
-    unsigned* shell_done;   // [n_sub] completed shell chunks of each substrate
+    unsigned* shell_done;   // [n_sub] completed shell and node chunks of each substrate
     int n_epi_chunks;       // over all substrates
+    // Dirichlet nodes (the kernel's NODES form): the nodes on the lines of
+    // each x and y task, written after the task's outputs, and every node by
+    // substrate, written by the epilogue's node chunks (after the substrate's
+    // shell, before its sources)
+    const int* node_task_first;   // [n_tasks + 1]
+    const NodePatch* node_patch;
+    const int* node_sfirst;       // [n_sub + 1]
+    const NodePatch* node_epi;
 };
 
 // Everything the epilogue reads: grid, the scales of state p + 1 (null when
@@ -90,6 +98,8 @@ struct EpiArgs {
 
 constexpr int kEpiUnroll = 8;                  // independent elements per lane
 constexpr int kEpiChunk = 32 * kEpiUnroll * 2;  // elements per claimed chunk (2 rounds)
+constexpr int kNodeUnroll = 4;                 // nodes per lane of an epilogue node chunk
+constexpr int kNodeChunk = 32 * kNodeUnroll;
 
 // Epilogue chunks, substrate by substrate: the shell chunks of s (Dirichlet
 // substrates only), then its source chunks (kEpiChunk occupied voxels each).
@@ -230,10 +240,12 @@ struct LinePre {
     int64_t base;
     int s;
     bool valid, dir;
-    double v, sa, sb, se0, se1, ia, ib;
+    double v, v1, sa, sb, se0, se1, ia, ib;   // v, v1: input values of the two ends
 };
 
-template <typename T, int AXIS, int MODE>
+// NODES: a Dirichlet node may sit at either end of the line (its value
+// then replaces the boundary value there)
+template <typename T, int AXIS, int MODE, bool NODES = false>
 __device__ __forceinline__ LinePre issue_line(const SweepArgs<T>& A, const LineSet& S,
                                               const int64_t* fs, const int* bck,
                                               const double* bcv, TaskRef r, int lane)
@@ -261,6 +273,8 @@ __device__ __forceinline__ LinePre issue_line(const SweepArgs<T>& A, const LineS
     }
     P.dir = bck[s] == BFVM_BC_DIRICHLET;
     P.v = bcv[s];
+    P.v1 = P.v;
+    if (NODES && P.dir) end_values(A.ends, full_line<T, AXIS>(A, s, ox, oy, oz), bcv[s], P.v, P.v1);
     P.sa = P.sb = P.se0 = P.se1 = P.ia = P.ib = 1.0;
     if (MODE >= 1 && P.dir) {
         const int64_t row = (int64_t)s * A.L;
@@ -285,7 +299,7 @@ __device__ __forceinline__ LinePre issue_line(const SweepArgs<T>& A, const LineS
     return P;
 }
 
-template <int MODE>
+template <int MODE, bool NODES = false>
 __device__ __forceinline__ Line finish_line(const LinePre& P)
 {
     Line L;
@@ -293,12 +307,16 @@ __device__ __forceinline__ Line finish_line(const LinePre& P)
     L.s = P.s;
     L.valid = P.valid;
     L.dir = P.dir;
-    if (MODE >= 1) {
+    if (MODE >= 1 && NODES) {
+        L.end0 = (P.v * P.sa * P.sb) * P.se0;
+        L.end1 = (P.v1 * P.sa * P.sb) * P.se1;
+    } else if (MODE >= 1) {
         const double kline = P.v * P.sa * P.sb;
         L.end0 = kline * P.se0;
         L.end1 = kline * P.se1;
     } else {
-        L.end0 = L.end1 = P.v;
+        L.end0 = P.v;
+        L.end1 = NODES ? P.v1 : P.v;
     }
     L.inv_other = P.ia * P.ib;
     return L;
@@ -467,13 +485,21 @@ __device__ __forceinline__ void wait_count(const StepSched& Q, const unsigned* p
     fence_acq_rel_gpu();
 }
 
+// Epilogue node chunks of substrate s (NODES form): kNodeChunk nodes each
+__device__ __forceinline__ int epi_node_chunks(const StepSched& Q, int s)
+{
+    return (Q.node_sfirst[s + 1] - Q.node_sfirst[s] + kNodeChunk - 1) / kNodeChunk;
+}
+
 // A warp with no sweep task left takes epilogue chunks, claimed in order:
 // for each substrate s, the shell chunks of s once every task of the last
-// swept axis of s is complete, then the source chunks of s once the shell
-// of s is complete too (a cell may sit in a shell voxel).  A chunk waits
-// only on sweep tasks and on earlier chunks that never wait on it, and a
-// warp acquires each completion at most once.
-template <typename T>
+// swept axis of s is complete, then (NODES) its node chunks once the shell
+// of s is complete too (a node overrides the shell), then the source chunks
+// of s once the shell and the nodes of s are complete (a cell may sit in a
+// shell voxel or on a node).  A chunk waits only on sweep tasks and on
+// earlier chunks that never wait on it, and a warp acquires each completion
+// at most once.
+template <typename T, bool NODES = false>
 __device__ __forceinline__ void step_epilogue(const StepSched& Q, const EpiArgs<T>& E,
                                               const int* tf, const int* bck, const double* bcv,
                                               int lane)
@@ -491,13 +517,49 @@ __device__ __forceinline__ void step_epilogue(const StepSched& Q, const EpiArgs<
         if (c >= (unsigned)Q.n_epi_chunks) return;
         int s = 0, k = (int)c;
         for (; s < n_sub; ++s) {
-            const int here = (bck[s] == BFVM_BC_DIRICHLET ? sh_chunks : 0) + src_chunks;
+            const int here = (bck[s] == BFVM_BC_DIRICHLET ? sh_chunks : 0) +
+                             (NODES ? epi_node_chunks(Q, s) : 0) + src_chunks;
             if (k < here) break;
             k -= here;
         }
         const bool dir = bck[s] == BFVM_BC_DIRICHLET;
         const bool mask_ok = s < 32;
         const bool shell = dir && k < sh_chunks;
+        const int nch = NODES ? epi_node_chunks(Q, s) : 0;
+        // node chunk kn of s (NODES), else -1
+        const int kn = (NODES && !shell && k - (dir ? sh_chunks : 0) < nch)
+                           ? k - (dir ? sh_chunks : 0) : -1;
+        if (NODES && kn >= 0) {
+            if (!(mask_ok && ((got >> s) & 1ull))) {
+                const int i = dep_index(tf, n_sub, 3, s);
+                if (i >= 0) wait_count(Q, Q.done + i, (unsigned)(tf[i + 1] - tf[i]) + Q.extra_need, lane);
+                if (mask_ok) got |= 1ull << s;
+            }
+            if (dir) wait_count(Q, Q.shell_done + s, (unsigned)sh_chunks + Q.extra_need, lane);
+            // the node values after the step's sweeps and shell (scales of
+            // state p + 1, or plain values)
+            const int lo = Q.node_sfirst[s] + kn * kNodeChunk;
+            const int hi = min(Q.node_sfirst[s + 1], lo + kNodeChunk);
+            NodePatch e[kNodeUnroll];
+#pragma unroll
+            for (int u = 0; u < kNodeUnroll; ++u)
+                if (lo + lane + 32 * u < hi) e[u] = Q.node_epi[lo + lane + 32 * u];
+#pragma unroll
+            for (int u = 0; u < kNodeUnroll; ++u) {
+                if (lo + lane + 32 * u >= hi) continue;
+                double v = e[u].v;
+                if (E.sc) {
+                    const double* q = E.sc + (int64_t)s * E.L;
+                    v = v * (__ldg(q + e[u].x) * __ldg(q + E.nx + e[u].y) *
+                             __ldg(q + E.nx + E.ny + e[u].z));
+                }
+                E.field[e[u].off] = (T)v;
+            }
+            fence_acq_rel_gpu();
+            __syncwarp();
+            if (lane == 0) atomicAdd(Q.shell_done + s, 1u);
+            continue;
+        }
         // a source chunk reads its entries (field offsets, the composed
         // maps, the scale of each voxel) before it waits for the sweeps:
         // none of them depends on the step, so only the field's gather and
@@ -507,7 +569,7 @@ __device__ __forceinline__ void step_epilogue(const StepSched& Q, const EpiArgs<
         int64_t o[R];
         double a[R], b[R];
         if (!shell) {
-            const int kk = dir ? k - sh_chunks : k;
+            const int kk = (dir ? k - sh_chunks : k) - nch;
             const int64_t lo = (int64_t)kk * kEpiChunk;
             const int64_t hi = min(n_seg, lo + kEpiChunk);
 #pragma unroll
@@ -550,8 +612,9 @@ __device__ __forceinline__ void step_epilogue(const StepSched& Q, const EpiArgs<
             if (lane == 0) atomicAdd(Q.shell_done + s, 1u);
             continue;
         }
-        if (dir && !(mask_ok && ((got >> (32 + s)) & 1ull))) {
-            wait_count(Q, Q.shell_done + s, (unsigned)sh_chunks + Q.extra_need, lane);
+        const unsigned need_sh = (dir ? (unsigned)sh_chunks : 0u) + (unsigned)nch;
+        if (need_sh > 0 && !(mask_ok && ((got >> (32 + s)) & 1ull))) {
+            wait_count(Q, Q.shell_done + s, need_sh + Q.extra_need, lane);
             if (mask_ok) got |= 1ull << (32 + s);
         }
         // entries are distinct voxel-substrate pairs, so no two touch one
@@ -632,7 +695,7 @@ __device__ __forceinline__ void mark_acquired(FState& f, int i)
 // dependency count, so neither round trip is on the pair's path at the
 // hand-over (an acquire fence there completes the acquire pattern; only when
 // the early read was short does F read the count again).
-template <typename T, int AXIS, int MODE>
+template <typename T, int AXIS, int MODE, bool NODES>
 __device__ __forceinline__ void f_axis(FState& f, const SweepArgs<T>& A, const LineSet& S,
                                        const int64_t* fs, const SweepArgs<T>* sA,
                                        const StepSched& Q, const int* tf, const PairShared<T>& P)
@@ -641,8 +704,9 @@ __device__ __forceinline__ void f_axis(FState& f, const SweepArgs<T>& A, const L
     while (f.t < NT) {
         const TaskRef r = decode_task(tf, Q.n_sub, f.t);
         if (r.a != AXIS) return;
-        const Line L = finish_line<MODE>(
-            f.have_line ? f.pre : issue_line<T, AXIS, MODE>(A, S, fs, P.bck, P.bcv, r, P.lane));
+        const Line L = finish_line<MODE, NODES>(
+            f.have_line ? f.pre
+                        : issue_line<T, AXIS, MODE, NODES>(A, S, fs, P.bck, P.bcv, r, P.lane));
         f.have_line = false;
         const bool has_next = f.tn < NT;
         TaskRef rn{0, 0, 0};
@@ -659,7 +723,7 @@ __device__ __forceinline__ void f_axis(FState& f, const SweepArgs<T>& A, const L
             if (P.lane == 0) raw2 = atomicAdd(Q.claim, 1u);
             if (rn.a == AXIS) {
                 // the next task's lines: their global reads overlap this task
-                f.pre = issue_line<T, AXIS, MODE>(A, S, fs, P.bck, P.bcv, rn, P.lane);
+                f.pre = issue_line<T, AXIS, MODE, NODES>(A, S, fs, P.bck, P.bcv, rn, P.lane);
                 f.have_line = true;
             }
         }
@@ -718,8 +782,31 @@ struct BState {
     T x;
 };
 
-// B warp: back substitutions of consecutive tasks on axis AXIS
+// B warp (NODES form): the Dirichlet nodes [i0, i1) on the lines of an x or
+// y task take their values after the sweep of AXIS (scales of the axes swept
+// so far in state p + 1, the others in state p), one node per lane.  The
+// warp barrier orders every lane's stores of the task's lines before them.
 template <typename T, int AXIS, int MODE>
+__device__ __forceinline__ void patch_task_nodes(const SweepArgs<T>& A, const StepSched& Q,
+                                                 T* field, int i0, int i1, int s, int lane)
+{
+    if (i0 == i1) return;
+    __syncwarp();
+    for (int i = i0 + lane; i < i1; i += 32) {
+        const NodePatch e = Q.node_patch[i];
+        double v = e.v;
+        if (MODE >= 1) {
+            const int64_t row = (int64_t)s * A.L;
+            const double* sy = AXIS >= 1 ? A.sc_p1 : A.sc_p;
+            v = v * (A.sc_p1[row + A.off_x + e.x] * sy[row + A.off_y + e.y] *
+                     A.sc_p[row + A.off_z + e.z]);
+        }
+        field[e.off] = (T)v;
+    }
+}
+
+// B warp: back substitutions of consecutive tasks on axis AXIS
+template <typename T, int AXIS, int MODE, bool NODES>
 __device__ __forceinline__ void b_axis(BState<T>& b, const SweepArgs<T>& A, const LineSet& S,
                                        const int64_t* fs, const SweepArgs<T>* sA,
                                        const StepSched& Q, const int* tf, const PairShared<T>& P)
@@ -736,7 +823,16 @@ __device__ __forceinline__ void b_axis(BState<T>& b, const SweepArgs<T>& A, cons
             iters = phase_iters(sA, rn.a, AXIS);
         }
         const int lane = P.lane;
-        auto rel = [&]() { task_done(Q, r, lane); };
+        // the task's node patches (read now, used after the task's stores)
+        int ni0 = 0, ni1 = 0;
+        if (NODES && AXIS < 2) {
+            ni0 = Q.node_task_first[b.t];
+            ni1 = Q.node_task_first[b.t + 1];
+        }
+        auto rel = [&]() {
+            if (NODES && AXIS < 2) patch_task_nodes<T, AXIS, MODE>(A, Q, P.field, ni0, ni1, r.s, lane);
+            task_done(Q, r, lane);
+        };
         b_task<T, AXIS, MODE>(A, S, fs, P.bck, P.bcv, P.field, P.K, P.W, P.ns, P.lane, P.bar_id,
                               r, P.rbB, P.hs, b.k & 1, b.x, paired, iters, rel);
         if (!more) {
@@ -793,8 +889,10 @@ __host__ __device__ constexpr int step_ncoef()
 
 // The step kernel.  T: element type; MXY: form of the x and y sweeps (0
 // plain, 1 rescaled); MZ: form of the z sweep (MXY, or 2: rescaled and
-// renormalising).
-template <typename T, int MXY, int MZ>
+// renormalising); NODES: the context holds Dirichlet nodes (line ends from
+// the node end tables, node patches after x and y tasks, node chunks in the
+// epilogue; the values before the x sweep are written by a launch ahead).
+template <typename T, int MXY, int MZ, bool NODES>
 __global__ void __launch_bounds__(64 * Groups<T>::MAX_PAIRS, 1)
     k_step_pair(SweepArgs<T> A0, SweepArgs<T> A1, SweepArgs<T> A2, LineSet S0, LineSet S1,
                 LineSet S2, StepSched Q, EpiArgs<T> E, int n_slots)
@@ -909,9 +1007,9 @@ __global__ void __launch_bounds__(64 * Groups<T>::MAX_PAIRS, 1)
             }
             pair_sync(bar_id);                          // nothing for B
         }
-        f_axis<T, 0, MXY>(f, sA[0], sS[0], fs0, sA, Q, tf, P);
-        f_axis<T, 1, MXY>(f, sA[1], sS[1], fs1, sA, Q, tf, P);
-        f_axis<T, 2, MZ>(f, sA[2], sS[2], fs2, sA, Q, tf, P);
+        f_axis<T, 0, MXY, NODES>(f, sA[0], sS[0], fs0, sA, Q, tf, P);
+        f_axis<T, 1, MXY, NODES>(f, sA[1], sS[1], fs1, sA, Q, tf, P);
+        f_axis<T, 2, MZ, NODES>(f, sA[2], sS[2], fs2, sA, Q, tf, P);
     } else {
         BState<T> b;
         pair_sync(bar_id);                              // first hand-over
@@ -920,13 +1018,13 @@ __global__ void __launch_bounds__(64 * Groups<T>::MAX_PAIRS, 1)
         b.paired = ho[2] != 0;
         b.x = handover[lane];
         b.k = 0;
-        b_axis<T, 0, MXY>(b, sA[0], sS[0], fs0, sA, Q, tf, P);
-        b_axis<T, 1, MXY>(b, sA[1], sS[1], fs1, sA, Q, tf, P);
-        b_axis<T, 2, MZ>(b, sA[2], sS[2], fs2, sA, Q, tf, P);
+        b_axis<T, 0, MXY, NODES>(b, sA[0], sS[0], fs0, sA, Q, tf, P);
+        b_axis<T, 1, MXY, NODES>(b, sA[1], sS[1], fs1, sA, Q, tf, P);
+        b_axis<T, 2, MZ, NODES>(b, sA[2], sS[2], fs2, sA, Q, tf, P);
     }
 
     // sweep tasks exhausted for this warp: the step's epilogue
-    step_epilogue(Q, E, tf, bck, bcv, lane);
+    step_epilogue<T, NODES>(Q, E, tf, bck, bcv, lane);
 
     __syncthreads();
     if (threadIdx.x == 0) {

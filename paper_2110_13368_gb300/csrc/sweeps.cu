@@ -97,7 +97,37 @@ struct SweepArgs {
     int dims;              // 3, or 2: the single z layer of a 2-D grid is not a boundary
     int zfaces;            // z planes on the grid's boundary: bit 0 z = 0, bit 1 z = nz - 1
     T* field2;             // second copy of the output (per-axis pair kernel with DUAL)
+    // Dirichlet nodes at line ends: [line][2] raw node values at the k = 0
+    // and k = n - 1 ends of each line of a Dirichlet substrate (NaN where no
+    // node sits), lines numbered as by full_line; null when no node lies on
+    // a Dirichlet shell face
+    const double* ends;
 };
+
+// Line number of the line along AXIS through (ox, oy, oz) of substrate s, over
+// all lines of the grid (the one-thread-per-line sweep's numbering)
+template <typename T, int AXIS>
+__device__ __forceinline__ int64_t full_line(const SweepArgs<T>& A, int s, int ox, int oy, int oz)
+{
+    if (AXIS == 0) return ((int64_t)s * A.nz + oz) * A.ny + oy;
+    if (AXIS == 1) return ((int64_t)s * A.nz + oz) * A.nx + ox;
+    return ((int64_t)s * A.ny + oy) * A.nx + ox;
+}
+
+// Unscaled input values of the two ends of a Dirichlet line: the boundary
+// value v, or the value of a Dirichlet node sitting at that end (the node is
+// applied right after the shell, so the solve sees the node's value there)
+__device__ __forceinline__ void end_values(const double* ends, int64_t fl, double v, double& v0,
+                                           double& v1)
+{
+    v0 = v;
+    v1 = v;
+    if (ends) {
+        const double e0 = ends[2 * fl], e1 = ends[2 * fl + 1];
+        if (!isnan(e0)) v0 = e0;
+        if (!isnan(e1)) v1 = e1;
+    }
+}
 
 // MODE 0: plain Thomas (3 flops per element: FMA + MUL forward, FMA back).
 // MODE 1: rescaled Thomas (one FMA forward, one FMA back).
@@ -171,18 +201,29 @@ __device__ __forceinline__ void sweep_one_line(const SweepArgs<T>& A, int64_t li
     double inv_other = 1.0;  // inverse of the other axes' scales (MODE 2)
     const double* own_in = nullptr;
     const double* own_out = nullptr;
+    // the two ends' input values (a Dirichlet node may sit at either end)
+    double v0 = v, v1 = v;
+    if (DIR == 0) end_values(A.ends, line, v, v0, v1);
+    double kl0 = v0, kl1 = v1;
     if (MODE >= 1) {
         own_in = A.sc_p + row + A.axis_off;
         own_out = A.sc_p1 + row + A.axis_off;
+        double sa, sb;
         if (AXIS == 0) {
-            kline = v * A.sc_p[row + A.off_y + oy] * A.sc_p[row + A.off_z + oz];
+            sa = A.sc_p[row + A.off_y + oy];
+            sb = A.sc_p[row + A.off_z + oz];
         } else if (AXIS == 1) {
-            kline = v * A.sc_p1[row + A.off_x + ox] * A.sc_p[row + A.off_z + oz];
+            sa = A.sc_p1[row + A.off_x + ox];
+            sb = A.sc_p[row + A.off_z + oz];
         } else {
-            kline = v * A.sc_p1[row + A.off_x + ox] * A.sc_p1[row + A.off_y + oy];
+            sa = A.sc_p1[row + A.off_x + ox];
+            sb = A.sc_p1[row + A.off_y + oy];
             if (MODE == 2)
                 inv_other = A.isc_p1[row + A.off_x + ox] * A.isc_p1[row + A.off_y + oy];
         }
+        kline = v * sa * sb;
+        kl0 = v0 * sa * sb;
+        kl1 = v1 * sa * sb;
     }
 
     if (dir && other_shell && DIR != 1) {
@@ -218,10 +259,10 @@ __device__ __forceinline__ void sweep_one_line(const SweepArgs<T>& A, int64_t li
     // on a Dirichlet shell line every input element is the shell value
     const bool all_in = dir && other_shell;
 
-    // Dirichlet prologue value of the two line ends
+    // Dirichlet prologue value of the two line ends (and of a shell line)
     auto end_in = [&](int k) -> T {
-        if (MODE == 0) return (T)v;
-        return (T)(kline * own_in[k]);
+        if (MODE == 0) return (T)(all_in ? v : (k == 0 ? v0 : v1));
+        return (T)((all_in ? kline : (k == 0 ? kl0 : kl1)) * own_in[k]);
     };
 
     // forward elimination (in place)
@@ -400,6 +441,7 @@ SweepArgs<T> make_args(Ctx* c, int axis, int p, const T* r, const T* cr,
     A.bc_value = c->d_bc_value;
     A.dims = c->dims;
     A.zfaces = c->zfaces();
+    A.ends = c->d_node_ends[axis];
     return A;
 }
 
@@ -544,6 +586,8 @@ bfvm_status launch_axis(Ctx* c, const SweepArgs<T>& A)
 // the rescaled FP64 form (MXY 1), the plain FP64 form and the FP32 form
 // (MXY 0).  Returns BFVM_ESTATE without launching when the context does not
 // qualify (the caller then launches the axes one by one).
+bfvm_status launch_nodes(Ctx* c, int p, bool renorm, int stage);
+
 template <typename T, int MXY>
 bfvm_status launch_step_fused(Ctx* c, int p, bool renorm, const T* r, const T* cr,
                               const T* cvec)
@@ -551,8 +595,10 @@ bfvm_status launch_step_fused(Ctx* c, int p, bool renorm, const T* r, const T* c
     // also runs the step's Dirichlet shell and cell sources (its epilogue)
     constexpr int G = persistent::Groups<T>::G;
     constexpr int NC = persistent::step_ncoef<T, MXY>();
+    // Dirichlet nodes: FP64 only, with the node tables built for this task list
+    const bool nodes = c->n_nodes > 0;
     if (!c->fused_step || c->sweep_kernel != 0 || !c->d_task_first || !c->d_sched ||
-        c->n_sub > 64 || c->dims != 3 || c->n_nodes > 0)
+        c->n_sub > 64 || c->dims != 3 || (nodes && (sizeof(T) != 8 || !c->d_node_task_first)))
         return BFVM_ESTATE;
     for (int a = 0; a < 3; ++a)
         if (!c->line_tables_ready[a]) return BFVM_ESTATE;
@@ -574,6 +620,11 @@ bfvm_status launch_step_fused(Ctx* c, int p, bool renorm, const T* r, const T* c
         // FP32: the per-axis launches measured faster at equal pair counts
         // (200^3 step 0.166 ms against 0.194 ms in one launch)
         if (sizeof(T) == 4) return BFVM_ESTATE;
+    }
+    // the node values the x sweep reads (the shell's part is the line ends)
+    if (nodes) {
+        const bfvm_status st = launch_nodes(c, p, renorm, 0);
+        if (st != BFVM_OK) return st;
     }
     KernelTimer timer(c, 4);
     SweepArgs<T> A[3];
@@ -604,8 +655,12 @@ bfvm_status launch_step_fused(Ctx* c, int p, bool renorm, const T* r, const T* c
     int64_t n_epi = 0;
     for (int s = 0; s < c->n_sub; ++s)
         n_epi += (c->bc_kind[s] == BFVM_BC_DIRICHLET ? persistent::epi_shell_chunks(c->nx, c->ny, c->nz) : 0) +
-                 persistent::epi_src_chunks(n_seg);
+                 (nodes ? c->node_chunks[s] : 0) + persistent::epi_src_chunks(n_seg);
     Q.n_epi_chunks = (int)n_epi;
+    Q.node_task_first = nodes ? c->d_node_task_first : nullptr;
+    Q.node_patch = nodes ? c->d_node_patch : nullptr;
+    Q.node_sfirst = nodes ? c->d_node_sfirst : nullptr;
+    Q.node_epi = nodes ? c->d_node_epi : nullptr;
     persistent::EpiArgs<T> E;
     E.field = reinterpret_cast<T*>(c->field);
     E.nx = c->nx;
@@ -626,8 +681,14 @@ bfvm_status launch_step_fused(Ctx* c, int p, bool renorm, const T* r, const T* c
     grid = std::max<int64_t>(grid, ceil_div(Q.n_epi_chunks, 8 * pairs));
     if (grid > c->sm_count) grid = c->sm_count;
     if (c->grid_limit > 0 && grid > c->grid_limit) grid = c->grid_limit;
-    auto kern = persistent::k_step_pair<T, MXY, MXY>;
-    if (MXY == 1 && renorm) kern = persistent::k_step_pair<T, MXY, 2 * MXY>;
+    auto kern = persistent::k_step_pair<T, MXY, MXY, false>;
+    if (MXY == 1 && renorm) kern = persistent::k_step_pair<T, MXY, 2 * MXY, false>;
+    if constexpr (sizeof(T) == 8) {
+        if (nodes) {
+            kern = persistent::k_step_pair<T, MXY, MXY, true>;
+            if (MXY == 1 && renorm) kern = persistent::k_step_pair<T, MXY, 2 * MXY, true>;
+        }
+    }
     BFVM_CUDA(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)smem));
     kern<<<(unsigned)grid, 64 * pairs, smem, c->stream>>>(A[0], A[1], A[2], S[0], S[1], S[2], Q,
@@ -792,6 +853,134 @@ bfvm_status build_line_tables(Ctx* c)
     const size_t nsched = 2 + 3 * (size_t)c->n_sub + 1 + (size_t)c->n_sub;
     BFVM_CUDA(c, cudaMalloc(&c->d_sched, sizeof(unsigned) * nsched));
     BFVM_CUDA(c, cudaMemset(c->d_sched, 0, sizeof(unsigned) * nsched));
+    return BFVM_OK;
+}
+
+// Dirichlet nodes as the sweeps see them.
+//
+// A node on a face of its substrate's Dirichlet shell (one coordinate at 0 or
+// n - 1 of its axis, the other two inside) is an end of the one line along
+// that axis that gets a solve: the solve must take the node's value there
+// instead of the boundary value (the node is applied right after the shell).
+// Such values go into a per-axis end table ([line][2], NaN where the end is
+// the boundary value).  Nodes on shell edges and corners lie on no solved line.
+//
+// For the one-launch step (sweep_step.cuh): every node goes into the
+// epilogue's list, by substrate (written once all of its substrate's sweeps
+// and shell are done, before its sources), and each node on a solved x or y
+// line into the patch list of the sweep task of that line (written after the
+// task's outputs, before its completion is published, so the next axis reads
+// the node's value).  The node values before the x sweep come from one
+// node-fill launch ahead of the step.
+bfvm_status build_node_tables(Ctx* c, const std::vector<int64_t>& vox,
+                              const std::vector<int32_t>& sub, const std::vector<double>& val,
+                              const std::vector<int64_t>& off)
+{
+    const int64_t m = (int64_t)val.size();
+    const int ext[3] = {c->nx, c->ny, c->nz};
+    std::vector<double> ends[3];
+    bool any_end[3] = {false, false, false};
+    auto coords = [&](int64_t v, int& x, int& y, int& z) {
+        x = (int)(v % c->nx);
+        y = (int)((v / c->nx) % c->ny);
+        z = (int)(v / ((int64_t)c->nx * c->ny));
+    };
+    for (int64_t i = 0; i < m; ++i) {
+        const int s = sub[i];
+        if (c->bc_kind[s] != BFVM_BC_DIRICHLET) continue;
+        int q[3];
+        coords(vox[i], q[0], q[1], q[2]);
+        for (int a = 0; a < 3; ++a) {
+            const int b1 = a == 0 ? 1 : 0, b2 = a == 2 ? 1 : 2;   // the other axes
+            auto inside = [&](int ax) { return q[ax] > 0 && q[ax] < ext[ax] - 1; };
+            if (!inside(b1) || !inside(b2)) continue;   // no solved line along a here
+            const bool lo = q[a] == 0, hi = q[a] == ext[a] - 1;
+            if (!lo && !hi) continue;                   // inside the line, not an end
+            if (ends[a].empty()) {
+                const int64_t lines = (int64_t)c->n_sub * ext[b1] * ext[b2];
+                ends[a].assign(2 * lines, (double)NAN);
+            }
+            int64_t fl;
+            if (a == 0) fl = ((int64_t)s * c->nz + q[2]) * c->ny + q[1];
+            else if (a == 1) fl = ((int64_t)s * c->nz + q[2]) * c->nx + q[0];
+            else fl = ((int64_t)s * c->ny + q[1]) * c->nx + q[0];
+            if (lo) ends[a][2 * fl] = val[i];
+            if (hi) ends[a][2 * fl + 1] = val[i];
+            any_end[a] = true;
+        }
+    }
+    for (int a = 0; a < 3; ++a) {
+        if (!any_end[a]) continue;
+        BFVM_CUDA(c, cudaMalloc(&c->d_node_ends[a], sizeof(double) * ends[a].size()));
+        BFVM_CUDA(c, cudaMemcpy(c->d_node_ends[a], ends[a].data(), sizeof(double) * ends[a].size(),
+                                cudaMemcpyHostToDevice));
+    }
+    if (c->n_tasks == 0 || !c->d_task_first) return BFVM_OK;   // no one-launch step
+    // task numbering of build_line_tables
+    std::vector<int64_t> tf(3 * c->n_sub + 1, 0);
+    int64_t t = 0;
+    for (int a = 0; a < 3; ++a)
+        for (int s = 0; s < c->n_sub; ++s) {
+            tf[a * c->n_sub + s] = t;
+            t += ceil_div(c->lines_first[a][s + 1] - c->lines_first[a][s], 32);
+        }
+    std::vector<std::pair<int64_t, NodePatch>> patches;
+    std::vector<std::vector<NodePatch>> by_sub(c->n_sub);
+    for (int64_t i = 0; i < m; ++i) {
+        const int s = sub[i];
+        NodePatch np{};
+        np.off = off[i];
+        np.v = val[i];
+        coords(vox[i], np.x, np.y, np.z);
+        by_sub[s].push_back(np);
+        const int q[3] = {np.x, np.y, np.z};
+        for (int a = 0; a < 2; ++a) {
+            // the line set of (a, s): coordinate lo_a + (t % cnt_a) of the fast
+            // other axis, lo_b + (t / cnt_a) of the slow one
+            const int fa = a == 0 ? q[1] : q[0];
+            const int fb = q[2];
+            const int lo_a = c->lines_lo_a[a][s], ca = c->lines_cnt_a[a][s];
+            const int lo_b = c->lines_lo_b[a][s];
+            const int64_t nl = c->lines_first[a][s + 1] - c->lines_first[a][s];
+            if (fa < lo_a || fa >= lo_a + ca || fb < lo_b) continue;
+            const int64_t tl = (int64_t)(fa - lo_a) + (int64_t)(fb - lo_b) * ca;
+            if (tl >= nl) continue;          // on a line without a solve
+            patches.push_back({tf[a * c->n_sub + s] + tl / 32, np});
+        }
+    }
+    std::stable_sort(patches.begin(), patches.end(),
+                     [](const std::pair<int64_t, NodePatch>& u,
+                        const std::pair<int64_t, NodePatch>& w) { return u.first < w.first; });
+    std::vector<int> first(c->n_tasks + 1, 0);
+    std::vector<NodePatch> flat(patches.size());
+    for (size_t i = 0; i < patches.size(); ++i) {
+        first[patches[i].first + 1] += 1;
+        flat[i] = patches[i].second;
+    }
+    for (int i = 0; i < c->n_tasks; ++i) first[i + 1] += first[i];
+    std::vector<int> sfirst(c->n_sub + 1, 0);
+    std::vector<NodePatch> epi;
+    c->node_chunks.assign(c->n_sub, 0);
+    for (int s = 0; s < c->n_sub; ++s) {
+        sfirst[s] = (int)epi.size();
+        epi.insert(epi.end(), by_sub[s].begin(), by_sub[s].end());
+        c->node_chunks[s] = (int)ceil_div((int64_t)by_sub[s].size(), persistent::kNodeChunk);
+    }
+    sfirst[c->n_sub] = (int)epi.size();
+    BFVM_CUDA(c, cudaMalloc(&c->d_node_task_first, sizeof(int) * first.size()));
+    BFVM_CUDA(c, cudaMemcpy(c->d_node_task_first, first.data(), sizeof(int) * first.size(),
+                            cudaMemcpyHostToDevice));
+    BFVM_CUDA(c, cudaMalloc(&c->d_node_patch, sizeof(NodePatch) * std::max<size_t>(flat.size(), 1)));
+    if (!flat.empty())
+        BFVM_CUDA(c, cudaMemcpy(c->d_node_patch, flat.data(), sizeof(NodePatch) * flat.size(),
+                                cudaMemcpyHostToDevice));
+    BFVM_CUDA(c, cudaMalloc(&c->d_node_sfirst, sizeof(int) * sfirst.size()));
+    BFVM_CUDA(c, cudaMemcpy(c->d_node_sfirst, sfirst.data(), sizeof(int) * sfirst.size(),
+                            cudaMemcpyHostToDevice));
+    BFVM_CUDA(c, cudaMalloc(&c->d_node_epi, sizeof(NodePatch) * std::max<size_t>(epi.size(), 1)));
+    if (!epi.empty())
+        BFVM_CUDA(c, cudaMemcpy(c->d_node_epi, epi.data(), sizeof(NodePatch) * epi.size(),
+                                cudaMemcpyHostToDevice));
     return BFVM_OK;
 }
 

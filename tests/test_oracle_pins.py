@@ -494,3 +494,33 @@ def test_node_on_shell_at_the_shell_value_changes_nothing():
     q = p.with_(nodes=(np.array([0, 5], dtype=np.int64), np.array([0, 0], dtype=np.int32),
                        np.array([38.0, 38.0])))
     np.testing.assert_array_equal(oracle.run(q, n_steps=4), oracle.run(p, n_steps=4))
+
+
+def test_nodes_on_dirichlet_faces_dense_lu():
+    """Nodes on every face, an edge and a corner of a Dirichlet substrate at
+    values other than the boundary's: the node projection follows the shell
+    projection, so the solve of the line a face node ends sees the node's
+    value there.  Against the dense solves, and the interior next to a face
+    node does depend on its value."""
+    nx, ny, nz = 5, 6, 4
+    p = inputs.make_problem(nx, ny, nz, n_sub=2, D=[1e5, 2e3], lam=[0.1, 0.02],
+                            bc_kind=[1, 0], bc_value=[38.0, 0.0], n_cells=4, U=[10.0, 1.0],
+                            S=[0.0, 3.0], rho_star=[1.0, 2.0], seed=23)
+
+    def v(x, y, z):
+        return x + nx * (y + ny * z)
+
+    faces = [v(0, 2, 1), v(nx - 1, 3, 2), v(2, 0, 2), v(1, ny - 1, 1), v(3, 2, 0),
+             v(2, 4, nz - 1), v(0, 0, 2), v(nx - 1, ny - 1, nz - 1)]
+    vox = np.array(faces + [v(2, 2, 2)], dtype=np.int64)
+    sub = np.zeros(len(vox), dtype=np.int32)
+    val = np.array([50.0, 20.0, 60.0, 10.0, 45.0, 30.0, 99.0, 5.0, 40.0])
+    q = p.with_(nodes=(vox, sub, val))
+    ref = _dense_run_nodes(q, 3)
+    got = oracle.run(q, n_steps=3)
+    np.testing.assert_allclose(got, ref, rtol=0, atol=1e-13 * np.abs(ref).max())
+    val2 = val.copy()
+    val2[0] = 38.0                        # the x = 0 face node at the boundary value
+    other = oracle.run(p.with_(nodes=(vox, sub, val2)), n_steps=1)
+    first = oracle.run(q, n_steps=1)
+    assert abs(first[0, 1, 2, 1] - other[0, 1, 2, 1]) > 1e-3   # its x line's neighbour

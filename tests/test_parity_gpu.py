@@ -471,3 +471,105 @@ def test_dirichlet_node_rules(bf):
     bf.bfvm_set_dirichlet_nodes(sim.handle, [], [], [])                      # removed again
     sim.record(2)
     sim.close()
+
+
+# -------------------------------- Dirichlet nodes on shell faces, in one launch
+def _with_face_nodes(p):
+    """Nodes where the shell and the sweeps meet them: on each face of the
+    Dirichlet substrate 0 (a line end of a solved line, at a value other
+    than the boundary's), on an edge and a corner, a short interior vessel,
+    on cells' voxels, on the zero-flux substrate 1's boundary and inside it,
+    and a repeat."""
+    nx, ny, nz = p.nx, p.ny, p.nz
+
+    def v(x, y, z):
+        return x + nx * (y + ny * z)
+
+    nodes = [
+        (v(0, ny // 3, nz // 2), 0, 50.0), (v(nx - 1, ny // 2, nz // 3), 0, 20.0),
+        (v(nx // 3, 0, nz // 2), 0, 60.0), (v(nx // 2, ny - 1, 1), 0, 10.0),
+        (v(nx // 4, ny // 4, 0), 0, 45.0), (v(nx // 2, ny // 3, nz - 1), 0, 30.0),
+        (v(0, 0, nz // 2), 0, 99.0), (v(nx - 1, ny - 1, nz - 1), 0, 5.0),
+        (v(0, ny // 2, nz // 4), 1, 7.0), (v(nx // 2, ny // 2, nz // 2), 1, 3.0),
+    ]
+    nodes += [(v(nx // 2, ny // 2, z), 0, 45.0) for z in range(2, nz - 2)]
+    for i in range(min(3, len(p.pos))):      # on cells' voxels, both substrates
+        nodes.append((oracle.cell_voxel(p, p.pos[i]), i % 2, 12.0 + i))
+    nodes.append((v(nx // 2, ny // 2, nz // 2), 1, 4.0))   # the later one holds
+    vox, sub, val = zip(*nodes)
+    return p.with_(nodes=(np.array(vox, dtype=np.int64), np.array(sub, dtype=np.int32),
+                          np.array(val, dtype=np.float64)))
+
+
+FACE_NODE_CASES = {
+    "ragged_37x45x50": lambda: _with_face_nodes(mixed(37, 45, 50)),
+    "cube_33": lambda: _with_face_nodes(mixed(33, 33, 33, n_cells=300, steps=9)),
+    "long_z_260": lambda: _with_face_nodes(mixed(9, 7, 260, n_cells=50, steps=3)),
+}
+
+
+@pytest.mark.parametrize("precision,variant,period,tol",
+                         [(64, 1, 0, TOL64), (64, 1, 3, TOL64), (64, 0, 0, TOL64),
+                          (32, None, 0, TOL32)])
+@pytest.mark.parametrize("fused", [1, 0])
+@pytest.mark.parametrize("case", sorted(FACE_NODE_CASES))
+def test_face_nodes_match_oracle(bf, case, fused, precision, variant, period, tol):
+    """Nodes on the Dirichlet shell's faces enter the solve of the line they
+    end with their own value; with option 8 at its default the FP64 forms
+    run the step as one launch plus the node fill ahead of it."""
+    p = FACE_NODE_CASES[case]()
+    ref = oracle.run(p)
+    sim = bf.Sim.from_problem(p, precision=precision)
+    if variant is not None:
+        sim.set_option(bf.OPT_VARIANT, variant)
+    if period:
+        sim.set_option(bf.OPT_PERIOD, period)
+    sim.set_option(bf.OPT_FUSED_STEP, fused)
+    sim.step(p.steps)
+    got = sim.get_density().double().cpu().numpy()
+    sim.close()
+    err = rel_inf(got, ref)
+    assert np.all(err <= tol), (case, fused, precision, variant, err)
+
+
+@pytest.mark.parametrize("opt,value", [("OPT_SWEEP_KERNEL", 1), ("OPT_SPLIT", 2)])
+def test_face_nodes_other_sweep_kernels(bf, opt, value):
+    """The one-warp-per-line sweeps and the split line solve take the node
+    values at line ends too (plain FP64 form, where the split solve runs)."""
+    p = FACE_NODE_CASES["ragged_37x45x50"]()
+    ref = oracle.run(p)
+    sim = bf.Sim.from_problem(p)
+    sim.set_option(bf.OPT_VARIANT, 0)
+    sim.set_option(getattr(bf, opt), value)
+    sim.step(p.steps)
+    got = sim.get_density().cpu().numpy()
+    sim.close()
+    assert np.all(rel_inf(got, ref) <= TOL64)
+
+
+@pytest.mark.parametrize("variant,period", [(1, 0), (1, 3), (0, 0)])
+@pytest.mark.parametrize("grid_limit", [0, 3])
+def test_nodes_one_launch_matches_per_axis_bitwise(bf, variant, period, grid_limit):
+    """With nodes the one-launch step (node fill, then one launch) gives the
+    per-axis launches' field bit for bit, in fewer launches; CTA caps make
+    the warp pairs walk many tasks, so node patches and the epilogue's node
+    chunks meet many interleavings."""
+    p = _with_face_nodes(mixed(37, 45, 50, steps=7))
+    outs, counts = [], []
+    for fused in (2, 0):
+        sim = bf.Sim.from_problem(p)
+        sim.set_option(bf.OPT_VARIANT, variant)
+        if period:
+            sim.set_option(bf.OPT_PERIOD, period)
+        sim.set_option(bf.OPT_FUSED_STEP, fused)
+        if grid_limit:
+            sim.set_option(bf.OPT_GRID_LIMIT, grid_limit)
+        n0 = sim.info()["launches"]
+        sim.step(p.steps)
+        sim.sync()
+        counts.append(sim.info()["launches"] - n0)
+        outs.append(sim.get_density().cpu().numpy())
+        sim.close()
+    assert counts[0] < counts[1]
+    np.testing.assert_array_equal(outs[0], outs[1])
+    assert np.all(rel_inf(outs[0], oracle.run(p)) <= TOL64)
