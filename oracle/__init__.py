@@ -106,6 +106,10 @@ def _load():
             lib.oracle_axis_solve_2d.restype = None
             lib.oracle_adjoint.argtypes = common + [ctypes.c_int] * 3 + [_dp] * 8
             lib.oracle_adjoint.restype = ctypes.c_int
+            lib.oracle_adjoint_ext.argtypes = ([ctypes.c_int] + common
+                                               + [ctypes.c_int64, _lp, _ip, _dp]
+                                               + [ctypes.c_int] * 3 + [_dp] * 8)
+            lib.oracle_adjoint_ext.restype = ctypes.c_int
             lib.oracle_max_threads.argtypes = []
             lib.oracle_max_threads.restype = ctypes.c_int
             _lib = lib
@@ -224,9 +228,27 @@ def adjoint(p, g_final, rho0=None, n_steps=None, checkpoint_every: int = 20,
     g0 = np.zeros_like(rho0)
     fin = np.zeros_like(rho0)
     args, keep = _common(p)
-    rc = lib.oracle_adjoint(*args, steps, int(checkpoint_every),
-                            int(n_threads or max_threads()), _d(rho0), _d(g_final),
-                            _d(dD), _d(dl), _d(dS), _d(dU), _d(g0), _d(fin))
+    tail = [steps, int(checkpoint_every), int(n_threads or max_threads()), _d(rho0),
+            _d(g_final), _d(dD), _d(dl), _d(dS), _d(dU), _d(g0), _d(fin)]
+    nodes = getattr(p, "nodes", None)
+    dims = int(getattr(p, "dims", 3))
+    if dims == 2 or (nodes is not None and len(nodes[0]) > 0):
+        # the 2-D variant, or Dirichlet nodes (oracle_adjoint_ext)
+        if nodes is None or len(nodes[0]) == 0:
+            vox = np.zeros(1, dtype=np.int64)
+            sub = np.zeros(1, dtype=np.int32)
+            val = np.zeros(1)
+            n_nodes = 0
+        else:
+            vox = np.ascontiguousarray(nodes[0], dtype=np.int64)
+            sub = np.ascontiguousarray(nodes[1], dtype=np.int32)
+            val = _f64(nodes[2])
+            n_nodes = len(vox)
+        rc = lib.oracle_adjoint_ext(dims, *args, ctypes.c_int64(n_nodes),
+                                    vox.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                    sub.ctypes.data_as(_ip), _d(val), *tail)
+    else:
+        rc = lib.oracle_adjoint(*args, *tail)
     if rc != 0:
         raise ValueError(f"oracle_adjoint failed ({rc})")
     del keep

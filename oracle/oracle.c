@@ -368,8 +368,11 @@ int oracle_run_nodes(int nx, int ny, int nz, double dx, double dt, int n_sub,
 /*    df/db = -f/(1+b);  a = w S rho*, b = w (S + U), w = dt V/V_vox.   */
 /*  - Dirichlet: the shell of a Dirichlet substrate no longer depends   */
 /*    on its input, so its adjoint is zeroed.                            */
+/*  - Dirichlet nodes (oracle_adjoint_ext): likewise, a node's adjoint  */
+/*    is zeroed after the shell's.                                       */
 /*  - axis solve y = A^{-1} x: A is symmetric, so g_x = A^{-1} g_y, and */
-/*    dL/dtheta -= <g_x, (dA/dtheta) y> with dA/dlambda = dt/3 I and     */
+/*    dL/dtheta -= <g_x, (dA/dtheta) y> with dA/dlambda = dt/3 I (dt/2   */
+/*    in the 2-D variant, oracle_adjoint_ext with dims 2) and            */
 /*    dA/dD = dt/dx^2 L, L the zero-flux line Laplacian (1 at both ends, */
 /*    2 inside, -1 off the diagonal; 0 for a line of length 1).          */
 /* The forward is recomputed from the initial field; the state at the   */
@@ -411,6 +414,67 @@ static double block_dot(int64_t n, const double* a, const double* b)
     return acc;
 }
 
+/* One step of the 3-D step with Dirichlet nodes (the step of
+ * oracle_run_nodes; none: oracle_step's) or of the 2-D variant (dims 2, the
+ * step of oracle_run_2d), in place. */
+static void step_any(int dims, int nx, int ny, int nz, double dx, double dt, int n_sub,
+                     const double* D, const double* lambda, const int* bc_kind,
+                     const double* bc_value, int64_t n_cells, const double* pos,
+                     const double* vol, const double* S, const double* U,
+                     const double* rho_star, int64_t n_nodes, const int64_t* vox,
+                     const int* sub, const double* val, double* rho, int n_threads)
+{
+    if (dims == 2) {
+        oracle_apply_dirichlet_2d(nx, ny, n_sub, bc_kind, bc_value, rho);
+        for (int axis = 0; axis < 2; ++axis) {
+            oracle_axis_solve_2d(axis, nx, ny, n_sub, dx, dt, D, lambda, rho);
+            oracle_apply_dirichlet_2d(nx, ny, n_sub, bc_kind, bc_value, rho);
+        }
+    } else {
+        oracle_apply_dirichlet(nx, ny, nz, n_sub, bc_kind, bc_value, rho);
+        oracle_apply_nodes(nx, ny, nz, n_nodes, vox, sub, val, rho);
+        for (int axis = 0; axis < 3; ++axis) {
+            oracle_axis_solve(axis, nx, ny, nz, n_sub, dx, dt, D, lambda, rho, n_threads);
+            oracle_apply_dirichlet(nx, ny, nz, n_sub, bc_kind, bc_value, rho);
+            oracle_apply_nodes(nx, ny, nz, n_nodes, vox, sub, val, rho);
+        }
+    }
+    oracle_apply_sources(nx, ny, nz, n_sub, dx, dt, n_cells, pos, vol, S, U, rho_star, rho);
+}
+
+/* The 2-D shell (the four edges x = 0, nx-1, y = 0, ny-1) of a Dirichlet
+ * substrate no longer depends on its input: its adjoint is zeroed. */
+static void project_dirichlet_adjoint_2d(int nx, int ny, int n_sub, const int* bc_kind,
+                                         double* g)
+{
+    for (int s = 0; s < n_sub; ++s) {
+        if (bc_kind[s] != 1) continue;
+        for (int y = 0; y < ny; ++y)
+            for (int x = 0; x < nx; ++x)
+                if (x == 0 || x == nx - 1 || y == 0 || y == ny - 1)
+                    g[((int64_t)s * ny + y) * nx + x] = 0.0;
+    }
+}
+
+/* A Dirichlet node's value no longer depends on its input: its adjoint
+ * is zeroed. */
+static void project_nodes_adjoint(int nx, int ny, int nz, int64_t n_nodes, const int64_t* vox,
+                                  const int* sub, double* g)
+{
+    const int64_t n_vox = (int64_t)nx * ny * nz;
+    for (int64_t i = 0; i < n_nodes; ++i) g[(int64_t)sub[i] * n_vox + vox[i]] = 0.0;
+}
+
+static int adjoint_any(int dims, int nx, int ny, int nz, double dx, double dt, int n_sub,
+                       const double* D, const double* lambda, const int* bc_kind,
+                       const double* bc_value, int64_t n_cells, const double* pos,
+                       const double* vol, const double* S, const double* U,
+                       const double* rho_star, int64_t n_nodes, const int64_t* vox,
+                       const int* sub, const double* val, int n_steps, int checkpoint_every,
+                       int n_threads, const double* rho0, const double* g_final,
+                       double* dD, double* dlambda, double* dS, double* dU,
+                       double* g0, double* rho_final);
+
 int oracle_adjoint(int nx, int ny, int nz, double dx, double dt, int n_sub,
                    const double* D, const double* lambda, const int* bc_kind,
                    const double* bc_value, int64_t n_cells, const double* pos,
@@ -419,6 +483,48 @@ int oracle_adjoint(int nx, int ny, int nz, double dx, double dt, int n_sub,
                    int n_threads, const double* rho0, const double* g_final,
                    double* dD, double* dlambda, double* dS, double* dU,
                    double* g0, double* rho_final)
+{
+    return adjoint_any(3, nx, ny, nz, dx, dt, n_sub, D, lambda, bc_kind, bc_value, n_cells,
+                       pos, vol, S, U, rho_star, 0, NULL, NULL, NULL, n_steps,
+                       checkpoint_every, n_threads, rho0, g_final, dD, dlambda, dS, dU, g0,
+                       rho_final);
+}
+
+/* The adjoint of the 2-D variant (dims 2: nz = 1, x- and y-solves with
+ * decay share lambda dt / 2, the four-edge shell) or of the 3-D step with
+ * Dirichlet nodes (dims 3; each node projection's adjoint zeroes the node's
+ * entry, right after the shell's).  Arguments as oracle_adjoint, with the
+ * nodes as in oracle_run_nodes (none for dims 2). */
+int oracle_adjoint_ext(int dims, int nx, int ny, int nz, double dx, double dt, int n_sub,
+                       const double* D, const double* lambda, const int* bc_kind,
+                       const double* bc_value, int64_t n_cells, const double* pos,
+                       const double* vol, const double* S, const double* U,
+                       const double* rho_star, int64_t n_nodes, const int64_t* vox,
+                       const int* sub, const double* val, int n_steps, int checkpoint_every,
+                       int n_threads, const double* rho0, const double* g_final,
+                       double* dD, double* dlambda, double* dS, double* dU,
+                       double* g0, double* rho_final)
+{
+    if (dims != 2 && dims != 3) return 1;
+    if (dims == 2 && (nz != 1 || n_nodes != 0)) return 1;
+    for (int64_t i = 0; i < n_nodes; ++i)
+        if (vox[i] < 0 || vox[i] >= (int64_t)nx * ny * nz || sub[i] < 0 || sub[i] >= n_sub)
+            return 2;
+    return adjoint_any(dims, nx, ny, nz, dx, dt, n_sub, D, lambda, bc_kind, bc_value, n_cells,
+                       pos, vol, S, U, rho_star, n_nodes, vox, sub, val, n_steps,
+                       checkpoint_every, n_threads, rho0, g_final, dD, dlambda, dS, dU, g0,
+                       rho_final);
+}
+
+static int adjoint_any(int dims, int nx, int ny, int nz, double dx, double dt, int n_sub,
+                       const double* D, const double* lambda, const int* bc_kind,
+                       const double* bc_value, int64_t n_cells, const double* pos,
+                       const double* vol, const double* S, const double* U,
+                       const double* rho_star, int64_t n_nodes, const int64_t* vox,
+                       const int* sub, const double* val, int n_steps, int checkpoint_every,
+                       int n_threads, const double* rho0, const double* g_final,
+                       double* dD, double* dlambda, double* dS, double* dU,
+                       double* g0, double* rho_final)
 {
     if (nx < 1 || ny < 1 || nz < 1 || n_sub < 1 || n_steps < 0) return 1;
     if (checkpoint_every < 1) checkpoint_every = 1;
@@ -443,8 +549,8 @@ int oracle_adjoint(int nx, int ny, int nz, double dx, double dt, int n_sub,
     for (int t = 0; t < n_steps; ++t) {
         if (t % checkpoint_every == 0)
             memcpy(ckpt + (size_t)(t / checkpoint_every) * n_field, cur, fbytes);
-        oracle_step(nx, ny, nz, dx, dt, n_sub, D, lambda, bc_kind, bc_value,
-                    n_cells, pos, vol, S, U, rho_star, cur, n_threads);
+        step_any(dims, nx, ny, nz, dx, dt, n_sub, D, lambda, bc_kind, bc_value, n_cells, pos,
+                 vol, S, U, rho_star, n_nodes, vox, sub, val, cur, n_threads);
     }
     if (rho_final) memcpy(rho_final, cur, fbytes);
 
@@ -465,17 +571,30 @@ int oracle_adjoint(int nx, int ny, int nz, double dx, double dt, int n_sub,
         memcpy(cur, ckpt + (size_t)k * n_field, fbytes);
         for (int t = t0; t < t1; ++t) {
             memcpy(seg + (size_t)(t - t0) * n_field, cur, fbytes);
-            oracle_step(nx, ny, nz, dx, dt, n_sub, D, lambda, bc_kind, bc_value,
-                        n_cells, pos, vol, S, U, rho_star, cur, n_threads);
+            step_any(dims, nx, ny, nz, dx, dt, n_sub, D, lambda, bc_kind, bc_value, n_cells,
+                     pos, vol, S, U, rho_star, n_nodes, vox, sub, val, cur, n_threads);
         }
         for (int t = t1 - 1; t >= t0; --t) {
             /* recompute the inner states of step t */
             memcpy(tmp, seg + (size_t)(t - t0) * n_field, fbytes);
-            oracle_apply_dirichlet(nx, ny, nz, n_sub, bc_kind, bc_value, tmp);
-            for (int a = 0; a < 3; ++a) {
-                oracle_axis_solve(a, nx, ny, nz, n_sub, dx, dt, D, lambda, tmp, n_threads);
-                memcpy(st_solve[a], tmp, fbytes);
+            if (dims == 2) {
+                oracle_apply_dirichlet_2d(nx, ny, n_sub, bc_kind, bc_value, tmp);
+            } else {
                 oracle_apply_dirichlet(nx, ny, nz, n_sub, bc_kind, bc_value, tmp);
+                oracle_apply_nodes(nx, ny, nz, n_nodes, vox, sub, val, tmp);
+            }
+            for (int a = 0; a < dims; ++a) {
+                if (dims == 2)
+                    oracle_axis_solve_2d(a, nx, ny, n_sub, dx, dt, D, lambda, tmp);
+                else
+                    oracle_axis_solve(a, nx, ny, nz, n_sub, dx, dt, D, lambda, tmp, n_threads);
+                memcpy(st_solve[a], tmp, fbytes);
+                if (dims == 2) {
+                    oracle_apply_dirichlet_2d(nx, ny, n_sub, bc_kind, bc_value, tmp);
+                } else {
+                    oracle_apply_dirichlet(nx, ny, nz, n_sub, bc_kind, bc_value, tmp);
+                    oracle_apply_nodes(nx, ny, nz, n_nodes, vox, sub, val, tmp);
+                }
             }
             memcpy(st_pre_src, tmp, fbytes);
             /* forward through the sources, remembering each cell's input */
@@ -504,18 +623,30 @@ int oracle_adjoint(int nx, int ny, int nz, double dx, double dt, int n_sub,
                     *gv = *gv / (1.0 + b);
                 }
             }
-            /* adjoint of z, y, x solves, each preceded by its Dirichlet */
-            for (int a = 2; a >= 0; --a) {
-                project_dirichlet_adjoint(nx, ny, nz, n_sub, bc_kind, g);
-                oracle_axis_solve(a, nx, ny, nz, n_sub, dx, dt, D, lambda, g, n_threads);
+            /* adjoint of the z, y, x solves (y, x in 2-D), each preceded by
+             * its Dirichlet (and nodes); each axis takes lambda dt / dims */
+            for (int a = dims - 1; a >= 0; --a) {
+                if (dims == 2) {
+                    project_dirichlet_adjoint_2d(nx, ny, n_sub, bc_kind, g);
+                    oracle_axis_solve_2d(a, nx, ny, n_sub, dx, dt, D, lambda, g);
+                } else {
+                    project_dirichlet_adjoint(nx, ny, nz, n_sub, bc_kind, g);
+                    project_nodes_adjoint(nx, ny, nz, n_nodes, vox, sub, g);
+                    oracle_axis_solve(a, nx, ny, nz, n_sub, dx, dt, D, lambda, g, n_threads);
+                }
                 for (int s = 0; s < n_sub; ++s) {
                     const double* gs = g + (int64_t)s * n_vox;
                     const double* ys = st_solve[a] + (int64_t)s * n_vox;
-                    dlambda[s] -= (dt / 3.0) * block_dot(n_vox, gs, ys);
+                    dlambda[s] -= (dt / (double)dims) * block_dot(n_vox, gs, ys);
                     dD[s] -= (dt / (dx * dx)) * axis_laplacian_dot(a, nx, ny, nz, gs, ys);
                 }
             }
-            project_dirichlet_adjoint(nx, ny, nz, n_sub, bc_kind, g);
+            if (dims == 2) {
+                project_dirichlet_adjoint_2d(nx, ny, n_sub, bc_kind, g);
+            } else {
+                project_dirichlet_adjoint(nx, ny, nz, n_sub, bc_kind, g);
+                project_nodes_adjoint(nx, ny, nz, n_nodes, vox, sub, g);
+            }
         }
     }
     if (g0) memcpy(g0, g, fbytes);

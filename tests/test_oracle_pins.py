@@ -524,3 +524,94 @@ def test_nodes_on_dirichlet_faces_dense_lu():
     other = oracle.run(p.with_(nodes=(vox, sub, val2)), n_steps=1)
     first = oracle.run(q, n_steps=1)
     assert abs(first[0, 1, 2, 1] - other[0, 1, 2, 1]) > 1e-3   # its x line's neighbour
+
+
+# ------------------------------- adjoint of the 2-D variant and of Dirichlet nodes
+def _adjoint_ext_problems():
+    """A 2-D problem and a 3-D problem with Dirichlet nodes (interior, on a
+    Dirichlet face, on a cell's voxel, on the zero-flux substrate)."""
+    p2 = inputs.make_problem(7, 6, 1, n_sub=2, D=[2e4, 8e2], lam=[0.2, 0.05],
+                             bc_kind=[1, 0], bc_value=[38.0, 0.0], n_cells=7,
+                             U=[10.0, 2.0], S=[1.0, 6.0], rho_star=[38.0, 3.0],
+                             seed=6, steps=5, dt=0.02, dims=2)
+    p3 = _small_adjoint_problem()
+    nx, ny = p3.nx, p3.ny
+
+    def v(x, y, z):
+        return x + nx * (y + ny * z)
+
+    vox = [v(2, 2, 1), v(0, 2, 2), v(3, 0, 1), oracle.cell_voxel(p3, p3.pos[0]), v(1, 1, 1)]
+    sub = [0, 0, 0, 1, 1]
+    val = [45.0, 50.0, 20.0, 4.0, 2.5]
+    p3 = p3.with_(nodes=(np.array(vox, dtype=np.int64), np.array(sub, dtype=np.int32),
+                         np.array(val)))
+    return {"2d": p2, "nodes": p3}
+
+
+@pytest.mark.parametrize("kind", ["2d", "nodes"])
+def test_adjoint_ext_field_gradient_dot_product(kind):
+    """The 2-D step and the step with nodes are affine in rho as well:
+    <dL/drho0, v> = <w, run(rho0 + v) - run(rho0)> for L = <w, rho_final>."""
+    p = _adjoint_ext_problems()[kind]
+    rng = np.random.default_rng(12)
+    w = rng.standard_normal(p.rho0.shape)
+    v = rng.standard_normal(p.rho0.shape)
+    out = oracle.adjoint(p, w, checkpoint_every=2)
+    lhs = np.vdot(out["g0"], v)
+    rhs = np.vdot(w, oracle.run(p, rho0=p.rho0 + v) - oracle.run(p))
+    assert lhs == pytest.approx(rhs, rel=1e-10)
+    np.testing.assert_array_equal(out["rho_final"], oracle.run(p))
+    if kind == "nodes":   # a node's value does not depend on the initial field
+        n_vox = p.nx * p.ny * p.nz
+        vox, sub, _ = p.nodes
+        g0 = out["g0"].reshape(p.n_sub, n_vox)
+        assert np.all(g0[sub, vox] == 0.0)
+
+
+@pytest.mark.parametrize("kind", ["2d", "nodes"])
+def test_adjoint_ext_parameter_gradients_match_central_differences(kind):
+    p = _adjoint_ext_problems()[kind]
+    rng = np.random.default_rng(14)
+    target = p.rho0 * 0.5 + rng.uniform(0, 1, p.rho0.shape)
+
+    def loss(q):
+        return float(((oracle.run(q) - target) ** 2).sum())
+
+    g = 2.0 * (oracle.run(p) - target)
+    out = oracle.adjoint(p, g, checkpoint_every=3)
+    h_rel = 1e-5
+    for s in range(p.n_sub):
+        for key, attr in (("dD", "D"), ("dlambda", "lam")):
+            base = getattr(p, attr)
+
+            def make(f, s=s, attr=attr, base=base):
+                val = base.copy()
+                val[s] *= f
+                return p.with_(**{attr: val})
+            est = (loss(make(1 + h_rel)) - loss(make(1 - h_rel))) / (2 * h_rel * base[s])
+            assert out[key][s] == pytest.approx(est, rel=2e-6), (kind, key, s)
+    for i in (0, 3, 6):
+        for s in range(p.n_sub):
+            for key, attr in (("dS", "S"), ("dU", "U")):
+                base = getattr(p, attr)
+                h = 1e-4 * max(abs(base[i, s]), 1e-2)
+
+                def mk(delta, i=i, s=s, attr=attr, base=base):
+                    val = base.copy()
+                    val[i, s] += delta
+                    return p.with_(**{attr: val})
+                est = (loss(mk(h)) - loss(mk(-h))) / (2 * h)
+                assert out[key][i, s] == pytest.approx(est, rel=1e-6, abs=1e-9), (kind, key, i, s)
+
+
+def test_adjoint_ext_without_nodes_is_the_3d_adjoint():
+    """oracle_adjoint_ext with dims 3 and no nodes gives oracle_adjoint's bits."""
+    p = _small_adjoint_problem()
+    rng = np.random.default_rng(3)
+    w = rng.standard_normal(p.rho0.shape)
+    a = oracle.adjoint(p, w, checkpoint_every=2)
+    q = p.with_(nodes=(np.array([0], dtype=np.int64), np.array([0], dtype=np.int32),
+                       np.array([38.0])))    # a node on the shell at the shell value
+    b = oracle.adjoint(q, w, checkpoint_every=2)
+    for k in ("dD", "dlambda", "dS", "dU", "g0", "rho_final"):
+        np.testing.assert_array_equal(a[k], b[k])
