@@ -37,7 +37,10 @@ MUTANTS = [
     ("adjoint: sign of the diffusion gradient",
      "dD[s] -= (dt / (dx * dx))", "dD[s] += (dt / (dx * dx))"),
     ("adjoint: decay gradient without the LOD share",
-     "dlambda[s] -= (dt / 3.0)", "dlambda[s] -= dt"),
+     "dlambda[s] -= (dt / (double)dims)", "dlambda[s] -= dt"),
+    ("adjoint: a node's entry is not zeroed",
+     "for (int64_t i = 0; i < n_nodes; ++i) g[(int64_t)sub[i] * n_vox + vox[i]] = 0.0;",
+     "for (int64_t i = 0; i < n_nodes; ++i) g[(int64_t)sub[i] * n_vox + vox[i]] *= 1.0;"),
 ]
 
 
