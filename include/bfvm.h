@@ -144,8 +144,8 @@ bfvm_status bfvm_set_cells(bfvm_ctx* ctx, int64_t n_cells, const double* pos,
  * nodes is one node-fill launch plus option 8's one launch (node values
  * written after the x and y tasks that solve their lines and at the end of
  * the step); FP32 runs it one launch per axis with node fills between them.
- * A context with nodes cannot record for the adjoint or join a batch
- * (BFVM_ESTATE).  Resets any recorded forward run.
+ * A context with nodes cannot join a batch (BFVM_ESTATE).  Resets any
+ * recorded forward run.
  */
 bfvm_status bfvm_set_dirichlet_nodes(bfvm_ctx* ctx, int64_t n_nodes, const int64_t* voxel,
                                      const int32_t* substrate, const double* value,
@@ -201,9 +201,11 @@ bfvm_status bfvm_record(bfvm_ctx* ctx, int32_t checkpoint_every);
  *                  field before the call
  * Every segment of k steps is replayed from its checkpoint; the adjoint of
  * each step runs the sources' adjoint, then the z, y, x solves (the line
- * matrices are symmetric), each after zeroing the Dirichlet shell's
- * adjoint.  Only FP64 contexts.  BFVM_ESTATE if nothing was recorded.
- * Output pointers follow on_device like the input.
+ * matrices are symmetric), each after zeroing the adjoint of the Dirichlet
+ * shell and of the Dirichlet nodes (a projection onto a fixed value does
+ * not depend on its input).  The 2-D variant runs the y and x solves, each
+ * with decay share lambda dt / 2.  Only FP64 contexts.  BFVM_ESTATE if
+ * nothing was recorded.  Output pointers follow on_device like the input.
  */
 bfvm_status bfvm_backward(bfvm_ctx* ctx, const double* dL_drho_final,
                           int32_t checkpoint_every, double* dD, double* dlambda,
@@ -258,8 +260,8 @@ bfvm_status bfvm_get_info(const bfvm_ctx* ctx, int64_t* info);
  *          decay share lambda dt / 2; the Dirichlet shell is the outer layer
  *          of the four edges (the z layer is not a boundary); sources as in
  *          3-D with V_vox = dx^3.  Needs nz == 1; FP64 then runs the plain
- *          Thomas form (option 1 = 0).  2-D contexts cannot record for the
- *          adjoint or join a batch (BFVM_ESTATE).
+ *          Thomas form (option 1 = 0).  2-D contexts cannot join a batch
+ *          (BFVM_ESTATE); dims cannot change while recording.
  *   key 11 split line solve of the plain form (the FP32 form, FP64 with
  *          key 1 = 0, and the 2-D variant): each line cut into segments
  *          solved in parallel, joined through the affine form of the two

@@ -56,11 +56,12 @@ __global__ void k_pitched_to_dense(const double* __restrict__ src, double* __res
 
 // out = in with the Dirichlet shell set to `value` (set = true) or zeroed;
 // out2 (may be null) receives the same values.  One thread per voxel of the
-// pitched field; n_sub nz ny nx < 2^32 (32-bit index arithmetic).
+// pitched field; n_sub nz ny nx < 2^32 (32-bit index arithmetic).  dims 2:
+// the shell is the four edges (the single z layer is not a boundary).
 __global__ void k_shell(const double* __restrict__ in, double* __restrict__ out,
                         double* __restrict__ out2, int nx, int ny, int nz, int n_sub,
                         int64_t pitch, const int32_t* __restrict__ kind,
-                        const double* __restrict__ value, bool set)
+                        const double* __restrict__ value, bool set, int dims)
 {
     const uint32_t n = (uint32_t)n_sub * nz * ny * nx;
     const uint32_t e = blockIdx.x * blockDim.x + threadIdx.x;
@@ -75,10 +76,33 @@ __global__ void k_shell(const double* __restrict__ in, double* __restrict__ out,
     const int64_t o = (int64_t)r * pitch + x;
     double v = in[o];
     if (kind[s] == BFVM_BC_DIRICHLET &&
-        (x == 0 || x == nx - 1 || y == 0 || y == ny - 1 || z == 0 || z == nz - 1))
+        (x == 0 || x == nx - 1 || y == 0 || y == ny - 1 ||
+         (dims == 3 && (z == 0 || z == nz - 1))))
         v = set ? value[s] : 0.0;
     out[o] = v;
     if (out2) out2[o] = v;
+}
+
+// Dirichlet nodes on a pitched buffer f: each node entry is kept in keep
+// (when not null), then set to the node's value, or to zero when val is null
+// (the node projection and its adjoint).  One thread per node.
+__global__ void k_node_set(double* __restrict__ f, int64_t n, const int64_t* __restrict__ off,
+                           const double* __restrict__ val, double* __restrict__ keep)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int64_t o = off[i];
+    if (keep) keep[i] = f[o];
+    f[o] = val ? val[i] : 0.0;
+}
+
+// the node entries of f back from keep
+__global__ void k_node_restore(double* __restrict__ f, int64_t n,
+                               const int64_t* __restrict__ off, const double* __restrict__ keep)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    f[off[i]] = keep[i];
 }
 
 // forward composed maps, in place: rho <- alpha rho + beta
@@ -130,21 +154,22 @@ __global__ void k_sources_adjoint(double* __restrict__ g, const double* __restri
     g[o] = gr;
 }
 
-// The parameter terms of one adjoint step for substrate s, all three axes
-// in one pass: for axis a, <g_a, v_a> and <g_a, L_a v_a>, with g_a the
+// The parameter terms of one adjoint step for substrate s, all `dims` axes
+// (3, or 2 for the 2-D variant: x and y) in one pass: for axis a,
+// <g_a, v_a> and <g_a, L_a v_a>, with g_a the
 // adjoint after the solve of axis a (gz, gy, gx) and v_a that axis' raw
 // forward solve output (vx, vy, vz), L_a the zero-flux line Laplacian along
 // a.  Per-block partial sums in a fixed order; the last block to finish (a
 // completion counter) adds the partials in block order and applies, for
-// axes z, y, x in turn, dlambda[s] -= dt/3 * <g, v> and dD[s] -= dt/dx^2 *
-// <g, L v>, then resets the counter.  The result is the same bits on every
-// run.
+// axes z, y, x in turn, dlambda[s] -= dt/dims * <g, v> and dD[s] -= dt/dx^2
+// * <g, L v>, then resets the counter.  The result is the same bits on
+// every run.
 __global__ void k_param_dots(const double* __restrict__ gx, const double* __restrict__ gy,
                              const double* __restrict__ gz, const double* __restrict__ vx,
                              const double* __restrict__ vy, const double* __restrict__ vz, int s,
                              int nx, int ny, int nz, int64_t pitch, double* __restrict__ partial,
                              unsigned* __restrict__ counter, double dt, double dx, double* dD,
-                             double* dl)
+                             double* dl, int dims)
 {
     __shared__ double sh[6][kRedThreads];
     __shared__ bool last;
@@ -173,6 +198,7 @@ __global__ void k_param_dots(const double* __restrict__ gx, const double* __rest
         const int ext[3] = {nx, ny, nz};
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
+            if (a >= dims) break;
             const double* V = Vv[a] + o;
             const double* Gg = G[a] + o;
             double v[5], g[5];
@@ -259,8 +285,8 @@ __global__ void k_param_dots(const double* __restrict__ gx, const double* __rest
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        for (int a = 2; a >= 0; --a) {
-            dl[s] -= (dt / 3.0) * sh[2 * a][0];
+        for (int a = dims - 1; a >= 0; --a) {
+            dl[s] -= (dt / (double)dims) * sh[2 * a][0];
             dD[s] -= (dt / (dx * dx)) * sh[2 * a + 1][0];
         }
         *counter = 0u;
@@ -325,6 +351,27 @@ bfvm_status run_backward(Ctx* c, const double* g_final, double* dD, double* dl,
     c->launches += 1;
 
     auto V = [&](int t, int which) { return seg + ((int64_t)t * 4 + which) * nf; };
+    // the 2-D variant sweeps x and y only; Dirichlet nodes are projected
+    // like the shell (set in the replay, their adjoint zeroed)
+    const int dims = c->dims;
+    const int last = dims - 1;
+    const int64_t nn = c->n_nodes;
+    const bool nodes = nn > 0;
+    const unsigned gn = (unsigned)ceil_div(nn > 0 ? nn : 1, 256);
+    double* keep = nullptr;   // a buffer's node entries, kept around one solve
+    if (nodes && (rc = alloc(nn, &keep)) != BFVM_OK) { release(); return rc; }
+    // a projection (shell or nodes) makes the field before the sources
+    // differ from the last raw solve: it is then kept apart
+    const bool proj = any_dir || nodes;
+    auto node_set = [&](double* f, const double* val, double* kp) {
+        k_node_set<<<gn, 256, 0, c->stream>>>(f, nn, c->d_node_off, val, kp);
+        c->launches += 1;
+    };
+    auto node_restore = [&](double* f) {
+        k_node_restore<<<gn, 256, 0, c->stream>>>(f, nn, c->d_node_off, keep);
+        c->launches += 1;
+    };
+    double* ga[3] = {g, gy, gz};   // the adjoint after the solve of each axis
     // One segment of len steps from its checkpoint (already in `cur`): the
     // replay that keeps each step's raw solve outputs and pre-source field,
     // then the adjoint steps in reverse.  Every launch reads and writes the
@@ -333,22 +380,32 @@ bfvm_status run_backward(Ctx* c, const double* g_final, double* dD, double* dl,
     auto segment = [&](int len) -> bfvm_status {
         bfvm_status r = BFVM_OK;
         for (int j = 0; j < len; ++j) {
+            // the solves apply the shell to their input themselves; the
+            // nodes are set in it around each solve (the raw outputs stay)
+            if (nodes) node_set(cur, c->d_node_val, nullptr);
             if ((r = launch_sweep_plain64(c, 0, cur, V(j, 0), 1)) != BFVM_OK) return r;
-            if ((r = launch_sweep_plain64(c, 1, V(j, 0), V(j, 1), 1)) != BFVM_OK) return r;
-            // without a Dirichlet shell the z solve also writes the next
-            // step's input (cur) itself
-            if ((r = launch_sweep_plain64(c, 2, V(j, 1), V(j, 2), 1, any_dir ? nullptr : cur)) !=
-                BFVM_OK)
-                return r;
-            if (any_dir || !c->dual_done) {
-                // the field before the sources: P(v3) (kept for the sources'
-                // adjoint when a Dirichlet shell makes it differ from v3), and
-                // the next step's input
-                k_shell<<<gd, 256, 0, c->stream>>>(V(j, 2), any_dir ? V(j, 3) : cur,
-                                                   any_dir ? cur : nullptr, c->nx, c->ny, c->nz,
+            for (int a = 1; a <= last; ++a) {
+                if (nodes) node_set(V(j, a - 1), c->d_node_val, keep);
+                // without a projection the last solve also writes the next
+                // step's input (cur) itself
+                r = launch_sweep_plain64(c, a, V(j, a - 1), V(j, a), 1,
+                                         (a == last && !proj) ? cur : nullptr);
+                if (r != BFVM_OK) return r;
+                if (nodes) node_restore(V(j, a - 1));
+            }
+            if (proj || !c->dual_done) {
+                // the field before the sources: P(v_last) (kept for the
+                // sources' adjoint when a projection makes it differ from
+                // v_last), and the next step's input
+                k_shell<<<gd, 256, 0, c->stream>>>(V(j, last), proj ? V(j, 3) : cur,
+                                                   proj ? cur : nullptr, c->nx, c->ny, c->nz,
                                                    n_sub, c->pitch, c->d_bc_kind, c->d_bc_value,
-                                                   true);
+                                                   true, dims);
                 c->launches += 1;
+                if (nodes) {
+                    node_set(V(j, 3), c->d_node_val, nullptr);
+                    node_set(cur, c->d_node_val, nullptr);
+                }
             }
             if (S.n_entries > 0) {
                 k_apply_maps<<<(unsigned)ceil_div(S.n_entries, 256), 256, 0, c->stream>>>(
@@ -359,24 +416,33 @@ bfvm_status run_backward(Ctx* c, const double* g_final, double* dD, double* dl,
         for (int j = len - 1; j >= 0; --j) {
             if (S.n_entries > 0) {
                 k_sources_adjoint<<<(unsigned)ceil_div(S.n_seg * n_sub, 128), 128, 0, c->stream>>>(
-                    g, any_dir ? V(j, 3) : V(j, 2), S.n_seg, n_sub, S.seg_start, S.off,
+                    g, proj ? V(j, 3) : V(j, last), S.n_seg, n_sub, S.seg_start, S.off,
                     S.cell_sorted, S.ca, S.cb, S.cw, S.crs, pre, dS, dU);
                 c->launches += 1;
             }
-            if ((r = launch_sweep_plain64(c, 2, g, gz, 2)) != BFVM_OK) return r;
-            if ((r = launch_sweep_plain64(c, 1, gz, gy, 2)) != BFVM_OK) return r;
-            if ((r = launch_sweep_plain64(c, 0, gy, g, 2)) != BFVM_OK) return r;
+            // solves of the last axis down to x, each preceded by P' (the
+            // solve zeroes the shell of its input itself; the node entries
+            // are zeroed around it, the dots need the unprojected adjoint)
+            if (nodes) node_set(g, nullptr, nullptr);
+            for (int a = last; a >= 0; --a) {
+                double* in = a == last ? g : ga[a + 1];
+                if (nodes && a < last) node_set(in, nullptr, keep);
+                if ((r = launch_sweep_plain64(c, a, in, ga[a], 2)) != BFVM_OK) return r;
+                if (nodes && a < last) node_restore(in);
+            }
             for (int s = 0; s < n_sub; ++s) {
                 k_param_dots<<<kRedBlocks, kRedThreads, 0, c->stream>>>(
-                    g, gy, gz, V(j, 0), V(j, 1), V(j, 2), s, c->nx, c->ny, c->nz, c->pitch,
-                    partial, counter, c->dt, c->dx, dD, dl);
+                    g, gy, dims == 3 ? gz : gy, V(j, 0), V(j, 1), V(j, dims == 3 ? 2 : 1), s,
+                    c->nx, c->ny, c->nz, c->pitch, partial, counter, c->dt, c->dx, dD, dl, dims);
                 c->launches += 1;
             }
             if (any_dir) {   // P' g: the shell's adjoint is zero
                 k_shell<<<gd, 256, 0, c->stream>>>(g, g, nullptr, c->nx, c->ny, c->nz, n_sub,
-                                                   c->pitch, c->d_bc_kind, c->d_bc_value, false);
+                                                   c->pitch, c->d_bc_kind, c->d_bc_value, false,
+                                                   dims);
                 c->launches += 1;
             }
+            if (nodes) node_set(g, nullptr, nullptr);
         }
         return r;
     };

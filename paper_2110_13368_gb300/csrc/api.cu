@@ -458,12 +458,8 @@ bfvm_status bfvm_record(bfvm_ctx* h, int32_t checkpoint_every)
     if (checkpoint_every < 0) return set_err(c, BFVM_EINVAL, "checkpoint_every must be >= 0");
     if (checkpoint_every > 0 && c->precision != 64)
         return set_err(c, BFVM_EINVAL, "the adjoint needs an FP64 context");
-    if (checkpoint_every > 0 && c->dims != 3)
-        return set_err(c, BFVM_ESTATE, "the adjoint covers the 3-D step only");
     if (checkpoint_every > 0 && c->slab >= 0)
         return set_err(c, BFVM_ESTATE, "the adjoint covers whole-grid contexts only");
-    if (checkpoint_every > 0 && c->n_nodes > 0)
-        return set_err(c, BFVM_ESTATE, "the adjoint does not cover Dirichlet nodes");
     if (checkpoint_every > 0) {
         bfvm_status st = sync_source_counts(c);
         if (st != BFVM_OK) return st;
@@ -576,8 +572,6 @@ bfvm_status bfvm_set_dirichlet_nodes(bfvm_ctx* h, int64_t n_nodes, const int64_t
         return set_err(c, BFVM_ESTATE, "Dirichlet nodes are defined for whole-grid contexts");
     if (n_nodes > 0 && c->dims != 3)
         return set_err(c, BFVM_EINVAL, "Dirichlet nodes are defined for the 3-D step");
-    if (n_nodes > 0 && c->record_every != 0)
-        return set_err(c, BFVM_ESTATE, "the adjoint does not cover Dirichlet nodes");
     std::vector<int64_t> hv(n_nodes);
     std::vector<int32_t> hs(n_nodes);
     std::vector<double> hval(n_nodes);
@@ -729,7 +723,8 @@ bfvm_status bfvm_set_option(bfvm_ctx* h, int32_t key, int64_t value)
             if (value == 2 && c->n_nodes > 0)
                 return set_err(c, BFVM_ESTATE, "Dirichlet nodes are defined for the 3-D step");
             if (c->scale_state != 0) return set_err(c, BFVM_ESTATE, "field is mid-rescale; step to a period end first");
-            if (c->record_every != 0) return set_err(c, BFVM_ESTATE, "the adjoint covers the 3-D step only");
+            if (c->record_every != 0)
+                return set_err(c, BFVM_ESTATE, "recording for the adjoint: stop it (bfvm_record(0)) before changing dims");
             c->dims = (int)value;
             // the rescaled form renormalises in the z sweep: 2-D runs the plain form
             c->variant = (c->precision == 64 && c->dims == 3) ? 1 : 0;

@@ -202,7 +202,7 @@ __global__ void __launch_bounds__(256) k_split_fwd(SweepArgs<T> A, SplitArgs Z)
             T d = V.get(k);
             if (L.all_shell) d = (T)vin;
             else if (L.dir && (k == 0 || k == n - 1))
-                d = (T)(DIR == 0 ? (k == 0 ? L.v0 : L.v1) : vin);
+                d = (T)(DIR != 2 ? (k == 0 ? L.v0 : L.v1) : vin);
             if (sizeof(T) == 8) {
                 prev = (T)(fma((double)c, (double)prev, (double)d) * (double)A.r[row + k]);
             } else {

@@ -201,9 +201,10 @@ __device__ __forceinline__ void sweep_one_line(const SweepArgs<T>& A, int64_t li
     double inv_other = 1.0;  // inverse of the other axes' scales (MODE 2)
     const double* own_in = nullptr;
     const double* own_out = nullptr;
-    // the two ends' input values (a Dirichlet node may sit at either end)
+    // the two ends' input values (a Dirichlet node may sit at either end;
+    // the adjoint's solve zeroes them like the shell)
     double v0 = v, v1 = v;
-    if (DIR == 0) end_values(A.ends, line, v, v0, v1);
+    if (DIR != 2) end_values(A.ends, line, v, v0, v1);
     double kl0 = v0, kl1 = v1;
     if (MODE >= 1) {
         own_in = A.sc_p + row + A.axis_off;

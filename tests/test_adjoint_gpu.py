@@ -245,3 +245,54 @@ def test_adjoint_workload_at_full_size(bf):
     # parity tests: |adjoint - fd| <= 1e-4 max_j |grad_j|
     for name, got, est, scale in report:
         assert abs(got - est) <= 1e-4 * scale, (name, got, est, scale)
+
+
+def adjoint_2d_problem():
+    return inputs.make_problem(37, 29, 1, n_sub=2, D=[3e4, 9e2], lam=[0.2, 0.05],
+                               bc_kind=[1, 0], bc_value=[38.0, 0.0], n_cells=40,
+                               U=[10.0, 2.0], S=[1.0, 6.0], rho_star=[38.0, 3.0], seed=7,
+                               steps=9, dt=0.02, dims=2)
+
+
+def adjoint_nodes_problem():
+    """The mixed adjoint problem with Dirichlet nodes: a vessel stub, nodes
+    on faces of the Dirichlet substrate (line ends) and on its edge, on a
+    cell's voxel, on the zero-flux substrate."""
+    p = mixed_adjoint_problem()
+    nx, ny, nz = p.nx, p.ny, p.nz
+
+    def v(x, y, z):
+        return x + nx * (y + ny * z)
+
+    nodes = [(v(9, 7, z), 0, 45.0) for z in range(2, nz - 2)]
+    nodes += [(v(0, 5, 5), 0, 50.0), (v(nx - 1, 8, 3), 0, 20.0), (v(4, 0, 6), 0, 60.0),
+              (v(6, 5, nz - 1), 0, 30.0), (v(0, 0, 4), 0, 99.0),
+              (oracle.cell_voxel(p, p.pos[0]), 0, 12.0), (oracle.cell_voxel(p, p.pos[1]), 1, 4.0),
+              (v(3, 3, 3), 1, 2.5)]
+    vox, sub, val = zip(*nodes)
+    return p.with_(nodes=(np.array(vox, dtype=np.int64), np.array(sub, dtype=np.int32),
+                          np.array(val)))
+
+
+@pytest.mark.parametrize("every,split", [(1, None), (4, None), (4, 2)])
+@pytest.mark.parametrize("kind", ["2d", "nodes"])
+def test_adjoint_2d_and_nodes_match_oracle(bf, kind, every, split):
+    """The adjoint of the 2-D variant and of a step with Dirichlet nodes
+    against the CPU oracle's adjoint (dD, dlambda, dS, dU, dL/drho0 at
+    1e-10); split 2 sends the replayed and adjoint solves through the split
+    line solve."""
+    import torch
+    p = adjoint_2d_problem() if kind == "2d" else adjoint_nodes_problem()
+    target = p.rho0 * 0.5 + np.random.default_rng(4).uniform(0, 1, p.rho0.shape)
+    sim, fin = gpu_forward(bf, p, record=every, split=split)
+    ref_fin = oracle.run(p)
+    assert rel_inf(fin, ref_fin).max() <= 1e-12
+    g = 2.0 * (fin - target)
+    out = sim.backward(torch.as_tensor(g, device="cuda"), want_g0=True)
+    sim.close()
+    ref = oracle.adjoint(p, 2.0 * (ref_fin - target), checkpoint_every=every)
+    for key in ("dD", "dlambda", "dS", "dU", "g0"):
+        a = out[key].cpu().numpy()
+        b = ref[key]
+        scale = np.abs(b).max()
+        assert np.abs(a - b).max() <= 1e-10 * scale, (kind, key, np.abs(a - b).max() / scale)
