@@ -160,14 +160,14 @@ struct PairSweeper {
     // One forward / backward recurrence step.  Plain form (MODE 0):
     // d'_k = (d_k + c d'_{k-1}) r_k, x_k = d'_k + (c r_k) x_{k+1}; in FP32
     // every coefficient is an unevaluated hi + lo pair and each step is a
-    // compensated multiply-add (comp_axpy).  Rescaled form: one FMA each.
+    // hi + lo multiply-add (comp_axpy).  Rescaled form: one FMA each.
     __device__ __forceinline__ T fwd_op(const CoefRow<T>& C, T prev, T d, int k) const
     {
         return fwd_val(C, prev, d, C.a[k], (MODE == 0 && sizeof(T) == 4) ? C.a_lo[k] : (T)0);
     }
     // the same step with the element's coefficients already in registers.
-    // EXACT (FP32, c exactly representable: c_lo = 0): fl(c prev + d) is the
-    // single rounding of one FMA, so the compensated sum is not needed
+    // EXACT (FP32, c exactly representable: c_lo = 0): fl(c prev + d), the
+    // single rounding of one FMA
     template <bool EXACT = false>
     __device__ __forceinline__ T fwd_val(const CoefRow<T>& C, T prev, T d, T a, T a_lo) const
     {

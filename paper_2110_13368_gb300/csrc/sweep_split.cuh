@@ -30,7 +30,7 @@
 // own row in the tile; the line count is padded to a multiple of 32 so that
 // a warp never straddles two segments.
 // In FP32 every table is an unevaluated hi + lo pair and every update a
-// compensated multiply-add (comp_axpy), as in the other FP32 sweeps.
+// hi + lo multiply-add (comp_axpy), as in the other FP32 sweeps.
 // DIR as in the one-thread-per-line sweep: 0 the step (Dirichlet ends set
 // before and after the solve); 1 ends set before only, raw solution kept;
 // 2 ends of the input zeroed, raw solution kept (the adjoint's solves, which

@@ -137,19 +137,19 @@ __device__ __forceinline__ void end_values(const double* ends, int64_t fl, doubl
 //        replay of a step for the adjoint needs it).
 // DIR 2: shell of the input zeroed, raw solution kept (the adjoint solve:
 //        the Dirichlet projection's Jacobian is zero on the shell).
-// fl(a*u + v) for an FP32 coefficient held as a = hi + lo, with one final
-// rounding of an almost exact value: the product error comes from an FMA
-// (TwoProduct) and the sum error from Knuth's TwoSum; explicit _rn
-// intrinsics keep the compiler from contracting them.
+// a*u + v for an FP32 coefficient held as a = hi + lo (lo the rounding error
+// of hi), as fl(fl(hi*u + fl(lo*u)) + v): the low part's product enters the
+// FMA below its rounding, so the product is rounded once from a*u itself
+// and carries no bias from the coefficient's own rounding (which would push
+// every sweep the same way); the sum then rounds once more.  Both roundings
+// are to nearest; in the Thomas recurrences every term is non-negative for a
+// non-negative field, so nothing cancels.  Three operations, three deep on
+// the recurrence's chain (a TwoSum-compensated sum, one rounding in all,
+// took eleven, nine deep, on chains that bound the FP32 sweeps).  Explicit
+// _rn intrinsics keep the compiler from contracting them.
 __device__ __forceinline__ float comp_axpy(float a_hi, float a_lo, float u, float v)
 {
-    float p = __fmul_rn(a_hi, u);
-    float pe = __fmaf_rn(a_hi, u, -p);
-    float s = __fadd_rn(p, v);
-    float z = __fsub_rn(s, p);
-    float se = __fadd_rn(__fsub_rn(p, __fsub_rn(s, z)), __fsub_rn(v, z));
-    float corr = __fmaf_rn(a_lo, u, __fadd_rn(pe, se));
-    return __fadd_rn(s, corr);
+    return __fadd_rn(__fmaf_rn(a_hi, u, __fmul_rn(a_lo, u)), v);
 }
 
 // One line per thread: the generic sweep used by the adjoint passes, by the
