@@ -260,8 +260,9 @@ bfvm_status bfvm_get_info(const bfvm_ctx* ctx, int64_t* info);
  *          decay share lambda dt / 2; the Dirichlet shell is the outer layer
  *          of the four edges (the z layer is not a boundary); sources as in
  *          3-D with V_vox = dx^3.  Needs nz == 1; FP64 then runs the plain
- *          Thomas form (option 1 = 0).  2-D contexts cannot join a batch
- *          (BFVM_ESTATE); dims cannot change while recording.
+ *          Thomas form (option 1 = 0).  2-D contexts can join a batch (it
+ *          then runs the plain form for all members); dims cannot change
+ *          while recording.
  *   key 11 split line solve of the plain form (the FP32 form, FP64 with
  *          key 1 = 0, and the 2-D variant): each line cut into segments
  *          solved in parallel, joined through the affine form of the two
@@ -299,11 +300,14 @@ bfvm_status bfvm_kernel_times(bfvm_ctx* ctx, double* ms, int64_t* counts, int32_
  * Motivation").  Create a batch over n_members existing contexts:
  *   members[i]  contexts of one device, all of the same precision, each at a
  *               rescale period boundary (fresh, or right after
- *               bfvm_set_density) and not recording; the batch keeps
+ *               bfvm_set_density) and not recording, 3-D or 2-D (option 10;
+ *               with any 2-D member the batch runs the plain Thomas form),
+ *               without Dirichlet nodes and not z-slabs; the batch keeps
  *               pointers to them, so they must outlive it
  *   cuda_stream stream of the batched launches
  * Errors: BFVM_EINVAL (NULL pointers, n_members < 1), BFVM_ESTATE (mixed
- * precision, a member mid-period or recording), BFVM_ENOMEM / BFVM_ECUDA.
+ * precision, a member mid-period, recording, holding Dirichlet nodes or a
+ * z-slab), BFVM_ENOMEM / BFVM_ECUDA.
  */
 bfvm_status bfvm_batch_create(bfvm_batch** out, bfvm_ctx* const* members,
                               int32_t n_members, void* cuda_stream);

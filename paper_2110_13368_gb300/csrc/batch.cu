@@ -96,7 +96,7 @@ bfvm_status bfvm_batch_create(bfvm_batch** out, bfvm_ctx* const* members, int32_
         }
         if (i == 0) b->precision = c->precision;
         if (c->precision != b->precision || c->scale_state != 0 || c->record_every != 0 ||
-            c->dims != 3 || c->n_nodes > 0 || c->slab >= 0) {
+            c->n_nodes > 0 || c->slab >= 0) {
             delete h;
             return BFVM_ESTATE;
         }

@@ -495,7 +495,7 @@ __device__ __forceinline__ void step_epilogue_b(const StepSched& Q, const BMembe
         const EpiArgs<T>& E = Dm[Gg.m].E;
         const int n_sub = Dm[Gg.m].n_sub;
         const int i = dep_index(tf, NS, 3, g);   // last swept axis of the group
-        const int sh_chunks = Gg.dir ? (int)epi_shell_chunks(E.nx, E.ny, E.nz) : 0;
+        const int sh_chunks = Gg.dir ? (int)epi_shell_chunks_z(E.nx, E.ny, E.nz, E.zf) : 0;
         const bool shell = k < sh_chunks;
         // a source chunk reads its entries before its waits (see
         // step_epilogue of the single-context step)
@@ -528,14 +528,16 @@ __device__ __forceinline__ void step_epilogue_b(const StepSched& Q, const BMembe
         }
         if (i >= 0) wait_count(Q, Q.done + i, (unsigned)(tf[i + 1] - tf[i]) + Q.extra_need, lane);
         if (shell) {
-            const int64_t per = shell_count(E);
+            const int64_t per = shell_count_z(E.nx, E.ny, E.nz, E.zf);
+            // without z faces the enumeration starts past its z planes
+            const int64_t skip = E.zf ? 0 : 2 * (int64_t)E.nx * E.ny;
             const int64_t lo_t = (int64_t)k * kEpiChunk;
             const int64_t hi_t = min(per, lo_t + kEpiChunk);
             for (int64_t t0 = lo_t + lane; t0 < hi_t; t0 += 32 * kEpiUnroll) {
 #pragma unroll
                 for (int u = 0; u < kEpiUnroll; ++u) {
                     const int64_t t = t0 + 32 * u;
-                    if (t < hi_t) shell_voxel(E, s, Gg.v, t);
+                    if (t < hi_t) shell_voxel(E, s, Gg.v, t + skip);
                 }
             }
             fence_acq_rel_gpu();

@@ -94,6 +94,7 @@ struct EpiArgs {
     const double* beta;
     const int32_t* vox;     // voxel x + nx (y + ny z)
     const int32_t* sub;
+    int zf;                 // batched step: z planes on the boundary (0: the 2-D variant)
 };
 
 constexpr int kEpiUnroll = 8;                  // independent elements per lane
@@ -111,6 +112,18 @@ __host__ __device__ inline int64_t epi_shell_chunks(int nx, int ny, int nz)
 __host__ __device__ inline int64_t epi_src_chunks(int64_t n_seg)
 {
     return (n_seg + kEpiChunk - 1) / kEpiChunk;
+}
+
+// The same for a grid whose z planes are boundary faces (zf != 0: the 3-D
+// shell) or not (zf == 0: the 2-D variant's four edges, the enumeration of
+// shell_voxel without its z-plane part)
+__host__ __device__ inline int64_t shell_count_z(int nx, int ny, int nz, int zf)
+{
+    return 2 * ((zf ? (int64_t)nx * ny : 0) + (int64_t)nx * nz + (int64_t)ny * nz);
+}
+__host__ __device__ inline int64_t epi_shell_chunks_z(int nx, int ny, int nz, int zf)
+{
+    return (shell_count_z(nx, ny, nz, zf) + kEpiChunk - 1) / kEpiChunk;
 }
 
 // about 2^21 polls with a 128 ns back-off: well over a second

@@ -677,6 +677,7 @@ bfvm_status launch_step_fused(Ctx* c, int p, bool renorm, const T* r, const T* c
     E.beta = c->src.beta;
     E.vox = c->src.vox;
     E.sub = c->src.sub;
+    E.zf = c->zfaces();
     const size_t smem = M.fixed + M.pair * pairs;
     int64_t grid = ceil_div(std::max<int64_t>(c->n_tasks, 1), pairs);
     grid = std::max<int64_t>(grid, ceil_div(Q.n_epi_chunks, 8 * pairs));
@@ -1254,7 +1255,7 @@ __global__ void k_batch_sources(const BatchDesc<T>* __restrict__ D,
 // solve is, per stage st (h = 2^st), d_k <- d_k - k1_k d_{k-h} - k2_k d_{k+h}
 // (two FMAs per element), and x_k = d_k / b_k after the last stage.
 struct PcrSys {
-    double c, ell;   // off-diagonal magnitude and lambda dt / 3
+    double c, ell;   // off-diagonal magnitude and lambda dt / dims (3, or 2 in 2-D)
     int n, S;        // line length and stage count (2^S >= n)
     int64_t off;     // first double of this system in the FP64 table
 };
@@ -1378,7 +1379,8 @@ __global__ void __launch_bounds__(256) k_batch_pcr_x(const BatchDesc<T>* __restr
         T* f = A.field + (((int64_t)s * nz + oz) * ny + oy) * A.pitch;
         const bool dir = A.bc_kind[s] == BFVM_BC_DIRICHLET;
         const double v = A.bc_value[s];
-        const bool shell = dir && (oy == 0 || oy == ny - 1 || oz == 0 || oz == nz - 1);
+        const bool shell = dir && (oy == 0 || oy == ny - 1 || ((A.zfaces & 1) && oz == 0) ||
+                                   ((A.zfaces & 2) && oz == nz - 1));
         const int64_t row = (int64_t)s * A.L;
         double kline = v;
         const double* scp1 = nullptr;
@@ -1493,7 +1495,8 @@ bfvm_status batch_build_one_launch(BatchImpl* b)
             const int64_t n_seg = c->src.cap > 0 ? c->src.n_seg : 0;
             for (int s = 0; s < c->n_sub; ++s, ++g)
                 epi[g + 1] = epi[g] +
-                             (c->bc_kind[s] == BFVM_BC_DIRICHLET ? epi_shell_chunks(c->nx, c->ny, c->nz) : 0) +
+                             (c->bc_kind[s] == BFVM_BC_DIRICHLET
+                                  ? epi_shell_chunks_z(c->nx, c->ny, c->nz, c->zfaces()) : 0) +
                              epi_src_chunks(n_seg);
         }
     }
@@ -1542,6 +1545,7 @@ bfvm_status batch_build_one_launch(BatchImpl* b)
             E.beta = c->src.beta;
             E.vox = c->src.vox;
             E.sub = c->src.sub;
+            E.zf = c->zfaces();
             d.n_sub = c->n_sub;
             d.g0 = g0;
             g0 += c->n_sub;
@@ -1644,6 +1648,7 @@ bfvm_status batch_build_t(BatchImpl* b)
         BatchDesc<T>& d = desc[m];
         for (int a = 0; a < 3; ++a) {
             d.ax[a] = make_args<T>(c, a, 0, r, cr, cv);
+            if (a >= c->dims) continue;   // a 2-D member has no z sweep
             if (d.ax[a].n > max_n) max_n = d.ax[a].n;
             int64_t nb = ceil_div(d.ax[a].n_lines, 32);
             for (int64_t k = 0; k < nb; ++k) tasks[a].push_back(make_int2(m, (int)k));
@@ -1684,7 +1689,7 @@ bfvm_status batch_build_t(BatchImpl* b)
             for (int sb = 0; sb < c->n_sub; ++sb) {
                 PcrSys q;
                 q.c = c->D[sb] * c->dt / (c->dx * c->dx);
-                q.ell = c->lambda[sb] * c->dt / 3.0;
+                q.ell = c->lambda[sb] * c->dt / (double)c->dims;   // the axis' decay share
                 q.n = c->nx;
                 q.S = S;
                 q.off = total;

@@ -240,3 +240,56 @@ def test_one_launch_batch_wait_gives_up_with_status(bf):
     for s in sims:
         s.close()
 
+
+
+def mixed_2d_batch(steps=7):
+    """2-D members (x lines of 1 to 128 voxels, Dirichlet and zero-flux
+    substrates) next to 3-D members; with any 2-D member the batch runs the
+    plain form."""
+    probs = []
+    for i, (nx, ny) in enumerate([(1, 9), (5, 7), (33, 20), (64, 3), (128, 17), (47, 61)]):
+        probs.append(inputs.make_problem(nx, ny, 1, n_sub=2, D=[2e4 * (i + 1), 3e2],
+                                         lam=[0.1, 0.01 * (i + 1)], bc_kind=[(i + 1) % 2, 0],
+                                         bc_value=[38.0, 0.0], n_cells=10 + 5 * i,
+                                         U=[10.0, 1.0], S=[0.5, 5.0], rho_star=[1.0, 2.0],
+                                         steps=steps, seed=40 + i, dims=2))
+    probs.append(inputs.make_problem(17, 9, 12, n_sub=2, D=[1e5, 4e3], lam=[0.1, 0.02],
+                                     bc_kind=[1, 0], bc_value=[38.0, 0.0], n_cells=80,
+                                     U=[10.0, 1.0], S=[0.0, 5.0], rho_star=[1.0, 2.0],
+                                     steps=steps, seed=9))
+    probs.append(inputs.make_problem(30, 4, 5, n_sub=2, D=[3e4, 1e3], lam=[0.2, 0.05],
+                                     bc_kind=[0, 1], bc_value=[0.0, 20.0], n_cells=40,
+                                     U=[5.0, 1.0], S=[1.0, 2.0], rho_star=[3.0, 9.0],
+                                     steps=steps, seed=11))
+    return probs
+
+
+@pytest.mark.parametrize("precision,tol", [(64, 1e-12), (32, 1e-5)])
+@pytest.mark.parametrize("mode", ["one_launch", "pcr_x", "thomas"])
+def test_batch_with_2d_members_matches_oracle(bf, precision, tol, mode):
+    """2-D members in a batch (no z sweep, the four-edge shell) beside 3-D
+    members: the one-launch step and the per-phase launches with PCR or
+    Thomas x lines, each member against its own oracle run."""
+    probs = mixed_2d_batch()
+    sims = [bf.Sim.from_problem(p, precision=precision) for p in probs]
+    batch = bf.Batch(sims)
+    if mode == "one_launch":
+        batch.set_option(bf.BATCH_OPT_ONE_LAUNCH, 1)
+    else:
+        batch.set_option(bf.BATCH_OPT_ONE_LAUNCH, 0)
+        batch.set_shape(0, 1 if mode == "pcr_x" else 0, 4)
+        batch.set_shape(1, 0, 4)
+        batch.set_shape(2, 0, 4)
+    launches0 = batch.info()["launches"]
+    for n in (3, 4):
+        batch.step(n)
+    batch.sync()
+    if mode == "one_launch":
+        assert (batch.info()["launches"] - launches0) / 7 == 1.0
+    for p, s in zip(probs, sims):
+        got = s.get_density().double().cpu().numpy()
+        err = rel_inf(got, oracle.run(p))
+        assert np.all(err <= tol), (p.name, p.nx, p.ny, p.nz, mode, err)
+    batch.close()
+    for s in sims:
+        s.close()
